@@ -1,0 +1,459 @@
+"""Pins for the CPU oracle: each test ties it to something other than itself.
+
+Closed forms (hand-derived TPFA matrices, exact Cholesky on a tridiagonal
+matrix), dense linear algebra built independently from the paper's formulas
+(Eq. barB, Eq. tildeB1, the block form of Section 2.1.2, the V-cycle recursion
+of Section 3.3, the Galerkin product of Section 3.2), dense solves and
+eigenvalues (Theorems 2.1 and 2.2), and invariants of the splitting rules.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1205_6113_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_op(apply, n):
+    """Materialise a linear operator column by column from unit vectors."""
+    M = np.zeros((n, n))
+    e = np.zeros(n)
+    for j in range(n):
+        e[j] = 1.0
+        M[:, j] = apply(e)
+        e[j] = 0.0
+    return M
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def a_norm(E, A):
+    """||E||_A = ||A^{1/2} E A^{-1/2}||_2."""
+    w, V = np.linalg.eigh(A)
+    Ah = V @ np.diag(np.sqrt(w)) @ V.T
+    Aih = V @ np.diag(1.0 / np.sqrt(w)) @ V.T
+    return np.linalg.norm(Ah @ E @ Aih, 2)
+
+
+@pytest.fixture(scope="module")
+def small3d():
+    """A 9 x 8 x 6 correlated problem with a 4-level hierarchy (coarse_max 20)."""
+    p = inputs.small_3d(9, 8, 6, seed=11)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=20)
+    assert orc.nlevels >= 3
+    return p, A, orc, A.to_dense()
+
+
+# --------------------------------------------------------------------------------------------
+# TPFA assembly (Section 4, Eq. model with c = 0)
+# --------------------------------------------------------------------------------------------
+def test_tpfa_matches_hand_derived_2x2():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "tpfa_2x2.txt")) if l.strip() and l[0] != "#"]
+    expect = np.zeros((4, 4))
+    for r, c, num, den in rows:
+        expect[int(r), int(c)] = float(num) / float(den)
+    A = O.tpfa(2, 2, 1, np.log([1.0, 3.0, 2.0, 4.0]), 1.0, inputs.FACE_X0)
+    assert A.nnz == 12
+    assert rel(A.to_dense(), expect) < 1e-14
+
+
+def test_tpfa_homogeneous_is_kronecker_laplacian():
+    nx, ny, nz, r = 5, 4, 3, 0.1
+
+    def lap1(m):      # 1-D Neumann Laplacian with unit transmissibility
+        L = 2 * np.eye(m) - np.eye(m, k=1) - np.eye(m, k=-1)
+        L[0, 0] = L[-1, -1] = 1.0
+        return L if m > 1 else np.zeros((1, 1))
+
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    expect = (np.kron(Iz, np.kron(Iy, lap1(nx))) + np.kron(Iz, np.kron(lap1(ny), Ix))
+              + r * np.kron(lap1(nz), np.kron(Iy, Ix)))
+    for c in range(nx * ny * nz):
+        if c % nx == 0:
+            expect[c, c] += 2.0
+    A = O.tpfa(nx, ny, nz, np.zeros(nx * ny * nz), r, inputs.FACE_X0)
+    assert A.nnz == O.lib().orc_tpfa_nnz(nx, ny, nz)
+    assert rel(A.to_dense(), expect) < 1e-15
+
+
+def test_tpfa_properties_random_field(small3d):
+    p, A, _, D = small3d
+    assert np.array_equal(D, D.T)
+    off = D - np.diag(np.diag(D))
+    assert np.all(off <= 0)
+    # A 1 = Dirichlet half-cell transmissibility on x = 0 cells, zero elsewhere
+    k = np.exp(p.logk)
+    bnd = np.where(np.arange(A.n) % p.nx == 0, 2.0 * k, 0.0)
+    assert np.max(np.abs(D.sum(axis=1) - bnd)) < 1e-12 * np.max(np.abs(D))
+    assert np.linalg.eigvalsh(D)[0] > 0
+
+
+# --------------------------------------------------------------------------------------------
+# IC(0) = Algorithm 3.1 with k = 0 (Section 3.1, Section 3.3)
+# --------------------------------------------------------------------------------------------
+def ic_factors(A, lu):
+    n = A.n
+    L = np.eye(n)
+    U = np.zeros((n, n))
+    for i in range(n):
+        for p in range(A.rowptr[i], A.rowptr[i + 1]):
+            j = A.col[p]
+            if j < i:
+                L[i, j] = lu[p]
+            else:
+                U[i, j] = lu[p]
+    return L, U
+
+
+def test_ic0_on_tridiagonal_is_exact_cholesky():
+    logk = inputs.random_vector(40, seed=3)
+    A = O.tpfa(40, 1, 1, logk, 1.0, inputs.FACE_X0)
+    orc = O.Oracle(A, coarse_max=8)
+    L, U = ic_factors(A, orc.ic0_values())
+    D = A.to_dense()
+    assert rel(L @ U, D) < 1e-14               # no fill is dropped: LU = A exactly
+    assert rel(U, np.diag(np.diag(U)) @ L.T) < 1e-14
+    b = inputs.random_vector(40, seed=4)
+    r = orc.pcg(b, op=O.B, tol=1e-12, maxit=10)
+    assert r["status"] == 0 and r["iters"] == 1
+    # B = A^{-1} => B_co = A^{-1} (Eq. tildeB1 with (I - S^T A) A^{-1} (I - A S) = A^{-1} - S~)
+    r = orc.pcg(b, op=O.BCO, tol=1e-12, maxit=10)
+    assert r["status"] == 0 and r["iters"] == 1
+
+
+def test_ic0_matches_a_on_its_pattern(small3d):
+    _, A, orc, D = small3d
+    L, U = ic_factors(A, orc.ic0_values())
+    LU = L @ U
+    pat = D != 0
+    assert rel(LU[pat], D[pat]) < 1e-13        # residual R = A - LU vanishes on the pattern
+    assert np.all(np.diag(U) > 0)
+    assert rel(U, np.diag(np.diag(U)) @ L.T) < 1e-13    # SPD => U = D L^T (IC(0))
+    B = np.linalg.inv(LU)
+    Bm = dense_op(lambda v: orc.apply(O.B, v), A.n)
+    assert rel(Bm, B) < 1e-11
+
+
+def test_ic0_breakdown_is_reported():
+    # [[1, 2], [2, 1]] has a negative second pivot
+    A = O.Csr(2, [0, 2, 4], [0, 1, 0, 1], [1.0, 2.0, 2.0, 1.0])
+    with pytest.raises(O.OracleError) as e:
+        O.Oracle(A)
+    assert e.value.status == 2
+
+
+def test_invalid_csr_is_rejected():
+    A = O.Csr(2, [0, 2, 3], [1, 0, 1], [1.0, 2.0, 1.0])     # unsorted row, missing diagonal
+    with pytest.raises(O.OracleError) as e:
+        O.Oracle(A)
+    assert e.value.status == 1
+
+
+# --------------------------------------------------------------------------------------------
+# AMG hierarchy (Section 3.2) and the V-cycle (Algorithm 3.2, Section 3.3)
+# --------------------------------------------------------------------------------------------
+def strength_dense(D, theta):
+    n = D.shape[0]
+    S = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        neg = -D[i].copy()
+        neg[i] = -np.inf
+        mx = neg.max()
+        if mx > 0:
+            S[i] = neg >= theta * mx
+            S[i, i] = False
+    return S
+
+
+def test_galerkin_products(small3d):
+    _, _, orc, _ = small3d
+    for l in range(orc.nlevels - 1):
+        Al = orc.level_A(l).to_dense()
+        P = orc.level_P(l).to_dense()
+        Ac = orc.level_A(l + 1).to_dense()
+        assert rel(Ac, P.T @ Al @ P) < 1e-13
+        assert rel(Ac, Ac.T) < 1e-14
+
+
+def test_splitting_and_interpolation_invariants(small3d):
+    _, _, orc, _ = small3d
+    for l in range(orc.nlevels - 1):
+        D = orc.level_A(l).to_dense()
+        S = strength_dense(D, 0.25)
+        cf, _ = orc.level_cf_colour(l)
+        P = orc.level_P(l).to_dense()
+        C = cf == 1
+        cnt_t = S.sum(axis=0)                          # |S^T_i|
+        assert set(np.unique(cf)) <= {0, 1}
+        assert np.all(cnt_t[C] > 0)                    # no C point without dependants
+        for i in np.where(~C)[0]:
+            if cnt_t[i] > 0:                           # F by a C point it strongly depends on
+                assert np.any(S[i] & C)
+        mutual = S & S.T
+        assert not np.any(mutual[np.ix_(C, C)])        # no two C points strongly coupled both ways
+        # C rows are identity rows; F rows interpolate only from strong C neighbours
+        cidx = np.cumsum(C) - 1
+        for i in range(D.shape[0]):
+            nzc = np.nonzero(P[i])[0]
+            if C[i]:
+                assert list(nzc) == [cidx[i]] and P[i, cidx[i]] == 1.0
+            else:
+                allowed = set(cidx[np.where(S[i] & C)[0]])
+                assert set(nzc) <= allowed
+                # zero row sum and no positive couplings => constants are interpolated exactly
+                if len(nzc) and abs(D[i].sum()) < 1e-12 * D[i, i] and np.all(np.delete(D[i], i) <= 0):
+                    assert abs(P[i].sum() - 1.0) < 1e-13
+        # every F point with strong C neighbours has a nonempty interpolation row
+        for i in np.where(~C)[0]:
+            if np.any(S[i] & C):
+                assert np.count_nonzero(P[i]) > 0
+
+
+def test_colouring_is_proper(small3d):
+    _, _, orc, _ = small3d
+    for l in range(orc.nlevels - 1):
+        D = orc.level_A(l).to_dense()
+        _, colour = orc.level_cf_colour(l)
+        ii, jj = np.nonzero(D)
+        off = ii != jj
+        assert np.all(colour[ii[off]] != colour[jj[off]])
+        assert colour.min() == 0 and orc.level_sizes(l)["ncolours"] == colour.max() + 1
+
+
+def gs_dense(D, colour, backward):
+    n = D.shape[0]
+    M = np.diag(np.diag(D)).copy()
+    for i in range(n):
+        for j in range(n):
+            if i != j and D[i, j] != 0:
+                if (colour[j] < colour[i]) != backward and colour[j] != colour[i]:
+                    M[i, j] = D[i, j]
+    return np.linalg.inv(M)
+
+
+def test_gauss_seidel_smoother_is_multicolour_gs(small3d):
+    _, _, orc, _ = small3d
+    for l in range(orc.nlevels - 1):
+        D = orc.level_A(l).to_dense()
+        _, colour = orc.level_cf_colour(l)
+        n = D.shape[0]
+        Sf = dense_op(lambda v: orc.level_apply(l, 1, v), n)
+        Sb = dense_op(lambda v: orc.level_apply(l, 2, v), n)
+        assert rel(Sf, gs_dense(D, colour, False)) < 1e-12
+        assert rel(Sb, gs_dense(D, colour, True)) < 1e-12
+        assert rel(Sb, Sf.T) < 1e-12                   # backward sweep = adjoint of forward sweep
+        assert a_norm(np.eye(n) - Sf @ D, D) < 1.0      # GS is norm-convergent
+
+
+def test_vcycle_matches_recursion(small3d):
+    """I - B_l A_l = (I - S_l^T A_l)(I - P B_{l-1} P^T A_l)(I - S_l A_l), B_0 = A_0^{-1} (Section 3.3)."""
+    _, _, orc, _ = small3d
+    L = orc.nlevels
+    Dc = orc.level_A(L - 1).to_dense()
+    Bc = np.linalg.inv(Dc)
+    assert rel(dense_op(lambda v: orc.level_apply(L - 1, 3, v), Dc.shape[0]), Bc) < 1e-12
+    Bnext = Bc
+    for l in range(L - 2, -1, -1):
+        D = orc.level_A(l).to_dense()
+        n = D.shape[0]
+        _, colour = orc.level_cf_colour(l)
+        P = orc.level_P(l).to_dense()
+        I = np.eye(n)
+        Sf, Sb = gs_dense(D, colour, False), gs_dense(D, colour, True)
+        E = (I - Sb @ D) @ (I - P @ Bnext @ P.T @ D) @ (I - Sf @ D)
+        B = (I - E) @ np.linalg.inv(D)
+        V = dense_op(lambda v: orc.level_apply(l, 4, v), n)
+        assert rel(V, B) < 1e-11
+        assert a_norm(E, D) < 1.0                      # the cycle is norm-convergent
+        Bnext = B
+
+
+def test_vcycle_symmetric_and_adjoint(small3d):
+    _, A, orc, D = small3d
+    n = A.n
+    S = dense_op(lambda v: orc.apply(O.S, v), n)
+    ST = dense_op(lambda v: orc.apply(O.ST, v), n)
+    assert rel(S, S.T) < 1e-12
+    assert rel(ST, S.T) < 1e-12
+    rho = a_norm(np.eye(n) - S @ D, D) ** 2
+    assert rho < 1.0
+
+
+def test_single_level_hierarchy_is_exact():
+    p = inputs.small_3d(5, 4, 3, seed=2)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=1000)
+    assert orc.nlevels == 1
+    D = A.to_dense()
+    S = dense_op(lambda v: orc.apply(O.S, v), A.n)
+    assert rel(S, np.linalg.inv(D)) < 1e-12            # S = A^{-1}
+    Bco = dense_op(lambda v: orc.apply(O.BCO, v), A.n)
+    assert rel(Bco, np.linalg.inv(D)) < 1e-11          # S = A^{-1} => B_co = A^{-1}
+    r = orc.pcg(p.rhs(), op=O.BCO, tol=1e-12, maxit=10)
+    assert r["status"] == 0 and r["iters"] == 1
+
+
+# --------------------------------------------------------------------------------------------
+# The combined preconditioner (Algorithm 2.1, Eqs. barB and tildeB1, Section 2.1)
+# --------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def materialised(small3d):
+    _, A, orc, D = small3d
+    n = A.n
+    ops = {k: dense_op(lambda v, op=op: orc.apply(op, v), n)
+           for k, op in dict(S=O.S, ST=O.ST, B=O.B, Bco=O.BCO, St=O.STILDE, Bh=O.BHAT).items()}
+    return D, ops
+
+
+def test_error_propagation_eq_barB(materialised):
+    D, M = materialised
+    I = np.eye(D.shape[0])
+    lhs = I - M["Bco"] @ D
+    rhs = (I - M["ST"] @ D) @ (I - M["B"] @ D) @ (I - M["S"] @ D)
+    assert rel(lhs, rhs) < 1e-11
+
+
+def test_closed_form_eq_tildeB1(materialised):
+    D, M = materialised
+    I = np.eye(D.shape[0])
+    S, ST, B = M["S"], M["ST"], M["B"]
+    St = S + ST - ST @ D @ S
+    assert rel(M["St"], St) < 1e-11                   # two cycles give S~
+    assert rel(M["Bco"], St + (I - ST @ D) @ B @ (I - D @ S)) < 1e-11
+    assert rel(M["Bco"], St + B - ST @ D @ B - B @ D @ S + ST @ D @ B @ D @ S) < 1e-11
+    assert rel(M["Bh"], St + B) < 1e-11                # additive variant, Eq. Ba
+
+
+def test_block_factorisation_form(materialised):
+    """(I, I) [[I, -S^T A], [0, I]] diag(S~, B) [[I, 0], [-A S, I]] (I; I) = B_co (Section 2.1.2)."""
+    D, M = materialised
+    n = D.shape[0]
+    I, Z = np.eye(n), np.zeros((n, n))
+    St = M["St"]
+    left = np.block([[I, -M["ST"] @ D], [Z, I]])
+    mid = np.block([[St, Z], [Z, M["B"]]])
+    right = np.block([[I, Z], [-D @ M["S"], I]])
+    II = np.vstack([I, I])
+    assert rel(II.T @ left @ mid @ right @ II, M["Bco"]) < 1e-11
+
+
+def test_bco_is_spd_theorem_2_1(materialised):
+    _, M = materialised
+    Bco = M["Bco"]
+    assert rel(Bco, Bco.T) < 1e-11
+    assert np.linalg.eigvalsh(0.5 * (Bco + Bco.T))[0] > 0
+
+
+def test_theorem_2_2_condition_bound(materialised):
+    D, M = materialised
+    Lh = np.linalg.cholesky(D)                         # similarity to symmetric forms
+    def eig(Bm):
+        return np.linalg.eigvalsh(Lh.T @ (0.5 * (Bm + Bm.T)) @ Lh)
+    ev_b = eig(M["B"])
+    m0, m1 = ev_b[0], ev_b[-1]
+    rho = 1.0 - eig(M["St"])[0]                        # ||I - S A||_A^2 = 1 - lambda_min(S~ A)
+    assert 0 < rho < 1
+    ev = eig(M["Bco"])
+    kappa = ev[-1] / ev[0]
+    lo, hi, bound = O.thm22_bound(m0, m1, rho)
+    assert ev[0] >= lo * (1 - 1e-10) and ev[-1] <= hi * (1 + 1e-10)
+    assert kappa <= bound * (1 + 1e-10)
+    assert kappa < m1 / m0                             # Eq. ine:better_B
+    if m1 > 1 >= m0 and rho >= 1 - m0 / (m1 - 1):     # Eq. ine:better_S
+        assert kappa <= 1.0 / (1.0 - rho) * (1 + 1e-10)
+
+
+def test_lanczos_estimate_matches_dense_extremes(small3d, materialised):
+    p, A, orc, D = small3d
+    _, M = materialised
+    r = orc.pcg(inputs.random_vector(A.n, seed=9), op=O.BCO, tol=1e-13, maxit=500)
+    assert r["status"] == 0
+    lo, hi = O.lanczos_extremes(r["alpha"], r["beta"])
+    Lh = np.linalg.cholesky(D)
+    ev = np.linalg.eigvalsh(Lh.T @ M["Bco"] @ Lh)
+    # Ritz values lie inside the spectrum; the small end (which sets kappa here) has converged
+    assert ev[0] * (1 - 1e-10) <= lo and hi <= ev[-1] * (1 + 1e-10)
+    assert abs(lo - ev[0]) < 1e-6 * ev[-1]
+    assert hi > 0.99 * ev[-1]
+
+
+# --------------------------------------------------------------------------------------------
+# PCG against dense Cholesky solves, SPD probes, status codes
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(6, 6, 1), (4, 4, 3), (7, 5, 4)])
+@pytest.mark.parametrize("opname", ["bco", "amg", "ilu", "bhat", "none"])
+def test_pcg_matches_dense_cholesky(shape, opname):
+    nx, ny, nz = shape
+    p = inputs.small_3d(nx, ny, nz, seed=5) if nz > 1 else inputs.lognormal_2d(nx, ny, seed=5)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=12)
+    b = inputs.random_vector(A.n, seed=6)
+    D = A.to_dense()
+    c = np.linalg.cholesky(D)
+    xs = np.linalg.solve(c.T, np.linalg.solve(c, b))
+    r = orc.pcg(b, op=O.OPS[opname], tol=1e-12, maxit=2000)
+    assert r["status"] == 0
+    assert np.linalg.norm(r["x"] - xs) / np.linalg.norm(xs) <= 1e-8
+    assert r["true_res"] < 1e-11
+    assert r["res_hist"][0] == 1.0 and r["res_hist"][-1] < 1e-12
+
+
+def test_pcg_on_64x64_lognormal_matches_dense():
+    p = inputs.lognormal_2d()
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A)
+    b = p.rhs()
+    xs = np.linalg.solve(A.to_dense(), b)
+    for opname in ("bco", "amg", "ilu"):
+        r = orc.pcg(b, op=O.OPS[opname], tol=1e-12, maxit=3000)
+        assert r["status"] == 0
+        assert np.linalg.norm(r["x"] - xs) / np.linalg.norm(xs) <= 1e-8
+
+
+def test_bco_symmetric_positive_on_random_vectors():
+    p = inputs.lognormal_2d()
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A)
+    rng = np.random.Generator(np.random.PCG64(12))
+    for _ in range(100):
+        x, y = rng.standard_normal(A.n), rng.standard_normal(A.n)
+        Bx, By = orc.apply(O.BCO, x), orc.apply(O.BCO, y)
+        assert abs(x @ By - y @ Bx) <= 1e-12 * abs(x @ By) + 1e-14 * np.linalg.norm(x) * np.linalg.norm(By)
+        assert x @ Bx > 0
+
+
+def test_status_codes():
+    p = inputs.small_3d(6, 5, 4, seed=1)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=12)
+    b = p.rhs()
+    r = orc.pcg(b, op=O.I, tol=1e-14, maxit=3)
+    assert r["status"] == 3 and r["iters"] == 3
+    r = orc.pcg(np.zeros(A.n), op=O.BCO, tol=1e-6, maxit=10)
+    assert r["status"] == 0 and r["iters"] == 0 and not r["x"].any()
+    bad = b.copy()
+    bad[3] = np.nan
+    r = orc.pcg(bad, op=O.BCO, tol=1e-6, maxit=10)
+    assert r["status"] == 4
+
+
+def test_colour_ordered_ic0_is_ic0_of_permuted_matrix(small3d):
+    p, A, _, D = small3d
+    orc = O.Oracle(A, coarse_max=20, ic_colour_order=True)
+    _, colour = orc.level_cf_colour(0)
+    order = np.concatenate([np.where(colour == c)[0] for c in range(colour.max() + 1)])
+    Dp = D[np.ix_(order, order)]
+    B = dense_op(lambda v: orc.apply(O.B, v), A.n)
+    Bp = B[np.ix_(order, order)]
+    # (L U) of the permuted matrix equals it on its pattern and L U is lower x upper
+    LU = np.linalg.inv(Bp)
+    pat = Dp != 0
+    assert rel(LU[pat], Dp[pat]) < 1e-11
+    r = orc.pcg(p.rhs(), op=O.BCO, tol=1e-10, maxit=200)
+    assert r["status"] == 0
