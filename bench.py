@@ -1,0 +1,381 @@
+"""Benchmark: PCG solve time to a 1e-6 relative residual on one GB300.
+
+Headline (``value``): milliseconds per combined-preconditioned (B_co) PCG solve, FP64, on the
+128 x 128 x 64 correlated-lognormal two-point-flux matrix (1,048,576 unknowns), inputs resident
+in HBM.  The same run times the AMG-alone (S~, two V-cycles) and IC(0)-alone preconditioners and
+the FP32 / FP32+BF16 preconditioner variants, the end-to-end solve through host buffers, the
+dominant kernel against the measured HBM roofline, and the CPU oracle as a reported baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the problem (independent replicas,
+weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1205_6113_gb300 import inputs  # noqa: E402
+
+WORKLOAD = "correlated3d_128x128x64"
+TOL = 1e-6
+MAXIT = 5000
+METRIC = "PCG ms to 1e-6 rel. residual (combined vs AMG/ILU alone, FP32 vs FP64 prec), %HBM peak"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                mx.append(float(s[2]))
+                for nm, v in zip(names, s[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# algorithmic bytes (compulsory traffic of each kernel, counted from the data structures)
+# ------------------------------------------------------------------------------------------------
+def a_pass_bytes(n, nnz, sv=8, sx=8):
+    """One sweep over a sparse matrix: values + column indices + row pointers, read x, write y."""
+    return nnz * (sv + 4) + 4 * (n + 1) + 2 * n * sx
+
+
+def bytes_per_iteration(s, precond, sv=8, sx=8, sv_coarse=None):
+    sv_coarse = sv if sv_coarse is None else sv_coarse
+    nl = s.nlevels
+    info = [s.level_info(l) for l in range(nl)]
+
+    def vcycle():
+        b = 0
+        for l in range(nl - 1):
+            i = info[l]
+            svl = sv if l == 0 else sv_coarse
+            b += 3 * a_pass_bytes(i["n"], i["nnz"], svl, sx)          # pre sweep, residual, post sweep
+            b += 2 * a_pass_bytes(i["n"], i["nnzP"], 4 if sx == 4 else 8, sx)   # restriction, prolongation
+        c = info[nl - 1]["n"]
+        b += c * c * sx
+        return b
+
+    n, nnz = info[0]["n"], info[0]["nnz"]
+    ic = a_pass_bytes(n, nnz, sv, sx)                                   # L and U together touch A's pattern once
+    pcg = a_pass_bytes(n, nnz, 8, 8) + 12 * n * 8                       # q = A p plus the vector updates
+    if precond == "bco":
+        return pcg + 2 * vcycle() + a_pass_bytes(n, nnz, sv, sx) + ic
+    if precond == "amg":
+        return pcg + 2 * vcycle()
+    if precond == "ic0":
+        return pcg + ic
+    return pcg
+
+
+# ------------------------------------------------------------------------------------------------
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_1205_6113_gb300 import cpc
+
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    p = inputs.workload(WORKLOAD)
+    logk = torch.tensor(p.logk, device=dev)
+    rowptr, col, val = cpc.tpfa_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+    b = torch.tensor(p.rhs(), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush_l2():
+        flush.fill_(1.0)
+
+    def dist_barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def time_solves(solver, steps, warmup, tol=TOL):
+        iters = []
+        for _ in range(warmup):
+            _, it, st, _ = solver.solve(b, tol=tol, maxit=MAXIT, hist=False)
+            assert st == 0, "solve failed with status %d" % st
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        dist_barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush_l2()
+            ev[k][0].record(stream)
+            _, it, st, _ = solver.solve(b, tol=tol, maxit=MAXIT, hist=False)
+            ev[k][1].record(stream)
+            assert st == 0, "solve failed with status %d" % st
+            iters.append(it)
+        torch.cuda.synchronize()
+        dist_barrier()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(c) for a, c in ev]
+        return ms, iters, wall
+
+    out = {}
+    # headline arm: B_co, FP64
+    setups = {}
+    t = time.perf_counter()
+    s_bco = cpc.Solver(rowptr, col, val, precond="bco", precision="fp64")
+    setups["bco_fp64"] = dict(zip(("ic0_ms", "amg_ms"), s_bco.setup_time_ms()))
+    setups["bco_fp64"]["wall_ms"] = (time.perf_counter() - t) * 1e3
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms, iters, wall = time_solves(s_bco, args.steps, args.warmup)
+    clk = clocks.stop()
+    out["headline"] = dict(ms=ms, iters=iters, wall=wall)
+
+    # end-to-end through the C ABI with host buffers (pinned): H2D of b, D2H of x inside the timed region
+    b_host = torch.tensor(p.rhs()).pin_memory()
+    x_host = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):
+        s_bco.solve_host(b_host, x_host, tol=TOL, maxit=MAXIT)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush_l2()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, st = s_bco.solve_host(b_host, x_host, tol=TOL, maxit=MAXIT)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        assert st == 0
+    xh = x_host.numpy()
+    true_res = float(np.linalg.norm(p.rhs() - csr_matvec(rowptr, col, val, xh)) / np.linalg.norm(p.rhs()))
+
+    # comparison arms (fewer steps: AMG-alone and IC(0)-alone)
+    arms = {}
+    for name, pre, prec, k in [("amg_fp64", "amg", "fp64", args.steps), ("ic0_fp64", "ic0", "fp64", 2),
+                               ("bco_fp32", "bco", "fp32", args.steps), ("bco_fp32_bf16", "bco", "fp32_bf16", args.steps),
+                               ("amg_fp32", "amg", "fp32", args.steps)]:
+        if world > 1 and name != "bco_fp32":
+            continue
+        t = time.perf_counter()
+        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec)
+        setup = dict(zip(("ic0_ms", "amg_ms"), s.setup_time_ms()))
+        setup["wall_ms"] = (time.perf_counter() - t) * 1e3
+        m, it, _ = time_solves(s, k, 1 if name == "ic0_fp64" else args.warmup)
+        x, _, _, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
+        xr = x.cpu().numpy()
+        arms[name] = dict(ms=round(float(np.mean(m)), 3), iters=int(it[-1]), setup=setup,
+                          true_res=float(np.linalg.norm(p.rhs() - csr_matvec(rowptr, col, val, xr)) / np.linalg.norm(p.rhs())),
+                          hbm_frac_solve=None)
+        bpi = bytes_per_iteration(s, pre, sv=8 if prec == "fp64" else 4, sx=8 if prec == "fp64" else 4,
+                                  sv_coarse=(2 if prec == "fp32_bf16" else None))
+        arms[name]["gbs_solve"] = round(bpi * it[-1] / (np.mean(m) * 1e-3) / 1e9, 1)
+        s.close()
+
+    # dominant-kernel roofline: the fine SpMV (SELL-32, FP64), one launch per event pair, L2 flushed
+    xv = torch.randn(p.n, dtype=torch.float64, device=dev)
+    yv = torch.empty_like(xv)
+    for _ in range(3):
+        s_bco.spmv(xv, yv)
+    kms = []
+    for _ in range(20):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_bco.spmv(xv, yv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms.append(e0.elapsed_time(e1))
+    info0 = s_bco.level_info(0)
+    kbytes = a_pass_bytes(info0["n"], info0["nnz"])
+    peak, peak_kind = peaks()
+    k_avg = float(np.mean(kms))
+    achieved = kbytes / (k_avg * 1e-3) / 1e9
+    bpi = bytes_per_iteration(s_bco, "bco")
+    headline_ms = float(np.mean(ms))
+    out.update(dict(p=p, arms=arms, clocks=clk, e2e_ms=e2e_ms, true_res=true_res, setups=setups,
+                    roofline=dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
+                                  frac=round(achieved / peak, 4), traffic=None, kernel="k_spmv (fine A, SELL-32, FP64)",
+                                  bytes_per_launch=kbytes, avg_launch_ms=round(k_avg, 5), peak_kind=peak_kind),
+                    headline_ms=headline_ms, bytes_per_iter=bpi, nodes=None, nlevels=s_bco.nlevels,
+                    levels=[s_bco.level_info(l) for l in range(s_bco.nlevels)]))
+    out["solve_gbs"] = bpi * iters[-1] / (headline_ms * 1e-3) / 1e9
+    out["launches"] = s_bco.solve_launches()
+    return out
+
+
+def csr_matvec(rowptr, col, val, x):
+    rp = rowptr.cpu().numpy()
+    c = col.cpu().numpy()
+    v = val.cpu().numpy()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return np.bincount(rows, weights=v * x[c], minlength=len(rp) - 1)
+
+
+def oracle_time(p, sample_iters=None):
+    """The oracle (single thread, FP64) on the same matrix: setup once, then one B_co PCG solve."""
+    import oracle as O
+    A = O.tpfa_problem(p)
+    t = time.perf_counter()
+    orc = O.Oracle(A)
+    setup_s = time.perf_counter() - t
+    t = time.perf_counter()
+    r = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=sample_iters or MAXIT)
+    solve_s = time.perf_counter() - t
+    return orc, r, setup_s, solve_s
+
+
+def reference_arm(args, rank, world):
+    """CPU oracle timed on the host cores (the reference arm for this build)."""
+    import oracle as O
+    if rank != 0:
+        return
+    p = inputs.workload(WORKLOAD)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A)
+    sample = 4
+    times, full_iters = [], None
+    for k in range(args.warmup + args.steps):
+        maxit = MAXIT if k == 0 else sample
+        t = time.perf_counter()
+        r = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=maxit)
+        dt = time.perf_counter() - t
+        if k == 0:
+            full_iters = r["iters"]
+        elif k >= args.warmup:
+            times.append(dt / r["iters"])
+    per_it_ms = float(np.mean(times)) * 1e3
+    value = per_it_ms * full_iters
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(value, 2), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": p.n, "nnz": A.nnz, "precond": "B_co", "tol": TOL,
+                       "l2": "cpu"},
+            "cpu_baseline": {"value": round(value, 2), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": "each step: %d B_co PCG iterations of the oracle on the %s matrix, "
+                                       "scaled by its full iteration count (%d)" % (sample, WORKLOAD, full_iters)},
+            "e2e": {"value": round(value, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "native" else "gloo")
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    out = gpu_arm(args, rank, world)
+    ms_local = float(np.sum(out["headline"]["ms"]))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_local = float(t.item())
+    if rank != 0:
+        return
+    k = args.steps
+    ms_per_step = ms_local / k
+    value = ms_per_step / world          # whole job: world solves per step time
+    p = out["p"]
+    iters = out["headline"]["iters"][-1]
+    per_it, fixed = out["launches"]
+    launches = int(sum(fixed + it * per_it for it in out["headline"]["iters"]))
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world, "steps": k,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": p.n, "nnz": int(out["levels"][0]["nnz"]), "precond": "B_co",
+                   "precision": "fp64", "tol": TOL, "iters": iters, "levels": out["nlevels"],
+                   "l2": "flushed (512 MiB write) before every timed solve",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": round(float(np.mean(out["e2e_ms"])), 3), "unit": "ms",
+                "h2d_bytes_per_step": 8 * p.n, "d2h_bytes_per_step": 8 * p.n},
+        "roofline": out["roofline"],
+        "solve_hbm": {"bytes_per_iter": int(out["bytes_per_iter"]), "gbs": round(out["solve_gbs"], 1),
+                      "frac": round(out["solve_gbs"] / out["roofline"]["peak"], 4)},
+        "arms": out["arms"],
+        "setup_ms": out["setups"],
+        "true_res": out["true_res"],
+        "clocks": out["clocks"],
+        "gpu_launches": launches,
+        "launches_per_iteration": per_it,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        _, r, setup_s, solve_s = oracle_time(p)
+        line["cpu_baseline"] = {"value": round(solve_s * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                                "sample": "one full B_co PCG solve (%d iterations) of the %s matrix on one host "
+                                          "core, solve phase only (oracle setup %.1f s excluded)"
+                                          % (r["iters"], WORKLOAD, setup_s),
+                                "iters": r["iters"]}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * cpc.h -- C ABI of the GB300 combined-preconditioned CG library ("cpc").
+ *
+ * The library solves A u = f for a symmetric positive definite sparse A (Section 2, Eq.
+ * linear_system of Hu, Wu, Wu, Xu, Zhang, Zhang, Zikatanov, "Combined Preconditioning with
+ * Applications in Reservoir Simulation") by preconditioned conjugate gradients.  The default
+ * preconditioner is the combined preconditioner B_co of Algorithm 2.1 / Eq. barB,
+ *     I - B_co A = (I - S^T A)(I - B A)(I - S A),
+ * with S one algebraic-multigrid V-cycle (Algorithm 3.2, Gauss-Seidel smoothing on every level,
+ * Section 3.3) and B the IC(0) factorisation (Algorithm 3.1 with k = 0, Section 3.3).  Setup
+ * (IC(0) factorisation, AMG hierarchy) and solve both run on the GPU.
+ *
+ * Conventions for every entry point:
+ *  - Sizes are int32; matrices are CSR with int32 row pointers and column indices, rows sorted by
+ *    column, the diagonal present in every row, structurally symmetric.
+ *  - Vectors are float64 DEVICE pointers owned by the caller unless a name says _host.
+ *  - Work is issued on the stream given in cpc_options.stream (a cudaStream_t; NULL = legacy
+ *    default stream).  Entry points that return host-visible results (iteration counts,
+ *    residual histories, timings) synchronise that stream before returning; the others are
+ *    asynchronous and stream-ordered.
+ *  - Return codes (never abort, never trap):
+ *      CPC_OK 0, CPC_EINVAL 1 (bad argument or CSR), CPC_EFACTOR 2 (IC(0) pivot <= 0 or not
+ *      finite), CPC_ENOCONV 3 (maxit reached; x holds the last iterate), CPC_EBREAKDOWN 4 (CG
+ *      breakdown: p^T A p <= 0, r^T z <= 0 or NaN), CPC_ECUDA 5 (CUDA error), CPC_ETIMEOUT 6 (a
+ *      bounded device wait gave up), CPC_ESETUP 7 (AMG setup failure).
+ *    cpc_last_error() describes the last failure on a handle.
+ */
+#ifndef CPC_H
+#define CPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CPC_OK = 0, CPC_EINVAL = 1, CPC_EFACTOR = 2, CPC_ENOCONV = 3, CPC_EBREAKDOWN = 4,
+    CPC_ECUDA = 5, CPC_ETIMEOUT = 6, CPC_ESETUP = 7
+};
+
+/* Preconditioners (Section 5, Table 2 protocol). */
+enum {
+    CPC_PRECOND_BCO = 0,    /* B_co, Algorithm 2.1: S, then B, then S^T                         */
+    CPC_PRECOND_AMG = 1,    /* S~ = S + S^T - S^T A S: two V-cycles ("AMG(GS)", Section 5)       */
+    CPC_PRECOND_IC0 = 2,    /* B = IC(0) alone ("ILU(0)", Section 5)                             */
+    CPC_PRECOND_BHAT = 3,   /* additive B^ = S~ + B, Eq. Ba with W_1 = V, Pi_1 = I, A_1^{-1} = B  */
+    CPC_PRECOND_NONE = 4    /* identity (plain CG)                                               */
+};
+
+/* Precision of the preconditioner (the outer PCG is always FP64). */
+enum {
+    CPC_PREC_FP64 = 0,      /* everything FP64                                                   */
+    CPC_PREC_FP32 = 1,      /* V-cycles, IC(0) and the SpMVs inside B_co in FP32                 */
+    CPC_PREC_FP32_BF16 = 2  /* as FP32, with coarse-level operators stored in BF16               */
+};
+
+/* CSR matrix, caller-owned; cpc_setup copies what it needs. */
+typedef struct {
+    int32_t n;              /* rows = columns                                                    */
+    int32_t nnz;            /* = rowptr[n]                                                       */
+    const int32_t* rowptr;  /* [n + 1]                                                           */
+    const int32_t* colidx;  /* [nnz], ascending within each row                                  */
+    const double* vals;     /* [nnz]                                                             */
+    int32_t on_device;      /* 1: the three arrays are device pointers, 0: host pointers         */
+} cpc_csr;
+
+typedef struct {
+    int32_t precond;        /* CPC_PRECOND_*                                       (default BCO) */
+    int32_t precision;      /* CPC_PREC_*                                          (default FP64)*/
+    int32_t ic_order;       /* 0: natural order (level-scheduled); 1: multicolour order of the
+                               finest level's Gauss-Seidel colouring                (default 0)   */
+    double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
+    int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (256)         */
+    int32_t max_levels;     /* at most this many levels                            (20)          */
+    void* stream;           /* cudaStream_t used by every call on the handle       (NULL)        */
+} cpc_options;
+
+typedef struct cpc_handle cpc_handle;   /* opaque, library-owned */
+
+/* Fill *opt with the defaults listed above.  Returns CPC_OK, or CPC_EINVAL if opt is NULL. */
+int cpc_default_options(cpc_options* opt);
+
+/*
+ * Two-point-flux pressure matrix of the model problem -div(k grad p) = f (Section 4, Eq. model,
+ * with c = 0) on an nx x ny x nz grid of unit cells, cell (i,j,k) numbered i + nx (j + ny k).
+ * logk[n]: natural log of the cell permeability k (device); k_z = kz_ratio * k.  Face
+ * transmissibility 2 k_a k_b / (k_a + k_b); faces flagged in dirichlet_mask (bits x0, x1, y0, y1,
+ * z0, z1 = 1, 2, 4, 8, 16, 32) are held at p = 0 through the half-cell term 2 k (2 k_z).
+ * Outputs (device, caller-allocated): rowptr[n + 1], colidx[nnz], vals[nnz] with
+ * nnz = cpc_tpfa_nnz(nx, ny, nz); columns ascending.  Asynchronous on `stream`.
+ */
+int64_t cpc_tpfa_nnz(int32_t nx, int32_t ny, int32_t nz);
+int cpc_tpfa_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, double kz_ratio,
+                      int32_t dirichlet_mask, int32_t* rowptr, int32_t* colidx, double* vals,
+                      void* stream);
+
+/*
+ * Build the solver for A: IC(0) factorisation (Algorithm 3.1, k = 0) and the AMG hierarchy
+ * A_l = P_l^T A_{l+1} P_l (Section 3.2), both on the GPU.  On success *out owns all device
+ * memory it needs; release it with cpc_destroy.  On failure *out is NULL and the return code
+ * says why (CPC_EINVAL, CPC_EFACTOR, CPC_ESETUP, CPC_ECUDA).  Synchronous.
+ */
+int cpc_setup(const cpc_csr* A, const cpc_options* opt, cpc_handle** out);
+
+/* Release every resource of the handle (NULL is ignored). */
+void cpc_destroy(cpc_handle* h);
+
+/* Text of the last error on h (or of the last failed cpc_setup when h is NULL). */
+const char* cpc_last_error(const cpc_handle* h);
+
+/*
+ * PCG on A x = b with x_0 = 0 and the handle's preconditioner, stopping when
+ * ||b - A x_k||_2 / ||b||_2 < tol (recursive residual) or after maxit iterations.
+ * b[n], x[n]: device pointers (x is output only).  *iters = iterations taken;
+ * res_hist[k] = ||r_k|| / ||b|| for k = 0..*iters (at most hist_cap values written; res_hist
+ * may be NULL).  Runs the whole iteration loop on the device; synchronises the stream.
+ * Returns CPC_OK, CPC_ENOCONV, CPC_EBREAKDOWN, CPC_ECUDA or CPC_EINVAL.
+ */
+int cpc_solve(cpc_handle* h, const double* b, double* x, double tol, int32_t maxit,
+              int32_t* iters, double* res_hist, int32_t hist_cap);
+
+/* As cpc_solve, with b and x in HOST memory: the library copies b in and x out itself. */
+int cpc_solve_host(cpc_handle* h, const double* b_host, double* x_host, double tol,
+                   int32_t maxit, int32_t* iters, double* res_hist, int32_t hist_cap);
+
+/* z = M r for one application of a preconditioner (which = CPC_PRECOND_*; -1 = the handle's).
+ * r[n], z[n] device.  Asynchronous.  cpc_apply_Bcom is which = CPC_PRECOND_BCO. */
+int cpc_apply_precond(cpc_handle* h, int32_t which, const double* r, double* z);
+int cpc_apply_Bcom(cpc_handle* h, const double* r, double* z);
+
+/* y = A x with the fine matrix (FP64).  x[n], y[n] device.  Asynchronous. */
+int cpc_spmv(cpc_handle* h, const double* x, double* y);
+
+/* Setup timings in milliseconds (GPU events): IC(0) factorisation and AMG hierarchy. */
+int cpc_setup_time_ms(const cpc_handle* h, double* ms_ic0, double* ms_amg);
+
+/* ---- inspection (tests and diagnostics; all synchronous, outputs in HOST memory) ---------- */
+
+/* Kernel launches of one cpc_solve with the handle's preconditioner: *per_iteration nodes in the
+ * captured loop body (one PCG iteration) and *fixed launches outside the loop.  Builds the solve
+ * graph if it does not exist yet. */
+int cpc_solve_launches(cpc_handle* h, int64_t* per_iteration, int64_t* fixed);
+
+/* Number of AMG levels (finest = 0). */
+int cpc_num_levels(const cpc_handle* h);
+
+/* info[0..5] = n_l, nnz(A_l), number of smoothing colours, columns of P_l (= n_{l+1}),
+ * nnz(P_l), number of IC(0) levels (level 0 only, else 0). */
+int cpc_level_info(const cpc_handle* h, int32_t level, int64_t* info);
+
+/* Copy A_l (CSR, natural order) to host arrays sized from cpc_level_info. */
+int cpc_level_matrix(const cpc_handle* h, int32_t level, int32_t* rowptr, int32_t* colidx,
+                     double* vals);
+
+/* Copy P_l (n_l x n_{l+1} CSR) to host arrays. */
+int cpc_level_interp(const cpc_handle* h, int32_t level, int32_t* rowptr, int32_t* colidx,
+                     double* vals);
+
+/* Copy the C/F splitting (1 = C, 0 = F) and the smoothing colour of every row of level l. */
+int cpc_level_splitting(const cpc_handle* h, int32_t level, int32_t* cf, int32_t* colour);
+
+/* Copy the IC(0) factor values (L strictly below the diagonal, U on and above) laid out on the
+ * pattern of the fine A in the IC ordering (natural order: the input CSR pattern). */
+int cpc_ic0_values(const cpc_handle* h, double* lu);
+
+/* Level operators on device vectors, for parity tests: op 0 y = A_l x; 1 y = S_l x (forward
+ * Gauss-Seidel sweep, zero guess); 2 y = S_l^T x (backward sweep); 3 y = A_l^{-1} x (coarsest
+ * level); 4 y = V-cycle from level l with zero initial guess.  Asynchronous. */
+int cpc_level_apply(cpc_handle* h, int32_t level, int32_t op, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPC_H */

@@ -1,0 +1,117 @@
+// common.cuh -- internal types of the cpc library (device buffers, CSR, SELL-C, handle).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cpc.h"
+
+namespace cpc {
+
+// ---------------------------------------------------------------------------------------------
+// Errors: internal code throws cpc::Error; every C entry point catches it and returns the code.
+// ---------------------------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define CPC_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw ::cpc::Error{CPC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define CPC_LAUNCH_CK() CPC_CK(cudaGetLastError())
+
+inline void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+// ---------------------------------------------------------------------------------------------
+// Device buffer (owning, move-only).
+// ---------------------------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;          // keep a valid pointer for empty arrays
+        CPC_CK(cudaMalloc(&p, count * sizeof(T)));
+        n = count;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    T* get() const { return p; }
+};
+
+// Stream-ordered temporary (setup scratch): freed on the stream when it goes out of scope.
+template <class T>
+struct Tmp {
+    T* p = nullptr;
+    cudaStream_t s = nullptr;
+    Tmp(size_t count, cudaStream_t st) : s(st) {
+        if (count == 0) count = 1;
+        CPC_CK(cudaMallocAsync(&p, count * sizeof(T), s));
+    }
+    Tmp(const Tmp&) = delete;
+    Tmp& operator=(const Tmp&) = delete;
+    ~Tmp() { if (p) cudaFreeAsync(p, s); }
+    T* get() const { return p; }
+};
+
+// Device CSR with FP64 values; n rows, m columns, columns ascending within a row.
+struct Csr {
+    int n = 0, m = 0;
+    int64_t nnz = 0;
+    DBuf<int> ptr, col;
+    DBuf<double> val;
+};
+
+// Value storage types of the preconditioner data.
+enum VType { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2 };
+
+// SELL-C (C = 32) storage of a set of matrix rows in a chosen slot order.
+//   slot s holds row perm[s] (or -1 for padding); chunk k = slots [32k, 32k+32) is processed by
+//   one warp, one row per lane; its entries live in val/col[cptr[k] + w*32 + lane], w < width.
+//   With split_diag the diagonal is kept apart in diag[s] and val/col hold off-diagonals only.
+//   Padding entries have val 0 and col = -1; kernels skip them (no load is issued).
+//   seg[] (host) gives chunk ranges: segment g is chunks [seg[g], seg[g+1]) -- a colour of a
+//   Gauss-Seidel sweep or a level of a triangular solve.
+struct Sell {
+    int nslots = 0, nchunks = 0;
+    int64_t nelem = 0;
+    DBuf<int> perm, cptr, col;
+    DBuf<double> val, diag;            // FP64 copy (always)
+    DBuf<float> val32, diag32;         // FP32 copy (mixed precision)
+    DBuf<__nv_bfloat16> val16;         // BF16 copy of off-diagonals (coarse levels, mode 2)
+    std::vector<int> seg;
+};
+
+// Kernel-side view of a SELL matrix in value type MT.
+template <class MT>
+struct SellView {
+    const int* perm;
+    const int* cptr;
+    const int* col;
+    const MT* val;
+    const MT* diag;
+};
+
+}  // namespace cpc

@@ -1,0 +1,87 @@
+// handle.cuh -- the solver handle: hierarchy, IC(0) factor, work vectors, captured graphs.
+#pragma once
+
+#include "common.cuh"
+
+namespace cpc {
+
+constexpr int CHUNK = 32;            // SELL chunk height = warp width
+constexpr int DENSE_MAX = 4096;      // largest coarsest level solved by the dense inverse
+constexpr int HIST_CAP = 100001;     // residual-history capacity on the device
+constexpr int NPART = 1024;          // partial-sum slots for deterministic reductions
+constexpr int NPRECOND = 5;          // CPC_PRECOND_* values
+
+// One AMG level (0 = finest).
+struct Level {
+    int n = 0;
+    int64_t nnz = 0;
+    Csr A;                  // A_l, natural order, FP64
+    Csr P, R;               // interpolation to this level from level l+1, and R = P^T
+    DBuf<int> cf, colour;   // C/F splitting, smoothing colour (natural order)
+    int ncolours = 0;
+    Sell S;                 // rows grouped by colour, diagonal split: Gauss-Seidel and residual
+    Sell SP, SR;            // P and R, natural row order
+    VType vt = VT_F64;      // storage type of this level's operators in the preconditioner
+    DBuf<double> x64, f64, r64;
+    DBuf<float> x32, f32, r32;
+};
+
+// Device-side scalars of one PCG run (all reductions finish in fixed order).
+struct PcgState {
+    double bnorm, rz, rz_old, pq, alpha, beta, rr, tol, res;
+    int k, maxit, status, pad;
+};
+
+struct Handle {
+    cpc_options opt{};
+    cudaStream_t s = nullptr;
+    int n = 0;
+    int64_t nnz = 0;
+    std::vector<Level> lev;
+    Sell Anat;              // fine A in natural row order, diagonal split (SpMVs of PCG and B_co)
+    // IC(0) (Algorithm 3.1, k = 0) of the fine A in the IC ordering
+    Csr Aic;                // A in the IC ordering (same as lev[0].A for natural order)
+    DBuf<double> lu;        // factor values on the pattern of Aic
+    DBuf<int> lu_diag;      // position of the diagonal in each row of Aic
+    DBuf<int> ic_order;     // ic row q <- original row ic_order[q] (empty: natural)
+    int ic_levels_L = 0, ic_levels_U = 0;
+    Sell L, U;              // strictly-lower rows by forward level; upper rows by backward level
+    // coarsest level: dense inverse
+    int nc = 0;
+    DBuf<double> Ainv;
+    DBuf<float> Ainv32;
+    // fine-level vectors
+    DBuf<double> b, x, r, z, p, q, t, y;
+    DBuf<float> z32, t32, y32;
+    DBuf<double> bt, yt;    // IC-ordered copies when the IC ordering is not natural
+    DBuf<float> bt32, yt32;
+    // reductions and PCG state
+    DBuf<double> partial;
+    DBuf<unsigned> counter;
+    DBuf<PcgState> state;
+    DBuf<double> hist;
+    DBuf<int> flags;        // [0] IC factor failure row + 1, [1] coarse Cholesky failure
+    cudaGraph_t graph[NPRECOND] = {};
+    cudaGraphExec_t gexec[NPRECOND] = {};
+    int64_t body_nodes[NPRECOND] = {};
+    float ms_ic0 = 0.f, ms_amg = 0.f;
+    std::string err;
+    ~Handle();
+};
+
+// setup.cu
+void tpfa_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask, int* rowptr,
+                   int* col, double* val, cudaStream_t s);
+void setup_handle(Handle& h, const cpc_csr& A);
+
+// solve.cu
+void record_precond(Handle& h, int which, const double* r, void* z, cudaStream_t s);
+void apply_precond(Handle& h, int which, const double* r, double* z);
+void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s);
+void solve_pcg(Handle& h, const double* b, double* x, double tol, int maxit, int* iters,
+               double* res_hist, int hist_cap, int* status);
+void level_apply(Handle& h, int l, int op, const double* x, double* y);
+void destroy_graphs(Handle& h);
+void ensure_solve_graph(Handle& h, int which);
+
+}  // namespace cpc

@@ -1,0 +1,1111 @@
+// setup.cu -- GPU setup: TPFA assembly, IC(0) factorisation, AMG hierarchy, SELL-C layouts.
+//
+// Everything here runs on the device; the host only sequences launches and reads back a few
+// counters (round loops of PMIS, colouring and level scheduling).  The rules are those of
+// Section 3 of the paper with the readings listed in the library docs:
+//   IC(0)   Algorithm 3.1 with k = 0 in IKJ form, rows factored level by level of the lower DAG;
+//   AMG     strength theta, PMIS splitting with weight (|S^T_i|, fmix32(i)), direct
+//           interpolation, R = P^T, Galerkin A_c = R (A P) (Section 3.2);
+//   colour  Jones-Plassmann with weight fmix32(i ^ 0x5bd1e995), smallest free colour.
+// Sums that define matrix entries are accumulated in a fixed order (the order the products are
+// generated in), so results do not depend on thread scheduling.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "handle.cuh"
+
+namespace cpc {
+
+namespace {
+
+constexpr uint32_t COLOUR_SEED = 0x5bd1e995u;
+constexpr int TPB = 256;
+
+// Published MurmurHash3 32-bit finaliser (a bijection): tie-break weights.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16; h *= 0x85ebca6bu; h ^= h >> 13; h *= 0xc2b2ae35u; h ^= h >> 16;
+    return h;
+}
+
+inline int nblk(int64_t n, int t = TPB) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
+
+template <class T>
+T d2h(const T* p, cudaStream_t s) {
+    T v;
+    CPC_CK(cudaMemcpyAsync(&v, p, sizeof(T), cudaMemcpyDeviceToHost, s));
+    CPC_CK(cudaStreamSynchronize(s));
+    return v;
+}
+
+template <class T>
+void h2d(T* dst, const T* src, size_t n, cudaStream_t s) {
+    CPC_CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+// out[0..n) = exclusive prefix sum of in[0..n)
+template <class T>
+void exclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s) {
+    size_t tmp = 0;
+    CPC_CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, n, s));
+    Tmp<char> t(tmp, s);
+    CPC_CK(cub::DeviceScan::ExclusiveSum(t.get(), tmp, in, out, n, s));
+}
+
+template <class T>
+void inclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s) {
+    size_t tmp = 0;
+    CPC_CK(cub::DeviceScan::InclusiveSum(nullptr, tmp, in, out, n, s));
+    Tmp<char> t(tmp, s);
+    CPC_CK(cub::DeviceScan::InclusiveSum(t.get(), tmp, in, out, n, s));
+}
+
+// Stable radix sort of (key, value) pairs over the low `bits` bits of the key.
+template <class K, class V>
+void sort_pairs(const K* kin, K* kout, const V* vin, V* vout, int64_t n, int bits, cudaStream_t s) {
+    size_t tmp = 0;
+    CPC_CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp, kin, kout, vin, vout, n, 0, bits, s));
+    Tmp<char> t(tmp, s);
+    CPC_CK(cub::DeviceRadixSort::SortPairs(t.get(), tmp, kin, kout, vin, vout, n, 0, bits, s));
+}
+
+int bits_for(uint64_t maxval) {
+    int b = 1;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+__global__ void k_iota(int* a, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+
+__global__ void k_fill_int(int* a, int64_t n, int v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+// ============================================================================================
+// a0: two-point-flux assembly (Section 4, Eq. model with c = 0), unit cells.
+// Entry order per row: z-, y-, x-, diagonal, x+, y+, z+.  Diagonal = neighbour
+// transmissibilities in that order, then Dirichlet half-cell terms in face order x0..z1.
+// ============================================================================================
+__device__ __forceinline__ double harmonic(double a, double b) { return (2.0 * a * b) / (a + b); }
+
+__global__ void k_tpfa_rowlen(int nx, int ny, int nz, int* len) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = nx * ny * nz;
+    if (c >= n) return;
+    int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+    len[c] = 1 + (i > 0) + (i < nx - 1) + (j > 0) + (j < ny - 1) + (k > 0) + (k < nz - 1);
+}
+
+__global__ void k_tpfa_fill(int nx, int ny, int nz, const double* logk, double kzr, int dmask,
+                            const int* rowptr, int* col, double* val) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = nx * ny * nz;
+    if (c >= n) return;
+    int i = c % nx, j = (c / nx) % ny, kk = c / (nx * ny);
+    const int sxy = nx * ny;
+    const double kc = exp(logk[c]);
+    const double kzc = kzr * kc;
+    int nb[6];
+    double t[6];
+    int cnt = 0;
+    if (kk > 0)      { nb[cnt] = c - sxy; t[cnt++] = harmonic(kzc, kzr * exp(logk[c - sxy])); }
+    if (j > 0)       { nb[cnt] = c - nx;  t[cnt++] = harmonic(kc, exp(logk[c - nx])); }
+    if (i > 0)       { nb[cnt] = c - 1;   t[cnt++] = harmonic(kc, exp(logk[c - 1])); }
+    const int nlow = cnt;
+    if (i < nx - 1)  { nb[cnt] = c + 1;   t[cnt++] = harmonic(kc, exp(logk[c + 1])); }
+    if (j < ny - 1)  { nb[cnt] = c + nx;  t[cnt++] = harmonic(kc, exp(logk[c + nx])); }
+    if (kk < nz - 1) { nb[cnt] = c + sxy; t[cnt++] = harmonic(kzc, kzr * exp(logk[c + sxy])); }
+    double d = 0.0;
+    for (int q = 0; q < cnt; ++q) d += t[q];
+    if ((dmask & 1) && i == 0)        d += 2.0 * kc;
+    if ((dmask & 2) && i == nx - 1)   d += 2.0 * kc;
+    if ((dmask & 4) && j == 0)        d += 2.0 * kc;
+    if ((dmask & 8) && j == ny - 1)   d += 2.0 * kc;
+    if ((dmask & 16) && kk == 0)      d += 2.0 * kzc;
+    if ((dmask & 32) && kk == nz - 1) d += 2.0 * kzc;
+    int p = rowptr[c];
+    for (int q = 0; q < nlow; ++q) { col[p] = nb[q]; val[p] = -t[q]; ++p; }
+    col[p] = c; val[p] = d; ++p;
+    for (int q = nlow; q < cnt; ++q) { col[p] = nb[q]; val[p] = -t[q]; ++p; }
+}
+
+// ============================================================================================
+// CSR validation and helpers
+// ============================================================================================
+// flags: [0] bad row pointer, [1] bad column / order, [2] missing diagonal
+__global__ void k_validate(int n, const int* ptr, const int* col, int nnz, int* bad, int* diag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = ptr[i], b = ptr[i + 1];
+    if (a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (i == n - 1 && b != nnz)) {
+        atomicOr(bad, 1);
+        diag[i] = -1;
+        return;
+    }
+    int d = -1;
+    for (int p = a; p < b; ++p) {
+        int j = col[p];
+        if (j < 0 || j >= n || (p > a && j <= col[p - 1])) { atomicOr(bad, 2); diag[i] = -1; return; }
+        if (j == i) d = p;
+    }
+    if (d < 0) atomicOr(bad, 4);
+    diag[i] = d;
+}
+
+// Row index of every entry.
+__global__ void k_entry_rows(int n, const int* ptr, int* rows) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) rows[p] = i;
+}
+
+// tpos[p] = position of (j, i) for entry p = (i, j); flags structural asymmetry.
+__global__ void k_transpose_pos(int n, const int* ptr, const int* col, int* tpos, int* bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        int j = col[p];
+        int lo = ptr[j], hi = ptr[j + 1] - 1, found = -1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int c = col[mid];
+            if (c == i) { found = mid; break; }
+            if (c < i) lo = mid + 1; else hi = mid - 1;
+        }
+        tpos[p] = found;
+        if (found < 0) atomicOr(bad, 8);
+    }
+}
+
+// ============================================================================================
+// Transpose and sparse products (ESC: expand, stable sort, sum each key in generation order)
+// ============================================================================================
+__global__ void k_col_count(int64_t nnz, const int* col, int* cnt) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) atomicAdd(&cnt[col[p]], 1);
+}
+
+__global__ void k_gather_transpose(int64_t nnz, const int* idx, const int* rows, const double* val,
+                                   int* tcol, double* tval) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    int p = idx[k];
+    tcol[k] = rows[p];
+    tval[k] = val[p];
+}
+
+void transpose(const Csr& A, Csr& T, cudaStream_t s) {
+    T.n = A.m; T.m = A.n; T.nnz = A.nnz;
+    T.ptr.alloc(T.n + 1);
+    T.col.alloc(A.nnz);
+    T.val.alloc(A.nnz);
+    Tmp<int> rows(A.nnz, s), idx(A.nnz, s), sk(A.nnz, s), sv(A.nnz, s), cnt(T.n + 1, s);
+    k_entry_rows<<<nblk(A.n), TPB, 0, s>>>(A.n, A.ptr.p, rows.get());
+    k_iota<<<nblk(A.nnz), TPB, 0, s>>>(idx.get(), (int)A.nnz);
+    sort_pairs(A.col.p, sk.get(), idx.get(), sv.get(), A.nnz, bits_for((uint64_t)std::max(1, A.m)), s);
+    CPC_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int) * (T.n + 1), s));
+    k_col_count<<<nblk(A.nnz), TPB, 0, s>>>(A.nnz, A.col.p, cnt.get());
+    exclusive_scan(cnt.get(), T.ptr.p, T.n + 1, s);
+    k_gather_transpose<<<nblk(A.nnz), TPB, 0, s>>>(A.nnz, sv.get(), rows.get(), A.val.p, T.col.p, T.val.p);
+    CPC_LAUNCH_CK();
+}
+
+__global__ void k_prod_count(int n, const int* aptr, const int* acol, const int* bptr, int64_t* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    if (i == n) { cnt[n] = 0; return; }
+    int64_t c = 0;
+    for (int p = aptr[i]; p < aptr[i + 1]; ++p) { int k = acol[p]; c += bptr[k + 1] - bptr[k]; }
+    cnt[i] = c;
+}
+
+__global__ void k_prod_expand(int n, const int* aptr, const int* acol, const double* aval,
+                              const int* bptr, const int* bcol, const double* bval, int64_t m,
+                              const int64_t* off, uint64_t* key, double* val) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = off[i];
+    for (int p = aptr[i]; p < aptr[i + 1]; ++p) {
+        const int k = acol[p];
+        const double a = aval[p];
+        for (int q = bptr[k]; q < bptr[k + 1]; ++q) {
+            key[o] = (uint64_t)i * (uint64_t)m + (uint64_t)bcol[q];
+            val[o] = a * bval[q];
+            ++o;
+        }
+    }
+}
+
+__global__ void k_seg_head(int64_t N, const uint64_t* key, int* head) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) head[t] = (t == 0 || key[t] != key[t - 1]) ? 1 : 0;
+}
+
+__global__ void k_seg_start(int64_t N, const int* head, const int* segid, int64_t* start) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N && head[t]) start[segid[t] - 1] = t;
+}
+
+__global__ void k_seg_sum(int nseg, int64_t N, const int64_t* start, const uint64_t* key, const double* val,
+                          int64_t m, int* ccol, double* cval, int* rowcnt) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    const int64_t a = start[g];
+    const int64_t b = (g + 1 < nseg) ? start[g + 1] : N;
+    double s = val[a];
+    for (int64_t t = a + 1; t < b; ++t) s += val[t];
+    const uint64_t kk = key[a];
+    ccol[g] = (int)(kk % (uint64_t)m);
+    cval[g] = s;
+    atomicAdd(&rowcnt[(int)(kk / (uint64_t)m)], 1);
+}
+
+// C = A * B; every entry sums its products in generation order (row of A ascending, then row of B).
+void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+    const int n = A.n;
+    C.n = n; C.m = B.m;
+    Tmp<int64_t> cnt(n + 1, s), off(n + 1, s);
+    k_prod_count<<<nblk(n + 1), TPB, 0, s>>>(n, A.ptr.p, A.col.p, B.ptr.p, cnt.get());
+    exclusive_scan(cnt.get(), off.get(), n + 1, s);
+    const int64_t N = d2h(off.get() + n, s);
+    C.ptr.alloc(n + 1);
+    if (N == 0) {
+        CPC_CK(cudaMemsetAsync(C.ptr.p, 0, sizeof(int) * (n + 1), s));
+        C.nnz = 0; C.col.alloc(1); C.val.alloc(1);
+        return;
+    }
+    if (N > (int64_t)INT_MAX) fail(CPC_ESETUP, "sparse product too large");
+    Tmp<uint64_t> key(N, s), key2(N, s);
+    Tmp<double> val(N, s), val2(N, s);
+    k_prod_expand<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, A.col.p, A.val.p, B.ptr.p, B.col.p, B.val.p,
+                                          (int64_t)B.m, off.get(), key.get(), val.get());
+    CPC_LAUNCH_CK();
+    sort_pairs(key.get(), key2.get(), val.get(), val2.get(), N,
+               bits_for((uint64_t)n * (uint64_t)B.m), s);
+    Tmp<int> head(N, s), segid(N, s);
+    k_seg_head<<<nblk(N), TPB, 0, s>>>(N, key2.get(), head.get());
+    inclusive_scan(head.get(), segid.get(), N, s);
+    const int nseg = d2h(segid.get() + N - 1, s);
+    Tmp<int64_t> start(nseg, s);
+    Tmp<int> rowcnt(n + 1, s);
+    CPC_CK(cudaMemsetAsync(rowcnt.get(), 0, sizeof(int) * (n + 1), s));
+    k_seg_start<<<nblk(N), TPB, 0, s>>>(N, head.get(), segid.get(), start.get());
+    C.nnz = nseg;
+    C.col.alloc(nseg);
+    C.val.alloc(nseg);
+    k_seg_sum<<<nblk(nseg), TPB, 0, s>>>(nseg, N, start.get(), key2.get(), val2.get(), (int64_t)B.m,
+                                         C.col.p, C.val.p, rowcnt.get());
+    exclusive_scan(rowcnt.get(), C.ptr.p, n + 1, s);
+    CPC_LAUNCH_CK();
+}
+
+// ============================================================================================
+// AMG: strength, PMIS, direct interpolation (Section 3.2 with the stated readings)
+// ============================================================================================
+__global__ void k_strength(int n, const int* ptr, const int* col, const double* val, double theta,
+                           uint8_t* strong) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double mx = 0.0;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p)
+        if (col[p] != i) mx = fmax(mx, -val[p]);
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p)
+        strong[p] = (col[p] != i && mx > 0.0 && -val[p] >= theta * mx) ? 1 : 0;
+}
+
+// |S^T_i| = number of rows j with i in S_j
+__global__ void k_st_count(int n, const int* ptr, const int* tpos, const uint8_t* strong, int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) c += strong[tpos[p]];
+    cnt[i] = c;
+}
+
+enum : int8_t { ST_UNDEC = -1, ST_F = 0, ST_C = 1 };
+
+__device__ __forceinline__ bool heavier(const int* cnt, int a, int b) {
+    if (cnt[a] != cnt[b]) return cnt[a] > cnt[b];
+    return fmix32((uint32_t)a) > fmix32((uint32_t)b);
+}
+
+__global__ void k_pmis_init(int n, const int* cnt, int8_t* st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) st[i] = cnt[i] == 0 ? ST_F : ST_UNDEC;
+}
+
+__global__ void k_pmis_select(int n, const int* ptr, const int* col, const int* tpos, const uint8_t* strong,
+                              const int* cnt, const int8_t* st, uint8_t* sel) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint8_t best = 0;
+    if (st[i] == ST_UNDEC) {
+        best = 1;
+        for (int p = ptr[i]; p < ptr[i + 1] && best; ++p) {
+            const int j = col[p];
+            if (j == i) continue;
+            if ((strong[p] || strong[tpos[p]]) && st[j] == ST_UNDEC && heavier(cnt, j, i)) best = 0;
+        }
+    }
+    sel[i] = best;
+}
+
+__global__ void k_pmis_setc(int n, const uint8_t* sel, int8_t* st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && sel[i]) st[i] = ST_C;
+}
+
+__global__ void k_pmis_setf(int n, const int* ptr, const int* col, const uint8_t* strong, int8_t* st, int* undec) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || st[i] != ST_UNDEC) return;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p)
+        if (strong[p] && st[col[p]] == ST_C) { st[i] = ST_F; return; }
+    atomicAdd(undec, 1);
+}
+
+__global__ void k_cf_flags(int n, const int8_t* st, int* cf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cf[i] = st[i] == ST_C ? 1 : 0;
+}
+
+__global__ void k_interp_count(int n, const int* ptr, const int* col, const uint8_t* strong, const int* cf,
+                               int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    if (i == n) { cnt[n] = 0; return; }
+    if (cf[i]) { cnt[i] = 1; return; }
+    int c = 0;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) c += (strong[p] && cf[col[p]]) ? 1 : 0;
+    cnt[i] = c;
+}
+
+// Direct interpolation:
+//   P_ij = -(sum_{k!=i} min(a_ik,0) / sum_{j in C_i} a_ij) a_ij / (a_ii + sum_{k!=i} max(a_ik,0))
+__global__ void k_interp_fill(int n, const int* ptr, const int* col, const double* val, const uint8_t* strong,
+                              const int* cf, const int* cidx, const int* pptr, int* pcol, double* pval) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = pptr[i];
+    if (cf[i]) { pcol[o] = cidx[i]; pval[o] = 1.0; return; }
+    double sum_neg = 0.0, sum_pos = 0.0, c_neg = 0.0, aii = 0.0;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int j = col[p];
+        const double a = val[p];
+        if (j == i) { aii = a; continue; }
+        if (a < 0.0) sum_neg += a; else sum_pos += a;
+        if (strong[p] && cf[j]) c_neg += a;
+    }
+    if (c_neg == 0.0) return;
+    const double alpha = sum_neg / c_neg;
+    const double d = aii + sum_pos;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int j = col[p];
+        if (j != i && strong[p] && cf[j]) { pcol[o] = cidx[j]; pval[o] = -alpha * val[p] / d; ++o; }
+    }
+}
+
+// ============================================================================================
+// Jones-Plassmann colouring
+// ============================================================================================
+__global__ void k_jp_select(int n, const int* ptr, const int* col, const int* colour, uint8_t* sel) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint8_t best = 0;
+    if (colour[i] < 0) {
+        best = 1;
+        const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
+        for (int p = ptr[i]; p < ptr[i + 1] && best; ++p) {
+            const int j = col[p];
+            if (j != i && colour[j] < 0 && fmix32((uint32_t)j ^ COLOUR_SEED) > hi) best = 0;
+        }
+    }
+    sel[i] = best;
+}
+
+__global__ void k_jp_assign(int n, const int* ptr, const int* col, const uint8_t* sel, int* colour, int* done) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !sel[i]) return;
+    for (int base = 0;; base += 64) {
+        unsigned long long used = 0ull;
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+            const int c = colour[col[p]];
+            if (col[p] != i && c >= base && c < base + 64) used |= 1ull << (c - base);
+        }
+        if (used != ~0ull) {
+            colour[i] = base + __ffsll((long long)~used) - 1;
+            break;
+        }
+    }
+    atomicAdd(done, 1);
+}
+
+// ============================================================================================
+// IC(0): level scheduling and factorisation (Algorithm 3.1, k = 0)
+// ============================================================================================
+// One round: rows whose dependencies (lower: j < i, upper: j > i) all have levels < round get
+// level = round.
+__global__ void k_dag_round(int n, const int* ptr, const int* col, int* lvl, int round, int upper, int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || lvl[i] >= 0) return;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int j = col[p];
+        if (upper ? j > i : j < i) {
+            const int lj = lvl[j];
+            if (lj < 0 || lj >= round) return;
+        }
+    }
+    lvl[i] = round;
+    atomicAdd(cnt, 1);
+}
+
+// IKJ elimination of the rows of one level: for m < i in the row (ascending), l_im = a_im / u_mm,
+// then a_ij -= l_im u_mj for j > m in both rows.  Products and differences are rounded
+// separately (no fused multiply-add), in the same order as the plain sequential algorithm.
+__global__ void k_ic0_level(const int* rows, int cnt, const int* ptr, const int* col, const int* diag,
+                            double* lu, int* fail) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int i = rows[t];
+    const int di = diag[i];
+    const int end_i = ptr[i + 1];
+    for (int p = ptr[i]; p < di; ++p) {
+        const int m = col[p];
+        const double l = lu[p] / lu[diag[m]];
+        lu[p] = l;
+        int pi = p + 1;
+        for (int q = diag[m] + 1; q < ptr[m + 1]; ++q) {
+            const int j = col[q];
+            while (pi < end_i && col[pi] < j) ++pi;
+            if (pi >= end_i) break;
+            if (col[pi] == j) lu[pi] = __dsub_rn(lu[pi], __dmul_rn(l, lu[q]));
+        }
+    }
+    const double u = lu[di];
+    if (!(u > 0.0) || !isfinite(u)) atomicMin(fail, i);
+}
+
+// Symmetric permutation B = Q^T A Q: new row q is old row order[q], columns renumbered by inv.
+__global__ void k_perm_rowlen(int n, const int* ptr, const int* order, int* len) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > n) return;
+    if (q == n) { len[n] = 0; return; }
+    const int i = order[q];
+    len[q] = ptr[i + 1] - ptr[i];
+}
+
+__global__ void k_perm_fill(int n, const int* ptr, const int* col, const double* val, const int* order,
+                            const int* inv, const int* bptr, int* bcol, double* bval) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int i = order[q];
+    const int o = bptr[q];
+    const int len = ptr[i + 1] - ptr[i];
+    for (int e = 0; e < len; ++e) {            // insertion sort by new column
+        const int c = inv[col[ptr[i] + e]];
+        const double v = val[ptr[i] + e];
+        int w = e;
+        while (w > 0 && bcol[o + w - 1] > c) { bcol[o + w] = bcol[o + w - 1]; bval[o + w] = bval[o + w - 1]; --w; }
+        bcol[o + w] = c;
+        bval[o + w] = v;
+    }
+}
+
+__global__ void k_inverse_perm(int n, const int* order, int* inv) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) inv[order[q]] = q;
+}
+
+// ============================================================================================
+// SELL-C construction
+// ============================================================================================
+enum SellMode { SELL_OFFDIAG = 0, SELL_LOWER = 1, SELL_UPPER = 2, SELL_ALL = 3 };
+
+__device__ __forceinline__ bool sell_keep(int mode, int j, int i) {
+    switch (mode) {
+        case SELL_OFFDIAG: return j != i;
+        case SELL_LOWER: return j < i;
+        case SELL_UPPER: return j > i;
+        default: return true;
+    }
+}
+
+__global__ void k_sell_width(const int* perm, int nchunks, const int* ptr, const int* col, int mode, int* width) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nchunks) return;
+    if (k == nchunks) { width[k] = 0; return; }
+    int w = 0;
+    for (int l = 0; l < CHUNK; ++l) {
+        const int i = perm[k * CHUNK + l];
+        if (i < 0) continue;
+        int c = 0;
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) c += sell_keep(mode, col[p], i) ? 1 : 0;
+        w = max(w, c);
+    }
+    width[k] = w * CHUNK;
+}
+
+// Slots refer to rows of the CSR; imap (optional) renames rows and columns on output
+// (IC factor stored in its own ordering but applied to naturally ordered vectors).
+__global__ void k_sell_fill(const int* perm, int nslots, const int* ptr, const int* col, const double* val,
+                            int mode, const int* cptr, const int* imap, int* perm_out, int* scol, double* sval,
+                            double* sdiag) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    const int k = s / CHUNK, lane = s % CHUNK;
+    const int base = cptr[k];
+    const int w = (cptr[k + 1] - base) / CHUNK;
+    const int i = perm[s];
+    const int out_row = i < 0 ? -1 : (imap ? imap[i] : i);
+    perm_out[s] = out_row;
+    int e = 0;
+    double d = 1.0;
+    if (i >= 0) {
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+            const int j = col[p];
+            if (j == i) d = val[p];
+            if (sell_keep(mode, j, i)) {
+                scol[base + e * CHUNK + lane] = imap ? imap[j] : j;
+                sval[base + e * CHUNK + lane] = val[p];
+                ++e;
+            }
+        }
+    }
+    for (; e < w; ++e) {                       // padding: column -1, skipped by every kernel
+        scol[base + e * CHUNK + lane] = -1;
+        sval[base + e * CHUNK + lane] = 0.0;
+    }
+    if (sdiag) sdiag[s] = d;
+}
+
+// Slot order from a per-row group key (colour or level): rows sorted by (key, row), each group
+// padded to a multiple of CHUNK.  Returns the chunk boundaries of the groups in seg.
+__global__ void k_group_count(int n, const int* key, int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[key[i]], 1);
+}
+
+__global__ void k_group_scatter(int n, const int* skey, const int* srow, const int* gstart, const int* sstart,
+                                int* perm) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int g = skey[t];
+    perm[sstart[g] + (t - gstart[g])] = srow[t];
+}
+
+// Build perm (device, nslots) from a group key per row; ngroups known.
+void grouped_slots(int n, const int* key, int ngroups, cudaStream_t s, DBuf<int>& perm, int& nslots,
+                   std::vector<int>& seg, DBuf<int>* sorted_rows = nullptr) {
+    Tmp<int> rows(n, s), skey(n, s), srow(n, s), cnt(ngroups, s);
+    k_iota<<<nblk(n), TPB, 0, s>>>(rows.get(), n);
+    sort_pairs(key, skey.get(), rows.get(), srow.get(), n, bits_for((uint64_t)std::max(1, ngroups)), s);
+    CPC_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int) * ngroups, s));
+    k_group_count<<<nblk(n), TPB, 0, s>>>(n, key, cnt.get());
+    std::vector<int> hc(ngroups);
+    CPC_CK(cudaMemcpyAsync(hc.data(), cnt.get(), sizeof(int) * ngroups, cudaMemcpyDeviceToHost, s));
+    CPC_CK(cudaStreamSynchronize(s));
+    std::vector<int> gstart(ngroups), sstart(ngroups);
+    seg.assign(ngroups + 1, 0);
+    int g0 = 0, s0 = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        gstart[g] = g0;
+        sstart[g] = s0;
+        seg[g] = s0 / CHUNK;
+        g0 += hc[g];
+        s0 += (hc[g] + CHUNK - 1) / CHUNK * CHUNK;
+    }
+    seg[ngroups] = s0 / CHUNK;
+    nslots = s0;
+    perm.alloc(nslots);
+    k_fill_int<<<nblk(nslots), TPB, 0, s>>>(perm.p, nslots, -1);
+    Tmp<int> dg(ngroups, s), ds(ngroups, s);
+    h2d(dg.get(), gstart.data(), ngroups, s);
+    h2d(ds.get(), sstart.data(), ngroups, s);
+    k_group_scatter<<<nblk(n), TPB, 0, s>>>(n, skey.get(), srow.get(), dg.get(), ds.get(), perm.p);
+    if (sorted_rows) {
+        sorted_rows->alloc(n);
+        CPC_CK(cudaMemcpyAsync(sorted_rows->p, srow.get(), sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    CPC_CK(cudaStreamSynchronize(s));      // host vectors above go out of scope
+    CPC_LAUNCH_CK();
+}
+
+void natural_slots(int n, cudaStream_t s, DBuf<int>& perm, int& nslots, std::vector<int>& seg) {
+    nslots = (n + CHUNK - 1) / CHUNK * CHUNK;
+    perm.alloc(nslots);
+    k_fill_int<<<nblk(nslots), TPB, 0, s>>>(perm.p, nslots, -1);
+    k_iota<<<nblk(n), TPB, 0, s>>>(perm.p, n);
+    seg = {0, nslots / CHUNK};
+    CPC_LAUNCH_CK();
+}
+
+// Fill a Sell from CSR rows in the slot order `slots` (device, nslots entries).
+void build_sell(const int* ptr, const int* col, const double* val, const DBuf<int>& slots, int nslots,
+                const std::vector<int>& seg, int mode, bool split_diag, const int* imap, Sell& S,
+                cudaStream_t s) {
+    S.nslots = nslots;
+    S.nchunks = nslots / CHUNK;
+    S.seg = seg;
+    Tmp<int> width(S.nchunks + 1, s);
+    k_sell_width<<<nblk(S.nchunks + 1), TPB, 0, s>>>(slots.p, S.nchunks, ptr, col, mode, width.get());
+    S.cptr.alloc(S.nchunks + 1);
+    exclusive_scan(width.get(), S.cptr.p, S.nchunks + 1, s);
+    S.nelem = d2h(S.cptr.p + S.nchunks, s);
+    S.perm.alloc(nslots);
+    S.col.alloc(S.nelem);
+    S.val.alloc(S.nelem);
+    if (split_diag) S.diag.alloc(nslots);
+    k_sell_fill<<<nblk(nslots), TPB, 0, s>>>(slots.p, nslots, ptr, col, val, mode, S.cptr.p, imap, S.perm.p,
+                                             S.col.p, S.val.p, split_diag ? S.diag.p : nullptr);
+    CPC_LAUNCH_CK();
+}
+
+__global__ void k_to_f32(int64_t n, const double* a, float* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_to_bf16(int64_t n, const double* a, __nv_bfloat16* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __double2bfloat16(a[i]);
+}
+
+void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
+    if (vt == VT_F64) return;
+    S.val32.alloc(S.nelem);
+    k_to_f32<<<nblk(S.nelem), TPB, 0, s>>>(S.nelem, S.val.p, S.val32.p);
+    if (S.diag.p) {
+        S.diag32.alloc(S.nslots);
+        k_to_f32<<<nblk(S.nslots), TPB, 0, s>>>(S.nslots, S.diag.p, S.diag32.p);
+    }
+    if (vt == VT_BF16) {
+        S.val16.alloc(S.nelem);
+        k_to_bf16<<<nblk(S.nelem), TPB, 0, s>>>(S.nelem, S.val.p, S.val16.p);
+    }
+    CPC_LAUNCH_CK();
+}
+
+// ============================================================================================
+// Coarsest level: dense Cholesky and explicit inverse, one block.
+// ============================================================================================
+__global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const double* val, double* M) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) M[(size_t)i * n + col[p]] = val[p];
+}
+
+__global__ void k_dense_chol_inverse(int n, double* M, double* Ainv, int* fail) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = M[(size_t)j * n + j];
+            if (!(d > 0.0) || !isfinite(d)) bad = 1;
+            else M[(size_t)j * n + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double djj = M[(size_t)j * n + j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(size_t)i * n + j] /= djj;
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const double lij = M[(size_t)i * n + j];
+            for (int k = j + 1; k <= i; ++k) M[(size_t)i * n + k] -= lij * M[(size_t)k * n + j];
+        }
+        __syncthreads();
+    }
+    if (bad) { if (threadIdx.x == 0) *fail = 1; return; }
+    // columns of A^{-1} = L^{-T} L^{-1} e_c, one per thread (A^{-1} symmetric: stored as row c)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double* x = Ainv + (size_t)c * n;
+        for (int r = 0; r < c; ++r) x[r] = 0.0;
+        for (int r = c; r < n; ++r) {
+            double sacc = (r == c) ? 1.0 : 0.0;
+            for (int k = c; k < r; ++k) sacc -= M[(size_t)r * n + k] * x[k];
+            x[r] = sacc / M[(size_t)r * n + r];
+        }
+        for (int r = n - 1; r >= 0; --r) {
+            double sacc = x[r];
+            for (int k = r + 1; k < n; ++k) sacc -= M[(size_t)k * n + r] * x[k];
+            x[r] = sacc / M[(size_t)r * n + r];
+        }
+    }
+}
+
+// ============================================================================================
+// Host orchestration
+// ============================================================================================
+void copy_csr_in(const cpc_csr& in, Csr& A, cudaStream_t s) {
+    A.n = A.m = in.n;
+    A.nnz = in.nnz;
+    A.ptr.alloc(in.n + 1);
+    A.col.alloc(in.nnz);
+    A.val.alloc(in.nnz);
+    const cudaMemcpyKind kind = in.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CPC_CK(cudaMemcpyAsync(A.ptr.p, in.rowptr, sizeof(int) * (in.n + 1), kind, s));
+    CPC_CK(cudaMemcpyAsync(A.col.p, in.colidx, sizeof(int) * in.nnz, kind, s));
+    CPC_CK(cudaMemcpyAsync(A.val.p, in.vals, sizeof(double) * in.nnz, kind, s));
+}
+
+// Level DAG (lower or upper) -> levels per row; returns the number of levels.
+int dag_levels(const Csr& A, bool upper, int* lvl, cudaStream_t s) {
+    const int n = A.n;
+    k_fill_int<<<nblk(n), TPB, 0, s>>>(lvl, n, -1);
+    Tmp<int> cnt(1, s);
+    CPC_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int), s));
+    int round = 0;
+    for (;;) {
+        for (int k = 0; k < 16; ++k, ++round)
+            k_dag_round<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, A.col.p, lvl, round, upper ? 1 : 0, cnt.get());
+        CPC_LAUNCH_CK();
+        const int done = d2h(cnt.get(), s);
+        if (done == n) break;
+        if (round > n + 16) fail(CPC_EINVAL, "triangular dependency graph has a cycle");
+    }
+    // number of levels = max level + 1
+    size_t tmp = 0;
+    Tmp<int> mx(1, s);
+    CPC_CK(cub::DeviceReduce::Max(nullptr, tmp, lvl, mx.get(), n, s));
+    Tmp<char> t(tmp, s);
+    CPC_CK(cub::DeviceReduce::Max(t.get(), tmp, lvl, mx.get(), n, s));
+    return d2h(mx.get(), s) + 1;
+}
+
+void setup_ic0(Handle& h, cudaStream_t s) {
+    Csr& A = h.Aic;
+    const int n = A.n;
+    h.lu.alloc(A.nnz);
+    CPC_CK(cudaMemcpyAsync(h.lu.p, A.val.p, sizeof(double) * A.nnz, cudaMemcpyDeviceToDevice, s));
+    h.lu_diag.alloc(n);
+    {
+        Tmp<int> bad(1, s);
+        CPC_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+        k_validate<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, A.col.p, (int)A.nnz, bad.get(), h.lu_diag.p);
+        if (d2h(bad.get(), s)) fail(CPC_EINVAL, "invalid CSR for the IC(0) ordering");
+    }
+    // forward levels, factorisation level by level
+    Tmp<int> lvl(n, s);
+    h.ic_levels_L = dag_levels(A, false, lvl.get(), s);
+    DBuf<int> slotsL, rowsL;
+    int nslotsL = 0;
+    std::vector<int> segL;
+    grouped_slots(n, lvl.get(), h.ic_levels_L, s, slotsL, nslotsL, segL, &rowsL);
+    // level g has rows rowsL[gstart..], count from segments: recompute counts from the slot layout
+    std::vector<int> hc(h.ic_levels_L);
+    {
+        Tmp<int> cnt(h.ic_levels_L, s);
+        CPC_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int) * h.ic_levels_L, s));
+        k_group_count<<<nblk(n), TPB, 0, s>>>(n, lvl.get(), cnt.get());
+        CPC_CK(cudaMemcpyAsync(hc.data(), cnt.get(), sizeof(int) * h.ic_levels_L, cudaMemcpyDeviceToHost, s));
+        CPC_CK(cudaStreamSynchronize(s));
+    }
+    Tmp<int> failrow(1, s);
+    k_fill_int<<<1, 1, 0, s>>>(failrow.get(), 1, INT_MAX);
+    int off = 0;
+    for (int g = 0; g < h.ic_levels_L; ++g) {
+        k_ic0_level<<<nblk(hc[g], 128), 128, 0, s>>>(rowsL.p + off, hc[g], A.ptr.p, A.col.p, h.lu_diag.p, h.lu.p,
+                                                      failrow.get());
+        off += hc[g];
+    }
+    CPC_LAUNCH_CK();
+    const int fr = d2h(failrow.get(), s);
+    if (fr != INT_MAX) fail(CPC_EFACTOR, "IC(0) pivot not positive at row " + std::to_string(fr));
+    // triangular-solve layouts: L by forward levels, U by backward levels; rows/cols renamed to the
+    // original numbering when the IC ordering is a permutation
+    const int* imap = h.ic_order.p;
+    build_sell(A.ptr.p, A.col.p, h.lu.p, slotsL, nslotsL, segL, SELL_LOWER, false, imap, h.L, s);
+    h.ic_levels_U = dag_levels(A, true, lvl.get(), s);
+    // backward solve processes levels of the upper DAG in ascending order
+    DBuf<int> slotsU;
+    int nslotsU = 0;
+    std::vector<int> segU;
+    grouped_slots(n, lvl.get(), h.ic_levels_U, s, slotsU, nslotsU, segU);
+    build_sell(A.ptr.p, A.col.p, h.lu.p, slotsU, nslotsU, segU, SELL_UPPER, true, imap, h.U, s);
+    CPC_CK(cudaStreamSynchronize(s));
+}
+
+void setup_level_sells(Level& L, cudaStream_t s, bool last) {
+    // colour-grouped A_l (Gauss-Seidel and residual)
+    if (!last) {
+        DBuf<int> slots;
+        int nslots = 0;
+        std::vector<int> seg;
+        grouped_slots(L.n, L.colour.p, L.ncolours, s, slots, nslots, seg);
+        build_sell(L.A.ptr.p, L.A.col.p, L.A.val.p, slots, nslots, seg, SELL_OFFDIAG, true, nullptr, L.S, s);
+        DBuf<int> ps;
+        int pn = 0;
+        std::vector<int> pseg;
+        natural_slots(L.P.n, s, ps, pn, pseg);
+        build_sell(L.P.ptr.p, L.P.col.p, L.P.val.p, ps, pn, pseg, SELL_ALL, false, nullptr, L.SP, s);
+        DBuf<int> rs;
+        int rn = 0;
+        std::vector<int> rseg;
+        natural_slots(L.R.n, s, rs, rn, rseg);
+        build_sell(L.R.ptr.p, L.R.col.p, L.R.val.p, rs, rn, rseg, SELL_ALL, false, nullptr, L.SR, s);
+        CPC_CK(cudaStreamSynchronize(s));
+    }
+}
+
+// One coarsening step on level l; returns false when l becomes the coarsest level.
+bool coarsen(Handle& h, int l, cudaStream_t s) {
+    Level& L = h.lev[l];
+    const int n = L.n;
+    const int64_t nnz = L.A.nnz;
+    Tmp<int> tpos(nnz, s), cnt(n, s), bad(1, s);
+    Tmp<uint8_t> strong(nnz, s), sel(n, s);
+    Tmp<int8_t> st(n, s);
+    CPC_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_transpose_pos<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, tpos.get(), bad.get());
+    if (d2h(bad.get(), s)) fail(CPC_EINVAL, "matrix is not structurally symmetric");
+    k_strength<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, L.A.val.p, h.opt.theta, strong.get());
+    k_st_count<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, tpos.get(), strong.get(), cnt.get());
+    k_pmis_init<<<nblk(n), TPB, 0, s>>>(n, cnt.get(), st.get());
+    Tmp<int> undec(1, s);
+    for (int round = 0;; ++round) {
+        k_pmis_select<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, tpos.get(), strong.get(), cnt.get(),
+                                              st.get(), sel.get());
+        k_pmis_setc<<<nblk(n), TPB, 0, s>>>(n, sel.get(), st.get());
+        CPC_CK(cudaMemsetAsync(undec.get(), 0, sizeof(int), s));
+        k_pmis_setf<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, strong.get(), st.get(), undec.get());
+        CPC_LAUNCH_CK();
+        if (d2h(undec.get(), s) == 0) break;
+        if (round > n) fail(CPC_ESETUP, "PMIS did not terminate");
+    }
+    L.cf.alloc(n);
+    k_cf_flags<<<nblk(n), TPB, 0, s>>>(n, st.get(), L.cf.p);
+    Tmp<int> cidx(n + 1, s), ccnt(n + 1, s);
+    CPC_CK(cudaMemsetAsync(ccnt.get() + n, 0, sizeof(int), s));
+    CPC_CK(cudaMemcpyAsync(ccnt.get(), L.cf.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    exclusive_scan(ccnt.get(), cidx.get(), n + 1, s);
+    const int nc = d2h(cidx.get() + n, s);
+    if (nc == 0 || nc == n) {
+        L.cf.release();
+        return false;
+    }
+    // interpolation
+    Csr& P = L.P;
+    P.n = n; P.m = nc;
+    Tmp<int> pcnt(n + 1, s);
+    k_interp_count<<<nblk(n + 1), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, strong.get(), L.cf.p, pcnt.get());
+    P.ptr.alloc(n + 1);
+    exclusive_scan(pcnt.get(), P.ptr.p, n + 1, s);
+    P.nnz = d2h(P.ptr.p + n, s);
+    P.col.alloc(P.nnz);
+    P.val.alloc(P.nnz);
+    k_interp_fill<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, L.A.val.p, strong.get(), L.cf.p, cidx.get(),
+                                          P.ptr.p, P.col.p, P.val.p);
+    CPC_LAUNCH_CK();
+    transpose(P, L.R, s);
+    // colouring of A_l
+    L.colour.alloc(n);
+    k_fill_int<<<nblk(n), TPB, 0, s>>>(L.colour.p, n, -1);
+    Tmp<int> done(1, s);
+    CPC_CK(cudaMemsetAsync(done.get(), 0, sizeof(int), s));
+    for (int round = 0;; ++round) {
+        k_jp_select<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, L.colour.p, sel.get());
+        k_jp_assign<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, sel.get(), L.colour.p, done.get());
+        CPC_LAUNCH_CK();
+        if (d2h(done.get(), s) == n) break;
+        if (round > n) fail(CPC_ESETUP, "colouring did not terminate");
+    }
+    {
+        size_t tmp = 0;
+        Tmp<int> mx(1, s);
+        CPC_CK(cub::DeviceReduce::Max(nullptr, tmp, L.colour.p, mx.get(), n, s));
+        Tmp<char> t(tmp, s);
+        CPC_CK(cub::DeviceReduce::Max(t.get(), tmp, L.colour.p, mx.get(), n, s));
+        L.ncolours = d2h(mx.get(), s) + 1;
+    }
+    // Galerkin coarse operator A_c = R (A P)
+    Csr AP;
+    spgemm(L.A, P, AP, s);
+    h.lev.emplace_back();
+    Level& Lc = h.lev.back();
+    spgemm(h.lev[l].R, AP, Lc.A, s);
+    Lc.n = Lc.A.n;
+    Lc.A.m = Lc.A.n;
+    Lc.nnz = Lc.A.nnz;
+    CPC_CK(cudaStreamSynchronize(s));
+    return true;
+}
+
+}  // namespace
+
+// ============================================================================================
+void tpfa_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask, int* rowptr, int* col,
+                   double* val, cudaStream_t s) {
+    const int n = nx * ny * nz;
+    Tmp<int> len(n + 1, s);
+    CPC_CK(cudaMemsetAsync(len.get() + n, 0, sizeof(int), s));
+    k_tpfa_rowlen<<<nblk(n), TPB, 0, s>>>(nx, ny, nz, len.get());
+    exclusive_scan(len.get(), rowptr, n + 1, s);
+    k_tpfa_fill<<<nblk(n), TPB, 0, s>>>(nx, ny, nz, logk, kzr, dmask, rowptr, col, val);
+    CPC_LAUNCH_CK();
+}
+
+void setup_handle(Handle& h, const cpc_csr& in) {
+    cudaStream_t s = h.s;
+    h.n = in.n;
+    h.nnz = in.nnz;
+    h.lev.clear();
+    h.lev.emplace_back();
+    {
+        Level& L0 = h.lev[0];
+        copy_csr_in(in, L0.A, s);
+        L0.n = in.n;
+        L0.nnz = in.nnz;
+        Tmp<int> bad(1, s), diag(in.n, s);
+        CPC_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+        k_validate<<<nblk(in.n), TPB, 0, s>>>(in.n, L0.A.ptr.p, L0.A.col.p, in.nnz, bad.get(), diag.get());
+        CPC_LAUNCH_CK();
+        const int b = d2h(bad.get(), s);
+        if (b & 1) fail(CPC_EINVAL, "invalid row pointers");
+        if (b & 2) fail(CPC_EINVAL, "column index out of range or not ascending");
+        if (b & 4) fail(CPC_EINVAL, "missing diagonal entry");
+    }
+    cudaEvent_t e0, e1, e2;
+    CPC_CK(cudaEventCreate(&e0));
+    CPC_CK(cudaEventCreate(&e1));
+    CPC_CK(cudaEventCreate(&e2));
+    struct EvGuard {
+        cudaEvent_t a, b, c;
+        ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c); }
+    } guard{e0, e1, e2};
+
+    const bool colour_ic = h.opt.ic_order == 1;
+    // natural-order IC(0) first (a breakdown is reported before any AMG work)
+    CPC_CK(cudaEventRecord(e0, s));
+    if (!colour_ic) {
+        Level& L0 = h.lev[0];
+        h.Aic.n = h.Aic.m = L0.n;
+        h.Aic.nnz = L0.nnz;
+        h.Aic.ptr.alloc(L0.n + 1);
+        h.Aic.col.alloc(L0.nnz);
+        h.Aic.val.alloc(L0.nnz);
+        CPC_CK(cudaMemcpyAsync(h.Aic.ptr.p, L0.A.ptr.p, sizeof(int) * (L0.n + 1), cudaMemcpyDeviceToDevice, s));
+        CPC_CK(cudaMemcpyAsync(h.Aic.col.p, L0.A.col.p, sizeof(int) * L0.nnz, cudaMemcpyDeviceToDevice, s));
+        CPC_CK(cudaMemcpyAsync(h.Aic.val.p, L0.A.val.p, sizeof(double) * L0.nnz, cudaMemcpyDeviceToDevice, s));
+        setup_ic0(h, s);
+    }
+    CPC_CK(cudaEventRecord(e1, s));
+    // AMG hierarchy
+    for (int l = 0;; ++l) {
+        const bool stop = h.lev[l].n <= h.opt.coarse_max || (int)h.lev.size() >= h.opt.max_levels;
+        if (stop || !coarsen(h, l, s)) break;
+    }
+    const int nl = (int)h.lev.size();
+    {
+        Level& Lc = h.lev[nl - 1];
+        h.nc = Lc.n;
+        if (h.nc > DENSE_MAX) fail(CPC_ESETUP, "coarsest level too large for the dense solve");
+        Tmp<double> M((size_t)h.nc * h.nc, s);
+        CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s));
+        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
+        h.Ainv.alloc((size_t)h.nc * h.nc);
+        Tmp<int> f(1, s);
+        CPC_CK(cudaMemsetAsync(f.get(), 0, sizeof(int), s));
+        k_dense_chol_inverse<<<1, 1024, 0, s>>>(h.nc, M.get(), h.Ainv.p, f.get());
+        CPC_LAUNCH_CK();
+        if (d2h(f.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
+    }
+    for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1);
+    {   // fine A in natural order for the SpMVs
+        DBuf<int> slots;
+        int nslots = 0;
+        std::vector<int> seg;
+        natural_slots(h.n, s, slots, nslots, seg);
+        build_sell(h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, slots, nslots, seg, SELL_OFFDIAG, true,
+                   nullptr, h.Anat, s);
+        CPC_CK(cudaStreamSynchronize(s));
+    }
+    CPC_CK(cudaEventRecord(e2, s));
+    if (colour_ic) {
+        // IC(0) of the colour-ordered fine matrix: order = rows sorted by (colour, index)
+        Level& L0 = h.lev[0];
+        if (nl < 2) fail(CPC_EINVAL, "colour-ordered IC(0) needs at least two AMG levels");
+        DBuf<int> rows;
+        {
+            DBuf<int> slots;
+            int nslots = 0;
+            std::vector<int> seg;
+            grouped_slots(L0.n, L0.colour.p, L0.ncolours, s, slots, nslots, seg, &rows);
+        }
+        h.ic_order = std::move(rows);
+        Tmp<int> inv(L0.n, s), len(L0.n + 1, s);
+        k_inverse_perm<<<nblk(L0.n), TPB, 0, s>>>(L0.n, h.ic_order.p, inv.get());
+        h.Aic.n = h.Aic.m = L0.n;
+        h.Aic.nnz = L0.nnz;
+        h.Aic.ptr.alloc(L0.n + 1);
+        h.Aic.col.alloc(L0.nnz);
+        h.Aic.val.alloc(L0.nnz);
+        k_perm_rowlen<<<nblk(L0.n + 1), TPB, 0, s>>>(L0.n, L0.A.ptr.p, h.ic_order.p, len.get());
+        exclusive_scan(len.get(), h.Aic.ptr.p, L0.n + 1, s);
+        k_perm_fill<<<nblk(L0.n), TPB, 0, s>>>(L0.n, L0.A.ptr.p, L0.A.col.p, L0.A.val.p, h.ic_order.p, inv.get(),
+                                               h.Aic.ptr.p, h.Aic.col.p, h.Aic.val.p);
+        CPC_LAUNCH_CK();
+        cudaEvent_t e3;
+        CPC_CK(cudaEventCreate(&e3));
+        CPC_CK(cudaEventRecord(e3, s));
+        setup_ic0(h, s);
+        cudaEvent_t e4;
+        CPC_CK(cudaEventCreate(&e4));
+        CPC_CK(cudaEventRecord(e4, s));
+        CPC_CK(cudaEventSynchronize(e4));
+        float a = 0.f;
+        cudaEventElapsedTime(&a, e3, e4);
+        cudaEventDestroy(e3);
+        cudaEventDestroy(e4);
+        h.ms_ic0 = a;
+    }
+    CPC_CK(cudaEventSynchronize(e2));
+    float a = 0.f, b = 0.f;
+    CPC_CK(cudaEventElapsedTime(&a, e0, e1));
+    CPC_CK(cudaEventElapsedTime(&b, e1, e2));
+    if (!colour_ic) h.ms_ic0 = a;
+    h.ms_amg = b;
+
+    // precision of the preconditioner data
+    const int prec = h.opt.precision;
+    for (int l = 0; l < nl; ++l) {
+        Level& L = h.lev[l];
+        L.vt = prec == CPC_PREC_FP64 ? VT_F64 : (prec == CPC_PREC_FP32_BF16 && l > 0 ? VT_BF16 : VT_F32);
+        if (l < nl - 1) {
+            sell_lowp(L.S, L.vt, s);
+            sell_lowp(L.SP, L.vt == VT_BF16 ? VT_F32 : L.vt, s);
+            sell_lowp(L.SR, L.vt == VT_BF16 ? VT_F32 : L.vt, s);
+        }
+        const size_t n = L.n;
+        if (L.vt == VT_F64) { L.x64.alloc(n); L.f64.alloc(n); L.r64.alloc(n); }
+        else { L.x32.alloc(n); L.f32.alloc(n); L.r32.alloc(n); }
+    }
+    if (prec != CPC_PREC_FP64) {
+        sell_lowp(h.Anat, VT_F32, s);
+        sell_lowp(h.L, VT_F32, s);
+        sell_lowp(h.U, VT_F32, s);
+        h.Ainv32.alloc((size_t)h.nc * h.nc);
+        k_to_f32<<<nblk((int64_t)h.nc * h.nc), TPB, 0, s>>>((int64_t)h.nc * h.nc, h.Ainv.p, h.Ainv32.p);
+        h.z32.alloc(h.n); h.t32.alloc(h.n); h.y32.alloc(h.n);
+    }
+    // PCG and preconditioner vectors
+    const size_t n = h.n;
+    h.b.alloc(n); h.x.alloc(n); h.r.alloc(n); h.z.alloc(n); h.p.alloc(n); h.q.alloc(n);
+    h.t.alloc(n); h.y.alloc(n);
+    h.partial.alloc(4 * NPART);
+    h.counter.alloc(8);
+    CPC_CK(cudaMemsetAsync(h.counter.p, 0, sizeof(unsigned) * 8, s));
+    h.state.alloc(1);
+    CPC_CK(cudaMemsetAsync(h.state.p, 0, sizeof(PcgState), s));
+    h.hist.alloc(HIST_CAP);
+    h.flags.alloc(8);
+    CPC_CK(cudaMemsetAsync(h.flags.p, 0, sizeof(int) * 8, s));
+    CPC_CK(cudaStreamSynchronize(s));
+    CPC_LAUNCH_CK();
+}
+
+}  // namespace cpc

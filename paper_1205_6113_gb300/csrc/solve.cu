@@ -1,0 +1,680 @@
+// solve.cu -- solve phase: V-cycle (Algorithm 3.2), IC(0) triangular solves, the combined
+// preconditioner (Algorithm 2.1) and PCG, all as sm_103a kernels; the PCG loop is one CUDA graph
+// with a device-side while node, so the host only launches it and reads back the result.
+//
+// Kernel layout: every matrix is SELL-C (C = 32): one warp per chunk of 32 rows, one row per lane,
+// entries column-major inside a chunk so that each load instruction of a warp is coalesced.
+// Reductions (dot products) finish in a fixed order (per-block tree, then the last block sums the
+// block partials in index order), so iteration counts are reproducible run to run.
+#include <algorithm>
+#include <cstdio>
+#include <type_traits>
+
+#include "handle.cuh"
+
+namespace cpc {
+
+namespace {
+
+constexpr int WPB = 4;                  // warps (= SELL chunks) per block
+constexpr int SELL_TPB = WPB * 32;
+constexpr int VEC_TPB = 256;
+
+__device__ __forceinline__ double cvt_d(double v) { return v; }
+__device__ __forceinline__ double cvt_d(float v) { return (double)v; }
+__device__ __forceinline__ float cvt_f(double v) { return (float)v; }
+__device__ __forceinline__ float cvt_f(float v) { return v; }
+__device__ __forceinline__ float cvt_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class VT> struct Cv;
+template <> struct Cv<double> {
+    template <class T> __device__ static __forceinline__ double f(T v) { return cvt_d(v); }
+};
+template <> struct Cv<float> {
+    template <class T> __device__ static __forceinline__ float f(T v) { return cvt_f(v); }
+};
+
+template <class MT, class DT>
+struct SV {       // SELL view passed by value
+    const int* __restrict__ perm;
+    const int* __restrict__ cptr;
+    const int* __restrict__ col;
+    const MT* __restrict__ val;
+    const DT* __restrict__ diag;
+};
+
+template <class MT, class DT>
+SV<MT, DT> view(const Sell& S, const MT* val, const DT* diag) {
+    return SV<MT, DT>{S.perm.p, S.cptr.p, S.col.p, val, diag};
+}
+
+inline int blocks_for_chunks(int nchunks) { return std::max(1, (nchunks + WPB - 1) / WPB); }
+inline int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + VEC_TPB - 1) / VEC_TPB, NPART)); }
+
+// ---------------------------------------------------------------------------------------------
+// Level kernels
+// ---------------------------------------------------------------------------------------------
+// Gauss-Seidel over the rows of one colour (chunks [c0, c1)): x_i = (f_i - sum_{j!=i} a_ij x_j) / a_ii.
+// Rows of one colour are not coupled, so they update in parallel exactly as in sequential order.
+template <class MT, class DT, class FT, class VT>
+__global__ void __launch_bounds__(SELL_TPB) k_gs(SV<MT, DT> A, int c0, int c1, const FT* __restrict__ f, VT* x) {
+    const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (k >= c1) return;
+    const int lane = threadIdx.x & 31;
+    const int s = k * 32 + lane;
+    const int row = A.perm[s];
+    if (row < 0) return;
+    const int b = A.cptr[k], e = A.cptr[k + 1];
+    VT acc = Cv<VT>::f(f[row]);
+    for (int o = b + lane; o < e; o += 32) {
+        const int c = A.col[o];
+        if (c >= 0) acc -= Cv<VT>::f(A.val[o]) * x[c];
+    }
+    x[row] = acc / Cv<VT>::f(A.diag[s]);
+}
+
+// r = f - A x over all chunks (grid-stride over chunks).
+template <class MT, class DT, class FT, class XT, class RT>
+__global__ void __launch_bounds__(SELL_TPB) k_resid(SV<MT, DT> A, int nchunks, const FT* __restrict__ f,
+                                                     const XT* __restrict__ x, RT* __restrict__ r) {
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
+        const int s = k * 32 + lane;
+        const int row = A.perm[s];
+        if (row < 0) continue;
+        const int b = A.cptr[k], e = A.cptr[k + 1];
+        RT acc = Cv<RT>::f(f[row]) - Cv<RT>::f(A.diag[s]) * Cv<RT>::f(x[row]);
+        for (int o = b + lane; o < e; o += 32) {
+            const int c = A.col[o];
+            if (c >= 0) acc -= Cv<RT>::f(A.val[o]) * Cv<RT>::f(x[c]);
+        }
+        r[row] = acc;
+    }
+}
+
+// y = A x (diagonal split) over all chunks.
+template <class MT, class DT, class XT, class YT>
+__global__ void __launch_bounds__(SELL_TPB) k_spmv(SV<MT, DT> A, int nchunks, const XT* __restrict__ x,
+                                                    YT* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
+        const int s = k * 32 + lane;
+        const int row = A.perm[s];
+        if (row < 0) continue;
+        const int b = A.cptr[k], e = A.cptr[k + 1];
+        YT acc = Cv<YT>::f(A.diag[s]) * Cv<YT>::f(x[row]);
+        for (int o = b + lane; o < e; o += 32) {
+            const int c = A.col[o];
+            if (c >= 0) acc += Cv<YT>::f(A.val[o]) * Cv<YT>::f(x[c]);
+        }
+        y[row] = acc;
+    }
+}
+
+// y = M x (full rows, no split diagonal): restriction f_c = R r.
+template <class MT, class VT>
+__global__ void __launch_bounds__(SELL_TPB) k_apply_full(SV<MT, MT> M, int nchunks, const VT* __restrict__ x,
+                                                          VT* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
+        const int row = M.perm[k * 32 + lane];
+        if (row < 0) continue;
+        const int b = M.cptr[k], e = M.cptr[k + 1];
+        VT acc = 0;
+        for (int o = b + lane; o < e; o += 32) {
+            const int c = M.col[o];
+            if (c >= 0) acc += Cv<VT>::f(M.val[o]) * x[c];
+        }
+        y[row] = acc;
+    }
+}
+
+// x += P e (prolongation and correction).
+template <class MT, class VT>
+__global__ void __launch_bounds__(SELL_TPB) k_prolong(SV<MT, MT> P, int nchunks, const VT* __restrict__ e,
+                                                       VT* __restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
+        const int row = P.perm[k * 32 + lane];
+        if (row < 0) continue;
+        const int b = P.cptr[k], en = P.cptr[k + 1];
+        VT acc = 0;
+        for (int o = b + lane; o < en; o += 32) {
+            const int c = P.col[o];
+            if (c >= 0) acc += Cv<VT>::f(P.val[o]) * e[c];
+        }
+        x[row] += acc;
+    }
+}
+
+// x = A_c^{-1} f with the dense inverse (row-major), one warp per row.
+template <class AT, class FT, class VT>
+__global__ void k_coarse(int n, const AT* __restrict__ Ainv, const FT* __restrict__ f, VT* __restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += gridDim.x * (blockDim.x >> 5)) {
+        VT acc = 0;
+        for (int j = lane; j < n; j += 32) acc += Cv<VT>::f(Ainv[(size_t)i * n + j]) * Cv<VT>::f(f[j]);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) x[i] = acc;
+    }
+}
+
+template <class VT>
+__global__ void k_zero(int64_t n, VT* x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 0;
+}
+
+template <class A, class B>
+__global__ void k_copy(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (B)a[i];
+}
+
+// Forward solve with the unit lower factor, rows of one level: y_i = t_i - sum_{j<i} l_ij y_j.
+template <class MT, class TT, class VT>
+__global__ void __launch_bounds__(SELL_TPB) k_lsolve(SV<MT, MT> L, int c0, int c1, const TT* __restrict__ t, VT* y) {
+    const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (k >= c1) return;
+    const int lane = threadIdx.x & 31;
+    const int row = L.perm[k * 32 + lane];
+    if (row < 0) return;
+    const int b = L.cptr[k], e = L.cptr[k + 1];
+    VT acc = Cv<VT>::f(t[row]);
+    for (int o = b + lane; o < e; o += 32) {
+        const int c = L.col[o];
+        if (c >= 0) acc -= Cv<VT>::f(L.val[o]) * y[c];
+    }
+    y[row] = acc;
+}
+
+// Backward solve with U, rows of one level: w_i = (y_i - sum_{j>i} u_ij w_j) / u_ii; optionally
+// z_i += w_i in the same pass.
+template <class MT, class VT>
+__global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> U, int c0, int c1, const VT* __restrict__ y, VT* w,
+                                                      VT* zadd) {
+    const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (k >= c1) return;
+    const int lane = threadIdx.x & 31;
+    const int s = k * 32 + lane;
+    const int row = U.perm[s];
+    if (row < 0) return;
+    const int b = U.cptr[k], e = U.cptr[k + 1];
+    VT acc = y[row];
+    for (int o = b + lane; o < e; o += 32) {
+        const int c = U.col[o];
+        if (c >= 0) acc -= Cv<VT>::f(U.val[o]) * w[c];
+    }
+    const VT v = acc / Cv<VT>::f(U.diag[s]);
+    w[row] = v;
+    if (zadd) zadd[row] += v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Deterministic reductions: block tree, then the last block to finish sums the partials in order.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block (valid in thread 0).
+__device__ double block_sum(double v) {
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+// Write this block's partial; returns true in every thread of the last block to arrive, which
+// then holds the total (in thread 0) of all partials, summed in block-index order.
+__device__ bool finish_sum(double v, double* part, unsigned* ctr, double* total) {
+    __shared__ bool last;
+    v = block_sum(v);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = v;
+        __threadfence();
+        last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double t = 0.0;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) t += __ldcg(&part[j]);
+    t = block_sum(t);
+    if (threadIdx.x == 0) { *total = t; *ctr = 0u; }
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// PCG kernels (textbook PCG; the order of the oracle's loop)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_pcg_init(int n, const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r,
+                           double* part, unsigned* ctr, PcgState* st, double* hist,
+                           cudaGraphConditionalHandle cond) {
+    double v = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        x[i] = 0.0;
+        r[i] = bi;
+        v += bi * bi;
+    }
+    double tot;
+    if (finish_sum(v, part, ctr, &tot) && threadIdx.x == 0) {
+        const double bn = sqrt(tot);
+        st->bnorm = bn;
+        st->k = 0;
+        st->rz_old = 0.0;
+        st->beta = 0.0;
+        st->alpha = 0.0;
+        st->res = bn > 0.0 ? 1.0 : 0.0;
+        st->status = isfinite(bn) ? CPC_OK : CPC_EBREAKDOWN;
+        hist[0] = st->res;
+        cudaGraphSetConditional(cond, (bn > 0.0 && isfinite(bn) && st->maxit > 0) ? 1u : 0u);
+        if (bn > 0.0 && isfinite(bn) && st->maxit <= 0) st->status = CPC_ENOCONV;
+    }
+}
+
+// First node of every loop iteration: clear the loop condition.  Only the last block of
+// k_pcg_update sets it again, so the loop cannot continue past an iteration whose final
+// reduction did not complete.
+__global__ void k_loop_guard(cudaGraphConditionalHandle cond) { cudaGraphSetConditional(cond, 0u); }
+
+template <class ZT>
+__global__ void k_pcg_rz(int n, const double* __restrict__ r, const ZT* __restrict__ z, double* part, unsigned* ctr,
+                         PcgState* st) {
+    double v = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v += r[i] * cvt_d(z[i]);
+    double tot;
+    if (finish_sum(v, part, ctr, &tot) && threadIdx.x == 0) {
+        if (!(tot > 0.0) || !isfinite(tot)) { if (st->status == CPC_OK) st->status = CPC_EBREAKDOWN; }
+        st->beta = st->k == 0 ? 0.0 : tot / st->rz_old;
+        st->rz = tot;
+        st->rz_old = tot;
+    }
+}
+
+template <class ZT>
+__global__ void k_pcg_p(int n, const ZT* __restrict__ z, double* __restrict__ p, const PcgState* st) {
+    const double beta = st->beta;
+    const bool first = st->k == 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = first ? cvt_d(z[i]) : cvt_d(z[i]) + beta * p[i];
+}
+
+// q = A p and p.q; the last block forms alpha = (r.z) / (p.q).
+__global__ void __launch_bounds__(SELL_TPB) k_pcg_spmv(SV<double, double> A, int nchunks, const double* __restrict__ p,
+                                                        double* __restrict__ q, double* part, unsigned* ctr,
+                                                        PcgState* st) {
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
+        const int s = k * 32 + lane;
+        const int row = A.perm[s];
+        if (row < 0) continue;
+        const int b = A.cptr[k], e = A.cptr[k + 1];
+        const double pr = p[row];
+        double acc = A.diag[s] * pr;
+        for (int o = b + lane; o < e; o += 32) {
+            const int c = A.col[o];
+            if (c >= 0) acc += A.val[o] * p[c];
+        }
+        q[row] = acc;
+        v += pr * acc;
+    }
+    double tot;
+    if (finish_sum(v, part, ctr, &tot) && threadIdx.x == 0) {
+        st->pq = tot;
+        if (!(tot > 0.0) || !isfinite(tot)) { if (st->status == CPC_OK) st->status = CPC_EBREAKDOWN; }
+        st->alpha = st->status == CPC_OK ? st->rz / tot : 0.0;
+    }
+}
+
+// x += alpha p, r -= alpha q, ||r||; the last block updates the iteration count, the residual
+// history and the loop condition.
+__global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                             const double* __restrict__ q, double* part, unsigned* ctr, PcgState* st, double* hist,
+                             int hist_cap, cudaGraphConditionalHandle cond) {
+    const double alpha = st->alpha;
+    double v = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        v += ri * ri;
+    }
+    double tot;
+    if (finish_sum(v, part, ctr, &tot) && threadIdx.x == 0) {
+        unsigned go = 0u;
+        if (st->status == CPC_OK) {
+            const int k = st->k + 1;
+            st->k = k;
+            st->rr = tot;
+            const double res = sqrt(tot) / st->bnorm;
+            st->res = res;
+            if (k < hist_cap) hist[k] = res;
+            if (!isfinite(res)) st->status = CPC_EBREAKDOWN;
+            else if (res < st->tol) st->status = CPC_OK;
+            else if (k >= st->maxit) st->status = CPC_ENOCONV;
+            else go = 1u;
+        }
+        cudaGraphSetConditional(cond, go);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Recording helpers (launch sequences; captured into graphs or run directly)
+// ---------------------------------------------------------------------------------------------
+template <class VT> VT* lx(Level& L);
+template <class VT> VT* lf(Level& L);
+template <class VT> VT* lr(Level& L);
+template <> double* lx<double>(Level& L) { return L.x64.p; }
+template <> double* lf<double>(Level& L) { return L.f64.p; }
+template <> double* lr<double>(Level& L) { return L.r64.p; }
+template <> float* lx<float>(Level& L) { return L.x32.p; }
+template <> float* lf<float>(Level& L) { return L.f32.p; }
+template <> float* lr<float>(Level& L) { return L.r32.p; }
+
+template <class VT> const VT* ainv(const Handle& h);
+template <> const double* ainv<double>(const Handle& h) { return h.Ainv.p; }
+template <> const float* ainv<float>(const Handle& h) { return h.Ainv32.p; }
+
+template <class FT, class VT>
+void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
+    const int c0 = L.S.seg[c], c1 = L.S.seg[c + 1];
+    if (c1 <= c0) return;
+    const int g = blocks_for_chunks(c1 - c0);
+    if constexpr (std::is_same<VT, double>::value) {
+        k_gs<<<g, SELL_TPB, 0, s>>>(view(L.S, L.S.val.p, L.S.diag.p), c0, c1, f, x);
+    } else {
+        if (L.vt == VT_BF16)
+            k_gs<<<g, SELL_TPB, 0, s>>>(view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), c0, c1, f, x);
+        else
+            k_gs<<<g, SELL_TPB, 0, s>>>(view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), c0, c1, f, x);
+    }
+}
+
+template <class FT, class VT>
+void rec_resid_level(Level& L, const FT* f, const VT* x, VT* r, cudaStream_t s) {
+    const int g = blocks_for_chunks(L.S.nchunks);
+    if constexpr (std::is_same<VT, double>::value) {
+        k_resid<<<g, SELL_TPB, 0, s>>>(view(L.S, L.S.val.p, L.S.diag.p), L.S.nchunks, f, x, r);
+    } else {
+        if (L.vt == VT_BF16)
+            k_resid<<<g, SELL_TPB, 0, s>>>(view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p),
+                                           L.S.nchunks, f, x, r);
+        else
+            k_resid<<<g, SELL_TPB, 0, s>>>(view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p),
+                                           L.S.nchunks, f, x, r);
+    }
+}
+
+template <class VT>
+SV<VT, VT> full_view(const Sell& S) {
+    if constexpr (std::is_same<VT, double>::value) return view(S, S.val.p, (const double*)nullptr);
+    else return view(S, (const float*)S.val32.p, (const float*)nullptr);
+}
+
+// Algorithm 3.2 from level l: x <- V-cycle(f, initial guess x) (zero guess when zero_guess).
+template <class FT, class VT>
+void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s) {
+    const int nl = (int)h.lev.size();
+    Level& L = h.lev[l];
+    if (l == nl - 1) {                                          // step 2(b): exact coarsest solve
+        k_coarse<<<std::max(1, (L.n + 7) / 8), 256, 0, s>>>(L.n, ainv<VT>(h), f, x);
+        return;
+    }
+    Level& C = h.lev[l + 1];
+    if (zero_guess) k_zero<<<vec_blocks(L.n), VEC_TPB, 0, s>>>(L.n, x);
+    for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);            // (1) S_l: colours ascending
+    rec_resid_level(L, f, x, lr<VT>(L), s);                              // (2a) r = f - A u
+    k_apply_full<<<blocks_for_chunks(L.SR.nchunks), SELL_TPB, 0, s>>>(full_view<VT>(L.SR), L.SR.nchunks,
+                                                                        (const VT*)lr<VT>(L), lf<VT>(C));
+    rec_vcycle<VT, VT>(h, l + 1, lf<VT>(C), lx<VT>(C), true, s);         // (2b) zero initial guess
+    k_prolong<<<blocks_for_chunks(L.SP.nchunks), SELL_TPB, 0, s>>>(full_view<VT>(L.SP), L.SP.nchunks,
+                                                                     (const VT*)lx<VT>(C), x);   // (2c)
+    for (int c = L.ncolours - 1; c >= 0; --c) rec_gs(L, c, f, x, s);     // (3) S_l^T: colours descending
+}
+
+// t = r - A z with the fine A in the preconditioner's precision.
+template <class VT>
+void rec_fine_resid(Handle& h, const double* r, const VT* z, VT* t, cudaStream_t s) {
+    const Sell& A = h.Anat;
+    const int g = blocks_for_chunks(A.nchunks);
+    if constexpr (std::is_same<VT, double>::value)
+        k_resid<<<g, SELL_TPB, 0, s>>>(view(A, A.val.p, A.diag.p), A.nchunks, r, z, t);
+    else
+        k_resid<<<g, SELL_TPB, 0, s>>>(view(A, (const float*)A.val32.p, (const float*)A.diag32.p), A.nchunks, r, z, t);
+}
+
+// w = (LU)^{-1} t level by level; with zadd, z += w as well.
+template <class TT, class VT>
+void rec_ic_solve(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s) {
+    const Sell& L = h.L;
+    const Sell& U = h.U;
+    SV<VT, VT> lv, uv;
+    if constexpr (std::is_same<VT, double>::value) {
+        lv = view(L, L.val.p, (const double*)nullptr);
+        uv = view(U, U.val.p, U.diag.p);
+    } else {
+        lv = view(L, (const float*)L.val32.p, (const float*)nullptr);
+        uv = view(U, (const float*)U.val32.p, (const float*)U.diag32.p);
+    }
+    for (int g = 0; g + 1 < (int)L.seg.size(); ++g) {
+        const int c0 = L.seg[g], c1 = L.seg[g + 1];
+        k_lsolve<<<blocks_for_chunks(c1 - c0), SELL_TPB, 0, s>>>(lv, c0, c1, t, y);
+    }
+    for (int g = 0; g + 1 < (int)U.seg.size(); ++g) {
+        const int c0 = U.seg[g], c1 = U.seg[g + 1];
+        k_usolve<<<blocks_for_chunks(c1 - c0), SELL_TPB, 0, s>>>(uv, c0, c1, (const VT*)y, w, zadd);
+    }
+}
+
+template <class VT> VT* ft(Handle& h);
+template <> double* ft<double>(Handle& h) { return h.t.p; }
+template <> float* ft<float>(Handle& h) { return h.t32.p; }
+template <class VT> VT* fy(Handle& h);
+template <> double* fy<double>(Handle& h) { return h.y.p; }
+template <> float* fy<float>(Handle& h) { return h.y32.p; }
+
+// z = M r for the chosen preconditioner (z in the preconditioner's vector type).
+template <class VT>
+void rec_precond_t(Handle& h, int which, const double* r, VT* z, cudaStream_t s) {
+    VT* t = ft<VT>(h);
+    VT* y = fy<VT>(h);
+    switch (which) {
+        case CPC_PRECOND_BCO:                         // Algorithm 2.1 with u^{k,0} = 0
+            rec_vcycle<double, VT>(h, 0, r, z, true, s);        // (1) z = S r
+            rec_fine_resid<VT>(h, r, z, t, s);                  // (2) z += B (r - A z)
+            rec_ic_solve<VT, VT>(h, t, y, t, z, s);
+            rec_vcycle<double, VT>(h, 0, r, z, false, s);       // (3) z += S^T (r - A z), S^T = S
+            break;
+        case CPC_PRECOND_AMG:                         // S~: two cycles
+            rec_vcycle<double, VT>(h, 0, r, z, true, s);
+            rec_vcycle<double, VT>(h, 0, r, z, false, s);
+            break;
+        case CPC_PRECOND_IC0:
+            rec_ic_solve<double, VT>(h, r, y, z, (VT*)nullptr, s);
+            break;
+        case CPC_PRECOND_BHAT:                        // S~ r + B r
+            rec_vcycle<double, VT>(h, 0, r, z, true, s);
+            rec_vcycle<double, VT>(h, 0, r, z, false, s);
+            rec_ic_solve<double, VT>(h, r, y, t, z, s);
+            break;
+        default:
+            k_copy<<<vec_blocks(h.n), VEC_TPB, 0, s>>>((int64_t)h.n, r, z);
+            break;
+    }
+}
+
+bool fp64(const Handle& h) { return h.opt.precision == CPC_PREC_FP64; }
+
+void check_which(int which) {
+    if (which < 0 || which >= NPRECOND) fail(CPC_EINVAL, "unknown preconditioner");
+}
+
+}  // namespace
+
+// =============================================================================================
+void record_precond(Handle& h, int which, const double* r, void* z, cudaStream_t s) {
+    check_which(which);
+    if (fp64(h)) rec_precond_t<double>(h, which, r, (double*)z, s);
+    else rec_precond_t<float>(h, which, r, (float*)z, s);
+}
+
+void apply_precond(Handle& h, int which, const double* r, double* z) {
+    check_which(which);
+    cudaStream_t s = h.s;
+    if (fp64(h)) {
+        rec_precond_t<double>(h, which, r, z, s);
+    } else {
+        rec_precond_t<float>(h, which, r, h.z32.p, s);
+        k_copy<<<vec_blocks(h.n), VEC_TPB, 0, s>>>((int64_t)h.n, (const float*)h.z32.p, z);
+    }
+    CPC_LAUNCH_CK();
+}
+
+void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s) {
+    const Sell& A = h.Anat;
+    k_spmv<<<blocks_for_chunks(A.nchunks), SELL_TPB, 0, s>>>(view(A, A.val.p, A.diag.p), A.nchunks, x, y);
+    CPC_LAUNCH_CK();
+}
+
+void level_apply(Handle& h, int l, int op, const double* x, double* y) {
+    const int nl = (int)h.lev.size();
+    if (l < 0 || l >= nl) fail(CPC_EINVAL, "level out of range");
+    if (!fp64(h)) fail(CPC_EINVAL, "level operators are inspected in FP64 mode only");
+    Level& L = h.lev[l];
+    cudaStream_t s = h.s;
+    const bool last = l == nl - 1;
+    switch (op) {
+        case 0:
+            if (l == 0) spmv_fine(h, x, y, s);
+            else if (last) fail(CPC_EINVAL, "coarsest level has no sparse layout");
+            else k_spmv<<<blocks_for_chunks(L.S.nchunks), SELL_TPB, 0, s>>>(view(L.S, L.S.val.p, L.S.diag.p),
+                                                                         L.S.nchunks, x, y);
+            break;
+        case 1:
+        case 2:
+            if (last) fail(CPC_EINVAL, "coarsest level has no smoother");
+            k_zero<<<vec_blocks(L.n), VEC_TPB, 0, s>>>(L.n, y);
+            if (op == 1) for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, x, y, s);
+            else for (int c = L.ncolours - 1; c >= 0; --c) rec_gs(L, c, x, y, s);
+            break;
+        case 3:
+            if (!last) fail(CPC_EINVAL, "not the coarsest level");
+            k_coarse<<<std::max(1, (L.n + 7) / 8), 256, 0, s>>>(L.n, h.Ainv.p, x, y);
+            break;
+        case 4:
+            rec_vcycle<double, double>(h, l, x, y, true, s);
+            break;
+        default:
+            fail(CPC_EINVAL, "unknown level operator");
+    }
+    CPC_LAUNCH_CK();
+}
+
+void destroy_graphs(Handle& h) {
+    for (int i = 0; i < NPRECOND; ++i) {
+        if (h.gexec[i]) cudaGraphExecDestroy(h.gexec[i]);
+        if (h.graph[i]) cudaGraphDestroy(h.graph[i]);
+        h.gexec[i] = nullptr;
+        h.graph[i] = nullptr;
+    }
+}
+
+// The whole PCG loop as one graph: init kernel, then a while node whose body is one iteration.
+static void build_solve_graph(Handle& h, int which) {
+    cudaStream_t cs;
+    CPC_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{cs};
+    cudaGraph_t g;
+    CPC_CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    CPC_CK(cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    const int n = h.n;
+    // init
+    CPC_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    k_pcg_init<<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.b.p, h.x.p, h.r.p, h.partial.p, h.counter.p, h.state.p,
+                                                  h.hist.p, cond);
+    CPC_CK(cudaStreamEndCapture(cs, &g));
+    size_t nn = 0;
+    CPC_CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CPC_CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CPC_CK(cudaGraphAddNode(&wnode, g, nodes.data(), nullptr, nn, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // body: one PCG iteration
+    CPC_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const Sell& A = h.Anat;
+    k_loop_guard<<<1, 1, 0, cs>>>(cond);
+    if (fp64(h)) {
+        rec_precond_t<double>(h, which, h.r.p, h.z.p, cs);
+        k_pcg_rz<double><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.r.p, h.z.p, h.partial.p, h.counter.p, h.state.p);
+        k_pcg_p<double><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.z.p, h.p.p, h.state.p);
+    } else {
+        rec_precond_t<float>(h, which, h.r.p, h.z32.p, cs);
+        k_pcg_rz<float><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.r.p, h.z32.p, h.partial.p, h.counter.p, h.state.p);
+        k_pcg_p<float><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.z32.p, h.p.p, h.state.p);
+    }
+    k_pcg_spmv<<<std::min(blocks_for_chunks(A.nchunks), NPART), SELL_TPB, 0, cs>>>(
+        view(A, A.val.p, A.diag.p), A.nchunks, h.p.p, h.q.p, h.partial.p, h.counter.p, h.state.p);
+    k_pcg_update<<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.x.p, h.r.p, h.p.p, h.q.p, h.partial.p, h.counter.p, h.state.p,
+                                                    h.hist.p, HIST_CAP, cond);
+    CPC_CK(cudaStreamEndCapture(cs, &body));
+    CPC_LAUNCH_CK();
+    size_t nb = 0;
+    CPC_CK(cudaGraphGetNodes(body, nullptr, &nb));
+    h.body_nodes[which] = (int64_t)nb;
+    cudaGraphExec_t ge;
+    CPC_CK(cudaGraphInstantiate(&ge, g, 0));
+    h.graph[which] = g;
+    h.gexec[which] = ge;
+}
+
+void ensure_solve_graph(Handle& h, int which) {
+    check_which(which);
+    if (!h.gexec[which]) build_solve_graph(h, which);
+}
+
+void solve_pcg(Handle& h, const double* b, double* x, double tol, int maxit, int* iters, double* res_hist,
+               int hist_cap, int* status) {
+    const int which = h.opt.precond;
+    check_which(which);
+    if (!h.gexec[which]) build_solve_graph(h, which);
+    cudaStream_t s = h.s;
+    const int n = h.n;
+    // parameters for this run, then the graph
+    PcgState init{};
+    init.tol = tol;
+    init.maxit = maxit;
+    CPC_CK(cudaMemcpyAsync(h.state.p, &init, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    CPC_CK(cudaMemcpyAsync(h.b.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CPC_CK(cudaGraphLaunch(h.gexec[which], s));
+    CPC_CK(cudaMemcpyAsync(x, h.x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    PcgState out{};
+    CPC_CK(cudaMemcpyAsync(&out, h.state.p, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    CPC_CK(cudaStreamSynchronize(s));
+    *iters = out.k;
+    *status = out.status;
+    if (res_hist && hist_cap > 0) {
+        const int cnt = std::min(std::min(hist_cap, out.k + 1), HIST_CAP);
+        CPC_CK(cudaMemcpy(res_hist, h.hist.p, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+    }
+}
+
+}  // namespace cpc

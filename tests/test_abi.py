@@ -1,0 +1,75 @@
+"""The C ABI: the library builds for sm_103a, loads, and exports every entry point of include/cpc.h."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(cpc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1205_6113_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cpc_setup", "cpc_solve", "cpc_apply_Bcom", "cpc_destroy", "cpc_last_error",
+                     "cpc_tpfa_assemble", "cpc_solve_host"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_1205_6113_gb300 import cpc
+    bound = {name for name, _, _ in cpc.SIGNATURES}
+    assert declared_functions() <= bound
+
+
+def test_pure_host_entry_points(lib):
+    """Entry points that need no GPU: option defaults, sizes and argument validation."""
+    from paper_1205_6113_gb300 import cpc
+    L = cpc.load()
+    opt = cpc._Options()
+    assert L.cpc_default_options(ctypes.byref(opt)) == 0
+    assert opt.precond == 0 and opt.theta == 0.25 and opt.coarse_max == 256 and opt.max_levels == 20
+    assert L.cpc_default_options(None) == 1
+    assert L.cpc_tpfa_nnz(128, 128, 64) == 7274496
+    assert L.cpc_tpfa_nnz(256, 256, 128) == 58458112
+    assert L.cpc_tpfa_nnz(64, 64, 1) == 20224
+    h = ctypes.c_void_p()
+    assert L.cpc_setup(None, None, ctypes.byref(h)) == 1 and not h.value
+    assert L.cpc_solve(None, None, None, 1e-6, 10, None, None, 0) == 1
+    L.cpc_destroy(None)
+
+
+def test_cuda_path_has_no_cpu_fallback():
+    """The binding raises when the library is absent; it never computes on the host."""
+    from paper_1205_6113_gb300 import cpc
+    src = open(cpc.__file__).read()
+    assert "import oracle" not in src and "from oracle" not in src
+    with pytest.raises(cpc.CpcError):
+        saved = cpc._lib
+        cpc._lib = None
+        try:
+            cpc.load(os.path.join(ROOT, "does-not-exist.so"))
+        finally:
+            cpc._lib = saved

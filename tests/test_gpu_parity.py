@@ -1,0 +1,249 @@
+"""GPU (CUDA, through the C ABI) against the CPU oracle, element by element.
+
+Tolerances: structural choices (C/F splitting, colouring, sparsity patterns) must be
+identical; FP64 matrix values agree to 1e-12 relative (same formulas, summation in the
+same order; only rounding of fused multiply-adds differs); operator applications to
+1e-11; PCG solutions run to tol 1e-10 agree to 1e-8 relative with iteration counts
+within +-2 (spec parity gate), and every GPU solve reaches its tolerance on the
+true FP64 residual.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1205_6113_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1205_6113_gb300 import cpc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def gpu_matrix(p):
+    logk = torch.tensor(p.logk, device=DEV)
+    return cpc.tpfa_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+
+
+PROBLEMS = {
+    "lognormal2d_64x64": lambda: inputs.lognormal_2d(),
+    "small3d_13x11x7": lambda: inputs.small_3d(13, 11, 7, seed=21),
+    "small3d_33x17x9": lambda: inputs.small_3d(33, 17, 9, seed=22),
+    "channels_40x36x10": lambda: inputs.channel_facies(40, 36, 10, seed=23),
+}
+
+
+@pytest.fixture(scope="module", params=list(PROBLEMS))
+def case(request):
+    p = PROBLEMS[request.param]()
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=64)
+    # the GPU handle is built from the oracle's CSR (host) so that both start from the same bits
+    solver = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=64)
+    return p, A, orc, solver
+
+
+def test_tpfa_assembly_matches_oracle(case):
+    p, A, _, _ = case
+    rowptr, col, val = gpu_matrix(p)
+    assert np.array_equal(rowptr.cpu().numpy(), A.rowptr)
+    assert np.array_equal(col.cpu().numpy(), A.col)
+    assert rel(val.cpu().numpy(), A.val) < 1e-14
+
+
+def test_tpfa_full_size_1m():
+    p = inputs.correlated_3d()
+    A = O.tpfa_problem(p)
+    rowptr, col, val = gpu_matrix(p)
+    assert np.array_equal(rowptr.cpu().numpy(), A.rowptr)
+    assert np.array_equal(col.cpu().numpy(), A.col)
+    assert rel(val.cpu().numpy(), A.val) < 1e-14
+
+
+def test_hierarchy_matches_oracle(case):
+    _, A, orc, s = case
+    assert s.nlevels == orc.nlevels
+    for l in range(orc.nlevels):
+        ptr, col, val = s.level_matrix(l)
+        Ao = orc.level_A(l)
+        assert np.array_equal(ptr, Ao.rowptr), l
+        assert np.array_equal(col, Ao.col), l
+        assert rel(val, Ao.val) < 1e-12, l
+        if l + 1 < orc.nlevels:
+            cf, colour = s.level_splitting(l)
+            cfo, colo = orc.level_cf_colour(l)
+            assert np.array_equal(cf, cfo), l
+            assert np.array_equal(colour, colo), l
+            pp, pc, pv = s.level_interp(l)
+            Po = orc.level_P(l)
+            assert np.array_equal(pp, Po.rowptr) and np.array_equal(pc, Po.col), l
+            assert rel(pv, Po.val) < 1e-13, l
+
+
+def test_ic0_factor_matches_oracle(case):
+    _, _, orc, s = case
+    assert rel(s.ic0_values(), orc.ic0_values()) < 1e-13
+
+
+def test_level_operators_match_oracle(case):
+    _, _, orc, s = case
+    for l in range(orc.nlevels):
+        n = orc.level_sizes(l)["n"]
+        x = inputs.random_vector(n, seed=100 + l)
+        xd = torch.tensor(x, device=DEV)
+        last = l == orc.nlevels - 1
+        ops = [3] if last else [0, 1, 2, 4]
+        if last and l == 0:
+            ops = [0, 3, 4]
+        for op in ops:
+            y = s.level_apply(l, op, xd).cpu().numpy()
+            assert rel(y, orc.level_apply(l, op, x)) < 1e-11, (l, op)
+
+
+@pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT)])
+def test_preconditioner_matches_oracle(case, which, op):
+    _, A, orc, s = case
+    r = inputs.random_vector(A.n, seed=7)
+    z = s.apply(torch.tensor(r, device=DEV), which=which).cpu().numpy()
+    assert rel(z, orc.apply(op, r)) < 1e-11
+
+
+@pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT)])
+def test_pcg_matches_oracle(case, which, op):
+    p, A, orc, _ = case
+    s = cpc.Solver(A.rowptr, A.col, A.val, precond=which, coarse_max=64)
+    b = p.rhs()
+    ref = orc.pcg(b, op=op, tol=1e-10, maxit=3000)
+    x, iters, status, hist = s.solve(torch.tensor(b, device=DEV), tol=1e-10, maxit=3000)
+    x = x.cpu().numpy()
+    assert status == 0 and ref["status"] == 0
+    assert abs(iters - ref["iters"]) <= 2
+    assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+    assert np.linalg.norm(b - A.matvec(x)) / np.linalg.norm(b) <= 1e-9
+    assert hist[0] == 1.0 and hist[-1] < 1e-10
+    # the first residuals agree tightly; later ones drift with rounding (CG amplifies it), so
+    # only their order of magnitude is compared
+    n = min(len(hist), len(ref["res_hist"]))
+    m = min(n, 8)
+    assert np.allclose(hist[:m], ref["res_hist"][:m], rtol=1e-8, atol=1e-15)
+    assert np.all(np.abs(np.log10(hist[:n] / ref["res_hist"][:n])) < 0.5)
+
+
+def test_pcg_tol_1e6_iteration_counts(case):
+    p, A, orc, s = case
+    b = p.rhs()
+    ref = orc.pcg(b, op=O.BCO, tol=1e-6, maxit=3000)
+    x, iters, status, _ = s.solve(torch.tensor(b, device=DEV), tol=1e-6, maxit=3000)
+    assert status == 0
+    assert abs(iters - ref["iters"]) <= 2
+    x = x.cpu().numpy()
+    assert np.linalg.norm(b - A.matvec(x)) / np.linalg.norm(b) <= 1e-6 * 1.0001
+
+
+def test_spmv_matches_oracle(case):
+    _, A, orc, s = case
+    x = inputs.random_vector(A.n, seed=3)
+    y = s.spmv(torch.tensor(x, device=DEV)).cpu().numpy()
+    assert rel(y, orc.apply(O.A, x)) < 1e-13
+
+
+# ------------------------------------------------------------------------------------------------
+# Edge cases
+# ------------------------------------------------------------------------------------------------
+def test_single_level_and_ragged_sizes():
+    for shape in [(5, 3, 2), (7, 5, 3), (31, 1, 1), (33, 1, 1)]:
+        p = inputs.small_3d(*shape, seed=4)
+        A = O.tpfa_problem(p)
+        orc = O.Oracle(A, coarse_max=40)
+        s = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=40)
+        assert s.nlevels == orc.nlevels
+        b = inputs.random_vector(A.n, seed=5)
+        ref = orc.pcg(b, op=O.BCO, tol=1e-12, maxit=200)
+        x, iters, status, _ = s.solve(torch.tensor(b, device=DEV), tol=1e-12, maxit=200)
+        assert status == 0 and abs(iters - ref["iters"]) <= 2
+        assert np.linalg.norm(x.cpu().numpy() - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+
+
+def test_zero_rhs_and_maxit():
+    p = inputs.small_3d(9, 8, 6, seed=1)
+    A = O.tpfa_problem(p)
+    s = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=20)
+    x, iters, status, hist = s.solve(torch.zeros(A.n, dtype=torch.float64, device=DEV), tol=1e-6)
+    assert status == 0 and iters == 0 and not x.cpu().numpy().any()
+    x, iters, status, hist = s.solve(torch.tensor(p.rhs(), device=DEV), tol=1e-14, maxit=2)
+    assert status == 3 and iters == 2 and len(hist) == 3
+
+
+def test_nan_rhs_is_breakdown():
+    p = inputs.small_3d(9, 8, 6, seed=1)
+    A = O.tpfa_problem(p)
+    s = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=20)
+    b = p.rhs()
+    b[5] = np.nan
+    _, iters, status, _ = s.solve(torch.tensor(b, device=DEV), tol=1e-6)
+    assert status == 4
+
+
+def test_invalid_csr_and_breakdown_codes():
+    with pytest.raises(cpc.CpcError) as e:
+        cpc.Solver(np.array([0, 2, 3]), np.array([1, 0, 1]), np.array([1.0, 2.0, 1.0]))
+    assert e.value.code == 1
+    with pytest.raises(cpc.CpcError) as e:      # second IC(0) pivot is 1 - 4 < 0
+        cpc.Solver(np.array([0, 2, 4]), np.array([0, 1, 0, 1]), np.array([1.0, 2.0, 2.0, 1.0]))
+    assert e.value.code == 2
+    with pytest.raises(cpc.CpcError) as e:      # structurally unsymmetric
+        cpc.Solver(np.array([0, 2, 3, 4]), np.array([0, 1, 1, 2]), np.array([4.0, -1.0, 4.0, 4.0]), coarse_max=1)
+    assert e.value.code == 1
+
+
+# ------------------------------------------------------------------------------------------------
+# Mixed precision: the preconditioner in FP32 (and BF16 coarse operators), outer PCG in FP64
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp32_bf16"])
+def test_mixed_precision_solution(case, precision):
+    p, A, orc, _ = case
+    s = cpc.Solver(A.rowptr, A.col, A.val, precision=precision, coarse_max=64)
+    b = p.rhs()
+    ref = orc.pcg(b, op=O.BCO, tol=1e-10, maxit=3000)
+    x, iters, status, _ = s.solve(torch.tensor(b, device=DEV), tol=1e-10, maxit=3000)
+    assert status == 0
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-5
+    assert np.linalg.norm(b - A.matvec(x)) / np.linalg.norm(b) <= 1e-9
+    assert iters <= ref["iters"] + 5
+
+
+def test_mixed_precision_preconditioner_close(case):
+    _, A, orc, _ = case
+    s = cpc.Solver(A.rowptr, A.col, A.val, precision="fp32", coarse_max=64)
+    r = inputs.random_vector(A.n, seed=8)
+    z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    assert rel(z, orc.apply(O.BCO, r)) < 1e-4
+
+
+def test_colour_ordered_ic0(case):
+    p, A, _, _ = case
+    orc = O.Oracle(A, coarse_max=64, ic_colour_order=True)
+    s = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=64, ic_order="colour")
+    assert rel(s.ic0_values(), orc.ic0_values()) < 1e-13
+    r = inputs.random_vector(A.n, seed=9)
+    z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    assert rel(z, orc.apply(O.BCO, r)) < 1e-11
+
+
+def test_host_buffers_solve(case):
+    p, A, orc, s = case
+    b = p.rhs()
+    x = np.zeros(A.n)
+    iters, status = s.solve_host(b, x, tol=1e-10, maxit=3000)
+    ref = orc.pcg(b, op=O.BCO, tol=1e-10, maxit=3000)
+    assert status == 0 and abs(iters - ref["iters"]) <= 2
+    assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
