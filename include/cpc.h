@@ -96,6 +96,24 @@ int cpc_tpfa_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, do
                       void* stream);
 
 /*
+ * Same result as cpc_tpfa_assemble (identical rowptr, colidx and vals) without allocating any
+ * device memory: for callers that cannot call cudaMalloc or cudaMallocAsync inside a library
+ * call, such as simulators that own every device allocation through their own pool, or loops
+ * that cannot take an allocation's synchronisation.  The paper has no counterpart; this is a
+ * deployment variant of the assembly above.
+ * Scratch: a 64 KiB array inside the library image (one int per block of 1024 cells), held by
+ * every GPU that loads the library until the process exits.  Grids of more than 16,777,216 cells
+ * (nx * ny * nz) are rejected with CPC_EINVAL.  The first call on each device looks up the
+ * array's device address with that device current; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents (every call rewrites
+ * what it reads), so calls whose work overlaps on the GPU race: order them on one stream.
+ * Returns CPC_OK, CPC_EINVAL or CPC_ECUDA.  Asynchronous on `stream`.
+ */
+int cpc_tpfa_assemble_noalloc(int32_t nx, int32_t ny, int32_t nz, const double* logk,
+                              double kz_ratio, int32_t dirichlet_mask, int32_t* rowptr,
+                              int32_t* colidx, double* vals, void* stream);
+
+/*
  * Build the solver for A: IC(0) factorisation (Algorithm 3.1, k = 0) and the AMG hierarchy
  * A_l = P_l^T A_{l+1} P_l (Section 3.2), both on the GPU.  On success *out owns all device
  * memory it needs; release it with cpc_destroy.  On failure *out is NULL and the return code

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("cpc_default_options", _I32, [_P]),
     ("cpc_tpfa_nnz", _I64, [_I32, _I32, _I32]),
     ("cpc_tpfa_assemble", _I32, [_I32, _I32, _I32, _P, _F64, _I32, _P, _P, _P, _P]),
+    ("cpc_tpfa_assemble_noalloc", _I32, [_I32, _I32, _I32, _P, _F64, _I32, _P, _P, _P, _P]),
     ("cpc_setup", _I32, [_P, _P, _P]),
     ("cpc_destroy", None, [_P]),
     ("cpc_last_error", ctypes.c_char_p, [_P]),
@@ -123,6 +124,16 @@ def tpfa_assemble(nx, ny, nz, logk, kz_ratio, dirichlet_mask, stream=None):
                                     _dptr(rowptr, torch.int32), _dptr(col, torch.int32),
                                     _dptr(val, torch.float64), _stream_ptr(stream)))
     return rowptr, col, val
+
+
+def tpfa_assemble_noalloc(nx, ny, nz, logk, kz_ratio, dirichlet_mask, rowptr, col, val, stream=None):
+    """As tpfa_assemble, into caller-provided device tensors, with no device allocation inside
+    the library (cpc_tpfa_assemble_noalloc).  Returns the C status code."""
+    torch = _torch()
+    return int(load().cpc_tpfa_assemble_noalloc(nx, ny, nz, _dptr(logk, torch.float64), float(kz_ratio),
+                                                int(dirichlet_mask), _dptr(rowptr, torch.int32),
+                                                _dptr(col, torch.int32), _dptr(val, torch.float64),
+                                                _stream_ptr(stream)))
 
 
 class Solver:
