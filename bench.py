@@ -180,7 +180,7 @@ def gpu_arm(args, rank, world):
     # headline arm: B_co, FP64
     setups = {}
     t = time.perf_counter()
-    s_bco = cpc.Solver(rowptr, col, val, precond="bco", precision="fp64")
+    s_bco = cpc.Solver(rowptr, col, val, precond="bco", precision="fp64", ic_order="colour")
     setups["bco_fp64"] = dict(zip(("ic0_ms", "amg_ms"), s_bco.setup_time_ms()))
     setups["bco_fp64"]["wall_ms"] = (time.perf_counter() - t) * 1e3
     clocks = ClockSampler(torch.cuda.current_device())
@@ -207,16 +207,22 @@ def gpu_arm(args, rank, world):
 
     # comparison arms (fewer steps: AMG-alone and IC(0)-alone)
     arms = {}
-    for name, pre, prec, k in [("amg_fp64", "amg", "fp64", args.steps), ("ic0_fp64", "ic0", "fp64", 2),
-                               ("bco_fp32", "bco", "fp32", args.steps), ("bco_fp32_bf16", "bco", "fp32_bf16", args.steps),
-                               ("amg_fp32", "amg", "fp32", args.steps)]:
-        if world > 1 and name != "bco_fp32":
+    for name, pre, prec, ico, k in [
+            ("amg_fp64", "amg", "fp64", "natural", args.steps),
+            ("ic0_fp64", "ic0", "fp64", "natural", 2),
+            ("ic0_rbic_fp64", "ic0", "fp64", "colour", 2),
+            ("bco_natic_fp64", "bco", "fp64", "natural", args.steps),
+            ("bhat_fp64", "bhat", "fp64", "colour", args.steps),
+            ("bco_fp32", "bco", "fp32", "colour", args.steps),
+            ("bco_fp32_bf16", "bco", "fp32_bf16", "colour", args.steps),
+            ("amg_fp32", "amg", "fp32", "natural", args.steps)]:
+        if world > 1:
             continue
         t = time.perf_counter()
-        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec)
+        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order=ico)
         setup = dict(zip(("ic0_ms", "amg_ms"), s.setup_time_ms()))
         setup["wall_ms"] = (time.perf_counter() - t) * 1e3
-        m, it, _ = time_solves(s, k, 1 if name == "ic0_fp64" else args.warmup)
+        m, it, _ = time_solves(s, k, 1 if name.startswith("ic0") else args.warmup)
         x, _, _, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
         xr = x.cpu().numpy()
         arms[name] = dict(ms=round(float(np.mean(m)), 3), iters=int(it[-1]), setup=setup,
@@ -352,7 +358,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": p.n, "nnz": int(out["levels"][0]["nnz"]), "precond": "B_co",
-                   "precision": "fp64", "tol": TOL, "iters": iters, "levels": out["nlevels"],
+                   "precision": "fp64", "ic_order": "red-black (2-colour)", "tol": TOL, "iters": iters, "levels": out["nlevels"],
                    "l2": "flushed (512 MiB write) before every timed solve",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": round(float(np.mean(out["e2e_ms"])), 3), "unit": "ms",

@@ -73,6 +73,8 @@ typedef struct {
     double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
     int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (256)         */
     int32_t max_levels;     /* at most this many levels                            (20)          */
+    int64_t tail_nnz_max;   /* coarse levels with at most this many nonzeros run as one cluster
+                               kernel; larger levels as separate launches; 0 = library default    */
     void* stream;           /* cudaStream_t used by every call on the handle       (NULL)        */
 } cpc_options;
 

@@ -234,9 +234,11 @@ Csr permute_sym(const Csr& A, const vector<int>& order) {   // order[new] = old
 //             C point: P_{i,c(i)} = 1; coarse points numbered in ascending fine index;
 //  Galerkin   A_c = R (A P) with R = P^T (explicit transpose);
 //  stop       n_l <= coarse_max, max_levels reached, or no coarsening; coarsest solved exactly;
-//  colouring  Jones-Plassmann on the pattern of A_l: each round, uncoloured points whose
-//             fmix32(i ^ COLOUR_SEED) beats all uncoloured neighbours take the smallest colour
-//             unused by their coloured neighbours.
+//  colouring  if the pattern graph of A_l is bipartite: breadth-first parity from the smallest
+//             index of each component (red-black on a structured grid); otherwise
+//             Jones-Plassmann: each round, uncoloured points whose fmix32(i ^ COLOUR_SEED) beats
+//             all uncoloured neighbours take the smallest colour unused by their coloured
+//             neighbours.
 // ---------------------------------------------------------------------------------------------
 struct Level {
     Csr A, P, R;
@@ -343,8 +345,44 @@ Csr direct_interpolation(const Csr& A, const Csr& S, const vector<int>& cf, int&
     return P;
 }
 
+// Two-colouring by breadth-first parity: each connected component of the pattern graph is
+// searched from its smallest index, colour = distance mod 2.  Returns false (colour undefined)
+// if some edge joins two vertices of equal parity, i.e. the graph is not bipartite.
+bool colour_bipartite(const Csr& A, vector<int>& colour) {
+    const int n = A.n;
+    colour.assign(n, -1);
+    vector<int> queue;
+    for (int root = 0; root < n; ++root) {
+        if (colour[root] >= 0) continue;
+        colour[root] = 0;
+        queue.assign(1, root);
+        for (size_t h = 0; h < queue.size(); ++h) {
+            const int i = queue[h];
+            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+                const int j = A.col[p];
+                if (j == i) continue;
+                if (colour[j] < 0) { colour[j] = colour[i] ^ 1; queue.push_back(j); }
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+            if (A.col[p] != i && colour[A.col[p]] == colour[i]) return false;
+    return true;
+}
+
+// Smoothing colours of a level: the breadth-first 2-colouring when the graph is bipartite (the
+// red-black colouring of a structured grid), otherwise Jones-Plassmann.
 void colour_jp(const Csr& A, vector<int>& colour, int& ncol, vector<int>& order) {
     const int n = A.n;
+    if (colour_bipartite(A, colour)) {
+        ncol = 0;
+        for (int i = 0; i < n; ++i) ncol = std::max(ncol, colour[i] + 1);
+        order.clear();
+        for (int c = 0; c < ncol; ++c)
+            for (int i = 0; i < n; ++i) if (colour[i] == c) order.push_back(i);
+        return;
+    }
     colour.assign(n, -1);
     vector<int> sel;
     vector<char> used;
@@ -416,7 +454,7 @@ void dense_cholesky_solve(const vector<double>& L, int n, const double* f, doubl
     }
 }
 
-const int DENSE_MAX = 8192;
+const int DENSE_MAX = 4096;
 
 // Returns 0 on success, 7 if the coarsest level is too large for the dense solve or not SPD.
 int amg_setup(const Csr& A0, double theta, int coarse_max, int max_levels, Hierarchy& H) {

@@ -36,7 +36,7 @@ class _Csr(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("ic_order", ctypes.c_int32),
                 ("theta", ctypes.c_double), ("coarse_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("tail_nnz_max", ctypes.c_int64), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -144,7 +144,7 @@ class Solver:
     """
 
     def __init__(self, rowptr, col, val, precond="bco", precision="fp64", ic_order="natural", theta=0.25,
-                 coarse_max=256, max_levels=20, stream=None):
+                 coarse_max=256, max_levels=20, tail_nnz_max=0, stream=None):
         torch = _torch()
         lib = load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -167,6 +167,7 @@ class Solver:
         opt.theta = float(theta)
         opt.coarse_max = int(coarse_max)
         opt.max_levels = int(max_levels)
+        opt.tail_nnz_max = int(tail_nnz_max)
         opt.stream = ctypes.c_void_p(self.stream.cuda_stream)
         h = ctypes.c_void_p()
         _check(lib.cpc_setup(ctypes.byref(csr), ctypes.byref(opt), ctypes.byref(h)))

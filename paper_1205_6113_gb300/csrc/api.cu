@@ -51,6 +51,7 @@ int cpc_default_options(cpc_options* opt) {
     opt->theta = 0.25;
     opt->coarse_max = 256;
     opt->max_levels = 20;
+    opt->tail_nnz_max = 0;
     opt->stream = nullptr;
     return CPC_OK;
 }

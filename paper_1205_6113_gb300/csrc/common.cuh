@@ -87,14 +87,16 @@ struct Csr {
 // Value storage types of the preconditioner data.
 enum VType { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2 };
 
-// SELL-C (C = 32) storage of a set of matrix rows in a chosen slot order.
-//   slot s holds row perm[s] (or -1 for padding); chunk k = slots [32k, 32k+32) is processed by
-//   one warp, one row per lane; its entries live in val/col[cptr[k] + w*32 + lane], w < width.
+// SELL-C storage of a set of matrix rows in a chosen slot order (C in {32, 16, 8, 4}).
+//   slot s holds row perm[s] (or -1 for padding); chunk k = slots [Ck, Ck+C) is processed by one
+//   warp with G = 32/C lanes per row; entry w of the row in slot Ck + r lives at
+//   val/col[cptr[k] + w*C + r], so that every warp-wide load covers 32 consecutive elements.
 //   With split_diag the diagonal is kept apart in diag[s] and val/col hold off-diagonals only.
 //   Padding entries have val 0 and col = -1; kernels skip them (no load is issued).
 //   seg[] (host) gives chunk ranges: segment g is chunks [seg[g], seg[g+1]) -- a colour of a
 //   Gauss-Seidel sweep or a level of a triangular solve.
 struct Sell {
+    int C = 32;                        // chunk height (rows per warp); 32 / C lanes share a row
     int nslots = 0, nchunks = 0;
     int64_t nelem = 0;
     DBuf<int> perm, cptr, col;
@@ -102,16 +104,6 @@ struct Sell {
     DBuf<float> val32, diag32;         // FP32 copy (mixed precision)
     DBuf<__nv_bfloat16> val16;         // BF16 copy of off-diagonals (coarse levels, mode 2)
     std::vector<int> seg;
-};
-
-// Kernel-side view of a SELL matrix in value type MT.
-template <class MT>
-struct SellView {
-    const int* perm;
-    const int* cptr;
-    const int* col;
-    const MT* val;
-    const MT* diag;
 };
 
 }  // namespace cpc

@@ -64,6 +64,11 @@ struct Handle {
     cudaGraph_t graph[NPRECOND] = {};
     cudaGraphExec_t gexec[NPRECOND] = {};
     int64_t body_nodes[NPRECOND] = {};
+    // coarse levels >= tail_start run as one cluster kernel (tail.cu)
+    int tail_start = 0;
+    int tail_cluster = 0;
+    DBuf<char> tail_desc;
+    std::vector<DBuf<int>> tail_seg;
     float ms_ic0 = 0.f, ms_amg = 0.f;
     std::string err;
     ~Handle();
@@ -73,6 +78,11 @@ struct Handle {
 void tpfa_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask, int* rowptr,
                    int* col, double* val, cudaStream_t s);
 void setup_handle(Handle& h, const cpc_csr& A);
+
+// tail.cu
+constexpr int64_t TAIL_NNZ_MAX = 1;            // default: only the coarsest solve runs in the cluster kernel
+void setup_tail(Handle& h, int64_t tail_nnz_max);
+void record_tail(Handle& h, int level, const void* f0, void* x0, cudaStream_t s);
 
 // solve.cu
 void record_precond(Handle& h, int which, const double* r, void* z, cudaStream_t s);

@@ -6,7 +6,9 @@
 //   IC(0)   Algorithm 3.1 with k = 0 in IKJ form, rows factored level by level of the lower DAG;
 //   AMG     strength theta, PMIS splitting with weight (|S^T_i|, fmix32(i)), direct
 //           interpolation, R = P^T, Galerkin A_c = R (A P) (Section 3.2);
-//   colour  Jones-Plassmann with weight fmix32(i ^ 0x5bd1e995), smallest free colour.
+//   colour  breadth-first parity 2-colouring when the level graph is bipartite (red-black on a
+//           structured grid), else Jones-Plassmann with weight fmix32(i ^ 0x5bd1e995) and the
+//           smallest free colour.
 // Sums that define matrix entries are accumulated in a fixed order (the order the products are
 // generated in), so results do not depend on thread scheduling.
 #include <cub/cub.cuh>
@@ -445,6 +447,32 @@ __global__ void k_jp_assign(int n, const int* ptr, const int* col, const uint8_t
     atomicAdd(done, 1);
 }
 
+// Breadth-first parity 2-colouring, propagated: every vertex adopts the smallest (root, parity^1)
+// offered by a neighbour; at the fixed point root = smallest index of the component and, for a
+// bipartite graph, parity = distance parity from it.  Jacobi-style rounds (old -> new arrays).
+__global__ void k_bip_round(int n, const int* ptr, const int* col, const int* root, const int* par,
+                            int* root2, int* par2, int* changed) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = root[i], q = par[i];
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int j = col[p];
+        if (j == i) continue;
+        const int rj = root[j];
+        if (rj < r) { r = rj; q = par[j] ^ 1; }
+    }
+    root2[i] = r;
+    par2[i] = q;
+    if (r != root[i]) atomicAdd(changed, 1);
+}
+
+__global__ void k_bip_check(int n, const int* ptr, const int* col, const int* par, int* bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p)
+        if (col[p] != i && par[col[p]] == par[i]) { atomicOr(bad, 1); return; }
+}
+
 // ============================================================================================
 // IC(0): level scheduling and factorisation (Algorithm 3.1, k = 0)
 // ============================================================================================
@@ -535,31 +563,32 @@ __device__ __forceinline__ bool sell_keep(int mode, int j, int i) {
     }
 }
 
-__global__ void k_sell_width(const int* perm, int nchunks, const int* ptr, const int* col, int mode, int* width) {
+__global__ void k_sell_width(const int* perm, int nchunks, int C, const int* ptr, const int* col, int mode,
+                             int* width) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k > nchunks) return;
     if (k == nchunks) { width[k] = 0; return; }
     int w = 0;
-    for (int l = 0; l < CHUNK; ++l) {
-        const int i = perm[k * CHUNK + l];
+    for (int l = 0; l < C; ++l) {
+        const int i = perm[k * C + l];
         if (i < 0) continue;
         int c = 0;
         for (int p = ptr[i]; p < ptr[i + 1]; ++p) c += sell_keep(mode, col[p], i) ? 1 : 0;
         w = max(w, c);
     }
-    width[k] = w * CHUNK;
+    width[k] = w * C;
 }
 
 // Slots refer to rows of the CSR; imap (optional) renames rows and columns on output
 // (IC factor stored in its own ordering but applied to naturally ordered vectors).
-__global__ void k_sell_fill(const int* perm, int nslots, const int* ptr, const int* col, const double* val,
+__global__ void k_sell_fill(const int* perm, int nslots, int C, const int* ptr, const int* col, const double* val,
                             int mode, const int* cptr, const int* imap, int* perm_out, int* scol, double* sval,
                             double* sdiag) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslots) return;
-    const int k = s / CHUNK, lane = s % CHUNK;
+    const int k = s / C, lane = s % C;
     const int base = cptr[k];
-    const int w = (cptr[k + 1] - base) / CHUNK;
+    const int w = (cptr[k + 1] - base) / C;
     const int i = perm[s];
     const int out_row = i < 0 ? -1 : (imap ? imap[i] : i);
     perm_out[s] = out_row;
@@ -570,21 +599,21 @@ __global__ void k_sell_fill(const int* perm, int nslots, const int* ptr, const i
             const int j = col[p];
             if (j == i) d = val[p];
             if (sell_keep(mode, j, i)) {
-                scol[base + e * CHUNK + lane] = imap ? imap[j] : j;
-                sval[base + e * CHUNK + lane] = val[p];
+                scol[base + e * C + lane] = imap ? imap[j] : j;
+                sval[base + e * C + lane] = val[p];
                 ++e;
             }
         }
     }
     for (; e < w; ++e) {                       // padding: column -1, skipped by every kernel
-        scol[base + e * CHUNK + lane] = -1;
-        sval[base + e * CHUNK + lane] = 0.0;
+        scol[base + e * C + lane] = -1;
+        sval[base + e * C + lane] = 0.0;
     }
     if (sdiag) sdiag[s] = d;
 }
 
 // Slot order from a per-row group key (colour or level): rows sorted by (key, row), each group
-// padded to a multiple of CHUNK.  Returns the chunk boundaries of the groups in seg.
+// padded to a multiple of the chunk height C.  Returns the chunk boundaries of the groups in seg.
 __global__ void k_group_count(int n, const int* key, int* cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(&cnt[key[i]], 1);
@@ -599,7 +628,7 @@ __global__ void k_group_scatter(int n, const int* skey, const int* srow, const i
 }
 
 // Build perm (device, nslots) from a group key per row; ngroups known.
-void grouped_slots(int n, const int* key, int ngroups, cudaStream_t s, DBuf<int>& perm, int& nslots,
+void grouped_slots(int n, const int* key, int ngroups, int C, cudaStream_t s, DBuf<int>& perm, int& nslots,
                    std::vector<int>& seg, DBuf<int>* sorted_rows = nullptr) {
     Tmp<int> rows(n, s), skey(n, s), srow(n, s), cnt(ngroups, s);
     k_iota<<<nblk(n), TPB, 0, s>>>(rows.get(), n);
@@ -615,11 +644,11 @@ void grouped_slots(int n, const int* key, int ngroups, cudaStream_t s, DBuf<int>
     for (int g = 0; g < ngroups; ++g) {
         gstart[g] = g0;
         sstart[g] = s0;
-        seg[g] = s0 / CHUNK;
+        seg[g] = s0 / C;
         g0 += hc[g];
-        s0 += (hc[g] + CHUNK - 1) / CHUNK * CHUNK;
+        s0 += (hc[g] + C - 1) / C * C;
     }
-    seg[ngroups] = s0 / CHUNK;
+    seg[ngroups] = s0 / C;
     nslots = s0;
     perm.alloc(nslots);
     k_fill_int<<<nblk(nslots), TPB, 0, s>>>(perm.p, nslots, -1);
@@ -635,24 +664,33 @@ void grouped_slots(int n, const int* key, int ngroups, cudaStream_t s, DBuf<int>
     CPC_LAUNCH_CK();
 }
 
-void natural_slots(int n, cudaStream_t s, DBuf<int>& perm, int& nslots, std::vector<int>& seg) {
-    nslots = (n + CHUNK - 1) / CHUNK * CHUNK;
+void natural_slots(int n, int C, cudaStream_t s, DBuf<int>& perm, int& nslots, std::vector<int>& seg) {
+    nslots = (n + C - 1) / C * C;
     perm.alloc(nslots);
     k_fill_int<<<nblk(nslots), TPB, 0, s>>>(perm.p, nslots, -1);
     k_iota<<<nblk(n), TPB, 0, s>>>(perm.p, n);
-    seg = {0, nslots / CHUNK};
+    seg = {0, nslots / C};
     CPC_LAUNCH_CK();
 }
 
-// Fill a Sell from CSR rows in the slot order `slots` (device, nslots entries).
+// Chunk height for rows of average length avg: 32 / G rows per warp with G lanes sharing a row,
+// G the largest power of two <= avg / 4 (1..8), so that a row costs one round of loads.
+int choose_chunk(double avg) {
+    int G = 1;
+    while (G < 8 && 2 * G <= avg / 4.0) G *= 2;
+    return 32 / G;
+}
+
+// Fill a Sell of chunk height C from CSR rows in the slot order `slots` (device, nslots entries).
 void build_sell(const int* ptr, const int* col, const double* val, const DBuf<int>& slots, int nslots,
-                const std::vector<int>& seg, int mode, bool split_diag, const int* imap, Sell& S,
+                const std::vector<int>& seg, int C, int mode, bool split_diag, const int* imap, Sell& S,
                 cudaStream_t s) {
     S.nslots = nslots;
-    S.nchunks = nslots / CHUNK;
+    S.C = C;
+    S.nchunks = nslots / C;
     S.seg = seg;
     Tmp<int> width(S.nchunks + 1, s);
-    k_sell_width<<<nblk(S.nchunks + 1), TPB, 0, s>>>(slots.p, S.nchunks, ptr, col, mode, width.get());
+    k_sell_width<<<nblk(S.nchunks + 1), TPB, 0, s>>>(slots.p, S.nchunks, C, ptr, col, mode, width.get());
     S.cptr.alloc(S.nchunks + 1);
     exclusive_scan(width.get(), S.cptr.p, S.nchunks + 1, s);
     S.nelem = d2h(S.cptr.p + S.nchunks, s);
@@ -660,7 +698,7 @@ void build_sell(const int* ptr, const int* col, const double* val, const DBuf<in
     S.col.alloc(S.nelem);
     S.val.alloc(S.nelem);
     if (split_diag) S.diag.alloc(nslots);
-    k_sell_fill<<<nblk(nslots), TPB, 0, s>>>(slots.p, nslots, ptr, col, val, mode, S.cptr.p, imap, S.perm.p,
+    k_sell_fill<<<nblk(nslots), TPB, 0, s>>>(slots.p, nslots, C, ptr, col, val, mode, S.cptr.p, imap, S.perm.p,
                                              S.col.p, S.val.p, split_diag ? S.diag.p : nullptr);
     CPC_LAUNCH_CK();
 }
@@ -795,7 +833,7 @@ void setup_ic0(Handle& h, cudaStream_t s) {
     DBuf<int> slotsL, rowsL;
     int nslotsL = 0;
     std::vector<int> segL;
-    grouped_slots(n, lvl.get(), h.ic_levels_L, s, slotsL, nslotsL, segL, &rowsL);
+    grouped_slots(n, lvl.get(), h.ic_levels_L, CHUNK, s, slotsL, nslotsL, segL, &rowsL);
     // level g has rows rowsL[gstart..], count from segments: recompute counts from the slot layout
     std::vector<int> hc(h.ic_levels_L);
     {
@@ -819,14 +857,14 @@ void setup_ic0(Handle& h, cudaStream_t s) {
     // triangular-solve layouts: L by forward levels, U by backward levels; rows/cols renamed to the
     // original numbering when the IC ordering is a permutation
     const int* imap = h.ic_order.p;
-    build_sell(A.ptr.p, A.col.p, h.lu.p, slotsL, nslotsL, segL, SELL_LOWER, false, imap, h.L, s);
+    build_sell(A.ptr.p, A.col.p, h.lu.p, slotsL, nslotsL, segL, CHUNK, SELL_LOWER, false, imap, h.L, s);
     h.ic_levels_U = dag_levels(A, true, lvl.get(), s);
     // backward solve processes levels of the upper DAG in ascending order
     DBuf<int> slotsU;
     int nslotsU = 0;
     std::vector<int> segU;
-    grouped_slots(n, lvl.get(), h.ic_levels_U, s, slotsU, nslotsU, segU);
-    build_sell(A.ptr.p, A.col.p, h.lu.p, slotsU, nslotsU, segU, SELL_UPPER, true, imap, h.U, s);
+    grouped_slots(n, lvl.get(), h.ic_levels_U, CHUNK, s, slotsU, nslotsU, segU);
+    build_sell(A.ptr.p, A.col.p, h.lu.p, slotsU, nslotsU, segU, CHUNK, SELL_UPPER, true, imap, h.U, s);
     CPC_CK(cudaStreamSynchronize(s));
 }
 
@@ -836,20 +874,50 @@ void setup_level_sells(Level& L, cudaStream_t s, bool last) {
         DBuf<int> slots;
         int nslots = 0;
         std::vector<int> seg;
-        grouped_slots(L.n, L.colour.p, L.ncolours, s, slots, nslots, seg);
-        build_sell(L.A.ptr.p, L.A.col.p, L.A.val.p, slots, nslots, seg, SELL_OFFDIAG, true, nullptr, L.S, s);
+        const int ca = choose_chunk((double)(L.A.nnz - L.n) / std::max(1, L.n));
+        grouped_slots(L.n, L.colour.p, L.ncolours, ca, s, slots, nslots, seg);
+        build_sell(L.A.ptr.p, L.A.col.p, L.A.val.p, slots, nslots, seg, ca, SELL_OFFDIAG, true, nullptr, L.S, s);
         DBuf<int> ps;
         int pn = 0;
         std::vector<int> pseg;
-        natural_slots(L.P.n, s, ps, pn, pseg);
-        build_sell(L.P.ptr.p, L.P.col.p, L.P.val.p, ps, pn, pseg, SELL_ALL, false, nullptr, L.SP, s);
+        const int cp = choose_chunk((double)L.P.nnz / std::max(1, L.P.n));
+        natural_slots(L.P.n, cp, s, ps, pn, pseg);
+        build_sell(L.P.ptr.p, L.P.col.p, L.P.val.p, ps, pn, pseg, cp, SELL_ALL, false, nullptr, L.SP, s);
         DBuf<int> rs;
         int rn = 0;
         std::vector<int> rseg;
-        natural_slots(L.R.n, s, rs, rn, rseg);
-        build_sell(L.R.ptr.p, L.R.col.p, L.R.val.p, rs, rn, rseg, SELL_ALL, false, nullptr, L.SR, s);
+        const int cr = choose_chunk((double)L.R.nnz / std::max(1, L.R.n));
+        natural_slots(L.R.n, cr, s, rs, rn, rseg);
+        build_sell(L.R.ptr.p, L.R.col.p, L.R.val.p, rs, rn, rseg, cr, SELL_ALL, false, nullptr, L.SR, s);
         CPC_CK(cudaStreamSynchronize(s));
     }
+}
+
+// Two-colouring by propagated breadth-first parity; returns false if the graph is not bipartite.
+bool colour_bipartite(const Csr& A, int* colour, cudaStream_t s) {
+    const int n = A.n;
+    Tmp<int> r0(n, s), r1(n, s), p0(n, s), p1(n, s), changed(1, s);
+    k_iota<<<nblk(n), TPB, 0, s>>>(r0.get(), n);
+    CPC_CK(cudaMemsetAsync(p0.get(), 0, sizeof(int) * n, s));
+    int* ra = r0.get(); int* rb = r1.get(); int* pa = p0.get(); int* pb = p1.get();
+    for (int round = 0;; round += 16) {
+        CPC_CK(cudaMemsetAsync(changed.get(), 0, sizeof(int), s));
+        for (int k = 0; k < 16; ++k) {
+            k_bip_round<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, A.col.p, ra, pa, rb, pb, changed.get());
+            std::swap(ra, rb);
+            std::swap(pa, pb);
+        }
+        CPC_LAUNCH_CK();
+        if (d2h(changed.get(), s) == 0) break;
+        if (round > n + 16) fail(CPC_ESETUP, "parity propagation did not converge");
+    }
+    Tmp<int> bad(1, s);
+    CPC_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_bip_check<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, A.col.p, pa, bad.get());
+    if (d2h(bad.get(), s)) return false;
+    CPC_CK(cudaMemcpyAsync(colour, pa, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    CPC_CK(cudaStreamSynchronize(s));
+    return true;
 }
 
 // One coarsening step on level l; returns false when l becomes the coarsest level.
@@ -902,17 +970,19 @@ bool coarsen(Handle& h, int l, cudaStream_t s) {
                                           P.ptr.p, P.col.p, P.val.p);
     CPC_LAUNCH_CK();
     transpose(P, L.R, s);
-    // colouring of A_l
+    // colouring of A_l: breadth-first parity if the graph is bipartite, else Jones-Plassmann
     L.colour.alloc(n);
-    k_fill_int<<<nblk(n), TPB, 0, s>>>(L.colour.p, n, -1);
-    Tmp<int> done(1, s);
-    CPC_CK(cudaMemsetAsync(done.get(), 0, sizeof(int), s));
-    for (int round = 0;; ++round) {
-        k_jp_select<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, L.colour.p, sel.get());
-        k_jp_assign<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, sel.get(), L.colour.p, done.get());
-        CPC_LAUNCH_CK();
-        if (d2h(done.get(), s) == n) break;
-        if (round > n) fail(CPC_ESETUP, "colouring did not terminate");
+    if (!colour_bipartite(L.A, L.colour.p, s)) {
+        k_fill_int<<<nblk(n), TPB, 0, s>>>(L.colour.p, n, -1);
+        Tmp<int> done(1, s);
+        CPC_CK(cudaMemsetAsync(done.get(), 0, sizeof(int), s));
+        for (int round = 0;; ++round) {
+            k_jp_select<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, L.colour.p, sel.get());
+            k_jp_assign<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, sel.get(), L.colour.p, done.get());
+            CPC_LAUNCH_CK();
+            if (d2h(done.get(), s) == n) break;
+            if (round > n) fail(CPC_ESETUP, "colouring did not terminate");
+        }
     }
     {
         size_t tmp = 0;
@@ -1019,9 +1089,9 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         DBuf<int> slots;
         int nslots = 0;
         std::vector<int> seg;
-        natural_slots(h.n, s, slots, nslots, seg);
-        build_sell(h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, slots, nslots, seg, SELL_OFFDIAG, true,
-                   nullptr, h.Anat, s);
+        natural_slots(h.n, CHUNK, s, slots, nslots, seg);
+        build_sell(h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, slots, nslots, seg, CHUNK, SELL_OFFDIAG,
+                   true, nullptr, h.Anat, s);
         CPC_CK(cudaStreamSynchronize(s));
     }
     CPC_CK(cudaEventRecord(e2, s));
@@ -1034,7 +1104,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
             DBuf<int> slots;
             int nslots = 0;
             std::vector<int> seg;
-            grouped_slots(L0.n, L0.colour.p, L0.ncolours, s, slots, nslots, seg, &rows);
+            grouped_slots(L0.n, L0.colour.p, L0.ncolours, CHUNK, s, slots, nslots, seg, &rows);
         }
         h.ic_order = std::move(rows);
         Tmp<int> inv(L0.n, s), len(L0.n + 1, s);
@@ -1092,6 +1162,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         k_to_f32<<<nblk((int64_t)h.nc * h.nc), TPB, 0, s>>>((int64_t)h.nc * h.nc, h.Ainv.p, h.Ainv32.p);
         h.z32.alloc(h.n); h.t32.alloc(h.n); h.y32.alloc(h.n);
     }
+    setup_tail(h, h.opt.tail_nnz_max > 0 ? h.opt.tail_nnz_max : TAIL_NNZ_MAX);
     // PCG and preconditioner vectors
     const size_t n = h.n;
     h.b.alloc(n); h.x.alloc(n); h.r.alloc(n); h.z.alloc(n); h.p.alloc(n); h.q.alloc(n);

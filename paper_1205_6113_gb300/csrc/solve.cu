@@ -2,14 +2,17 @@
 // preconditioner (Algorithm 2.1) and PCG, all as sm_103a kernels; the PCG loop is one CUDA graph
 // with a device-side while node, so the host only launches it and reads back the result.
 //
-// Kernel layout: every matrix is SELL-C (C = 32): one warp per chunk of 32 rows, one row per lane,
-// entries column-major inside a chunk so that each load instruction of a warp is coalesced.
+// Kernel layout: every matrix is SELL-C (C in {32, 16, 8, 4}): one warp per chunk of C rows with
+// 32 / C lanes per row, entries column-major inside a chunk so that each load instruction of a
+// warp reads 32 consecutive elements.
 // Reductions (dot products) finish in a fixed order (per-block tree, then the last block sums the
 // block partials in index order), so iteration counts are reproducible run to run.
 #include <algorithm>
 #include <cstdio>
 #include <type_traits>
+#include <utility>
 
+#include "device.cuh"
 #include "handle.cuh"
 
 namespace cpc {
@@ -20,75 +23,63 @@ constexpr int WPB = 4;                  // warps (= SELL chunks) per block
 constexpr int SELL_TPB = WPB * 32;
 constexpr int VEC_TPB = 256;
 
-__device__ __forceinline__ double cvt_d(double v) { return v; }
-__device__ __forceinline__ double cvt_d(float v) { return (double)v; }
-__device__ __forceinline__ float cvt_f(double v) { return (float)v; }
-__device__ __forceinline__ float cvt_f(float v) { return v; }
-__device__ __forceinline__ float cvt_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <class VT> struct Cv;
-template <> struct Cv<double> {
-    template <class T> __device__ static __forceinline__ double f(T v) { return cvt_d(v); }
-};
-template <> struct Cv<float> {
-    template <class T> __device__ static __forceinline__ float f(T v) { return cvt_f(v); }
-};
-
-template <class MT, class DT>
-struct SV {       // SELL view passed by value
-    const int* __restrict__ perm;
-    const int* __restrict__ cptr;
-    const int* __restrict__ col;
-    const MT* __restrict__ val;
-    const DT* __restrict__ diag;
-};
-
-template <class MT, class DT>
-SV<MT, DT> view(const Sell& S, const MT* val, const DT* diag) {
-    return SV<MT, DT>{S.perm.p, S.cptr.p, S.col.p, val, diag};
+// Launch with programmatic stream serialisation (see pdl_wait in device.cuh).
+template <class... KArgs, class... Args>
+void launch(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)block, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CPC_CK(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
 }
 
 inline int blocks_for_chunks(int nchunks) { return std::max(1, (nchunks + WPB - 1) / WPB); }
 inline int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + VEC_TPB - 1) / VEC_TPB, NPART)); }
 
 // ---------------------------------------------------------------------------------------------
-// Level kernels
+// Level kernels.  A warp owns one chunk of A.C rows; lane l works on row l % C of the chunk with
+// G = 32 / C lanes per row (sub-lane l / C takes entries l / C, l / C + G, ...); sub_sum() adds
+// the G partial sums, after which sub-lane 0 writes the row.
 // ---------------------------------------------------------------------------------------------
+template <class VT>
+__device__ __forceinline__ VT sub_sum(VT v, int C) {
+    for (int o = C; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Gauss-Seidel over the rows of one colour (chunks [c0, c1)): x_i = (f_i - sum_{j!=i} a_ij x_j) / a_ii.
 // Rows of one colour are not coupled, so they update in parallel exactly as in sequential order.
 template <class MT, class DT, class FT, class VT>
 __global__ void __launch_bounds__(SELL_TPB) k_gs(SV<MT, DT> A, int c0, int c1, const FT* __restrict__ f, VT* x) {
     const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
     if (k >= c1) return;
-    const int lane = threadIdx.x & 31;
-    const int s = k * 32 + lane;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31, C = A.C, r = lane & (C - 1), g = lane / C;
+    const int s = k * C + r;
     const int row = A.perm[s];
-    if (row < 0) return;
-    const int b = A.cptr[k], e = A.cptr[k + 1];
-    VT acc = Cv<VT>::f(f[row]);
-    for (int o = b + lane; o < e; o += 32) {
-        const int c = A.col[o];
-        if (c >= 0) acc -= Cv<VT>::f(A.val[o]) * x[c];
-    }
-    x[row] = acc / Cv<VT>::f(A.diag[s]);
+    VT dot = sell_dot<VT, true>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], x);
+    dot = sub_sum(dot, C);
+    if (g == 0 && row >= 0) x[row] = (Cv<VT>::f(f[row]) - dot) / Cv<VT>::f(A.diag[s]);
 }
 
 // r = f - A x over all chunks (grid-stride over chunks).
 template <class MT, class DT, class FT, class XT, class RT>
 __global__ void __launch_bounds__(SELL_TPB) k_resid(SV<MT, DT> A, int nchunks, const FT* __restrict__ f,
                                                      const XT* __restrict__ x, RT* __restrict__ r) {
-    const int lane = threadIdx.x & 31;
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, C = A.C, rr = lane & (C - 1), g = lane / C;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
-        const int s = k * 32 + lane;
+        const int s = k * C + rr;
         const int row = A.perm[s];
-        if (row < 0) continue;
-        const int b = A.cptr[k], e = A.cptr[k + 1];
-        RT acc = Cv<RT>::f(f[row]) - Cv<RT>::f(A.diag[s]) * Cv<RT>::f(x[row]);
-        for (int o = b + lane; o < e; o += 32) {
-            const int c = A.col[o];
-            if (c >= 0) acc -= Cv<RT>::f(A.val[o]) * Cv<RT>::f(x[c]);
-        }
-        r[row] = acc;
+        RT dot = sell_dot<RT>(A.col, A.val, A.cptr[k] + g * C + rr, A.cptr[k + 1], x);
+        dot = sub_sum(dot, C);
+        if (g == 0 && row >= 0) r[row] = Cv<RT>::f(f[row]) - (Cv<RT>::f(A.diag[s]) * Cv<RT>::f(x[row]) + dot);
     }
 }
 
@@ -96,18 +87,15 @@ __global__ void __launch_bounds__(SELL_TPB) k_resid(SV<MT, DT> A, int nchunks, c
 template <class MT, class DT, class XT, class YT>
 __global__ void __launch_bounds__(SELL_TPB) k_spmv(SV<MT, DT> A, int nchunks, const XT* __restrict__ x,
                                                     YT* __restrict__ y) {
-    const int lane = threadIdx.x & 31;
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, C = A.C, r = lane & (C - 1), g = lane / C;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
-        const int s = k * 32 + lane;
+        const int s = k * C + r;
         const int row = A.perm[s];
-        if (row < 0) continue;
-        const int b = A.cptr[k], e = A.cptr[k + 1];
-        YT acc = Cv<YT>::f(A.diag[s]) * Cv<YT>::f(x[row]);
-        for (int o = b + lane; o < e; o += 32) {
-            const int c = A.col[o];
-            if (c >= 0) acc += Cv<YT>::f(A.val[o]) * Cv<YT>::f(x[c]);
-        }
-        y[row] = acc;
+        YT dot = sell_dot<YT>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], x);
+        dot = sub_sum(dot, C);
+        if (g == 0 && row >= 0) y[row] = Cv<YT>::f(A.diag[s]) * Cv<YT>::f(x[row]) + dot;
     }
 }
 
@@ -115,17 +103,29 @@ __global__ void __launch_bounds__(SELL_TPB) k_spmv(SV<MT, DT> A, int nchunks, co
 template <class MT, class VT>
 __global__ void __launch_bounds__(SELL_TPB) k_apply_full(SV<MT, MT> M, int nchunks, const VT* __restrict__ x,
                                                           VT* __restrict__ y) {
-    const int lane = threadIdx.x & 31;
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, C = M.C, r = lane & (C - 1), g = lane / C;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
-        const int row = M.perm[k * 32 + lane];
-        if (row < 0) continue;
-        const int b = M.cptr[k], e = M.cptr[k + 1];
-        VT acc = 0;
-        for (int o = b + lane; o < e; o += 32) {
-            const int c = M.col[o];
-            if (c >= 0) acc += Cv<VT>::f(M.val[o]) * x[c];
-        }
-        y[row] = acc;
+        const int row = M.perm[k * C + r];
+        VT dot = sell_dot<VT>(M.col, M.val, M.cptr[k] + g * C + r, M.cptr[k + 1], x);
+        dot = sub_sum(dot, C);
+        if (g == 0 && row >= 0) y[row] = dot;
+    }
+}
+
+// f_c = R r and x_c = 0 (the next level starts from a zero guess).
+template <class MT, class VT>
+__global__ void __launch_bounds__(SELL_TPB) k_restrict_zero(SV<MT, MT> M, int nchunks, const VT* __restrict__ x,
+                                                             VT* __restrict__ y, VT* __restrict__ yz) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, C = M.C, r = lane & (C - 1), g = lane / C;
+    for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
+        const int row = M.perm[k * C + r];
+        VT dot = sell_dot<VT>(M.col, M.val, M.cptr[k] + g * C + r, M.cptr[k + 1], x);
+        dot = sub_sum(dot, C);
+        if (g == 0 && row >= 0) { y[row] = dot; yz[row] = VT(0); }
     }
 }
 
@@ -133,23 +133,22 @@ __global__ void __launch_bounds__(SELL_TPB) k_apply_full(SV<MT, MT> M, int nchun
 template <class MT, class VT>
 __global__ void __launch_bounds__(SELL_TPB) k_prolong(SV<MT, MT> P, int nchunks, const VT* __restrict__ e,
                                                        VT* __restrict__ x) {
-    const int lane = threadIdx.x & 31;
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, C = P.C, r = lane & (C - 1), g = lane / C;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
-        const int row = P.perm[k * 32 + lane];
-        if (row < 0) continue;
-        const int b = P.cptr[k], en = P.cptr[k + 1];
-        VT acc = 0;
-        for (int o = b + lane; o < en; o += 32) {
-            const int c = P.col[o];
-            if (c >= 0) acc += Cv<VT>::f(P.val[o]) * e[c];
-        }
-        x[row] += acc;
+        const int row = P.perm[k * C + r];
+        VT dot = sell_dot<VT>(P.col, P.val, P.cptr[k] + g * C + r, P.cptr[k + 1], e);
+        dot = sub_sum(dot, C);
+        if (g == 0 && row >= 0) x[row] += dot;
     }
 }
 
 // x = A_c^{-1} f with the dense inverse (row-major), one warp per row.
 template <class AT, class FT, class VT>
 __global__ void k_coarse(int n, const AT* __restrict__ Ainv, const FT* __restrict__ f, VT* __restrict__ x) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += gridDim.x * (blockDim.x >> 5)) {
         VT acc = 0;
@@ -161,12 +160,16 @@ __global__ void k_coarse(int n, const AT* __restrict__ Ainv, const FT* __restric
 
 template <class VT>
 __global__ void k_zero(int64_t n, VT* x) {
+    pdl_launch_dependents();
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] = 0;
 }
 
 template <class A, class B>
 __global__ void k_copy(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
+    pdl_launch_dependents();
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (B)a[i];
 }
@@ -176,16 +179,12 @@ template <class MT, class TT, class VT>
 __global__ void __launch_bounds__(SELL_TPB) k_lsolve(SV<MT, MT> L, int c0, int c1, const TT* __restrict__ t, VT* y) {
     const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
     if (k >= c1) return;
-    const int lane = threadIdx.x & 31;
-    const int row = L.perm[k * 32 + lane];
-    if (row < 0) return;
-    const int b = L.cptr[k], e = L.cptr[k + 1];
-    VT acc = Cv<VT>::f(t[row]);
-    for (int o = b + lane; o < e; o += 32) {
-        const int c = L.col[o];
-        if (c >= 0) acc -= Cv<VT>::f(L.val[o]) * y[c];
-    }
-    y[row] = acc;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31, C = L.C, r = lane & (C - 1), g = lane / C;
+    const int row = L.perm[k * C + r];
+    VT dot = sell_dot<VT, true>(L.col, L.val, L.cptr[k] + g * C + r, L.cptr[k + 1], y);
+    dot = sub_sum(dot, C);
+    if (g == 0 && row >= 0) y[row] = Cv<VT>::f(t[row]) - dot;
 }
 
 // Backward solve with U, rows of one level: w_i = (y_i - sum_{j>i} u_ij w_j) / u_ii; optionally
@@ -195,19 +194,17 @@ __global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> U, int c0, int c
                                                       VT* zadd) {
     const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
     if (k >= c1) return;
-    const int lane = threadIdx.x & 31;
-    const int s = k * 32 + lane;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31, C = U.C, r = lane & (C - 1), g = lane / C;
+    const int s = k * C + r;
     const int row = U.perm[s];
-    if (row < 0) return;
-    const int b = U.cptr[k], e = U.cptr[k + 1];
-    VT acc = y[row];
-    for (int o = b + lane; o < e; o += 32) {
-        const int c = U.col[o];
-        if (c >= 0) acc -= Cv<VT>::f(U.val[o]) * w[c];
+    VT dot = sell_dot<VT, true>(U.col, U.val, U.cptr[k] + g * C + r, U.cptr[k + 1], w);
+    dot = sub_sum(dot, C);
+    if (g == 0 && row >= 0) {
+        const VT v = (y[row] - dot) / Cv<VT>::f(U.diag[s]);
+        w[row] = v;
+        if (zadd) zadd[row] += v;
     }
-    const VT v = acc / Cv<VT>::f(U.diag[s]);
-    w[row] = v;
-    if (zadd) zadd[row] += v;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -259,6 +256,8 @@ __device__ bool finish_sum(double v, double* part, unsigned* ctr, double* total)
 __global__ void k_pcg_init(int n, const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r,
                            double* part, unsigned* ctr, PcgState* st, double* hist,
                            cudaGraphConditionalHandle cond) {
+    pdl_launch_dependents();
+    pdl_wait();
     double v = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double bi = b[i];
@@ -285,11 +284,17 @@ __global__ void k_pcg_init(int n, const double* __restrict__ b, double* __restri
 // First node of every loop iteration: clear the loop condition.  Only the last block of
 // k_pcg_update sets it again, so the loop cannot continue past an iteration whose final
 // reduction did not complete.
-__global__ void k_loop_guard(cudaGraphConditionalHandle cond) { cudaGraphSetConditional(cond, 0u); }
+__global__ void k_loop_guard(cudaGraphConditionalHandle cond) {
+    pdl_launch_dependents();
+    pdl_wait();
+    cudaGraphSetConditional(cond, 0u);
+}
 
 template <class ZT>
 __global__ void k_pcg_rz(int n, const double* __restrict__ r, const ZT* __restrict__ z, double* part, unsigned* ctr,
                          PcgState* st) {
+    pdl_launch_dependents();
+    pdl_wait();
     double v = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         v += r[i] * cvt_d(z[i]);
@@ -304,6 +309,8 @@ __global__ void k_pcg_rz(int n, const double* __restrict__ r, const ZT* __restri
 
 template <class ZT>
 __global__ void k_pcg_p(int n, const ZT* __restrict__ z, double* __restrict__ p, const PcgState* st) {
+    pdl_launch_dependents();
+    pdl_wait();
     const double beta = st->beta;
     const bool first = st->k == 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -314,21 +321,21 @@ __global__ void k_pcg_p(int n, const ZT* __restrict__ z, double* __restrict__ p,
 __global__ void __launch_bounds__(SELL_TPB) k_pcg_spmv(SV<double, double> A, int nchunks, const double* __restrict__ p,
                                                         double* __restrict__ q, double* part, unsigned* ctr,
                                                         PcgState* st) {
-    const int lane = threadIdx.x & 31;
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, C = A.C, r = lane & (C - 1), g = lane / C;
     double v = 0.0;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
-        const int s = k * 32 + lane;
+        const int s = k * C + r;
         const int row = A.perm[s];
-        if (row < 0) continue;
-        const int b = A.cptr[k], e = A.cptr[k + 1];
-        const double pr = p[row];
-        double acc = A.diag[s] * pr;
-        for (int o = b + lane; o < e; o += 32) {
-            const int c = A.col[o];
-            if (c >= 0) acc += A.val[o] * p[c];
+        double dot = sell_dot<double>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], p);
+        dot = sub_sum(dot, C);
+        if (g == 0 && row >= 0) {
+            const double pr = p[row];
+            const double acc = A.diag[s] * pr + dot;
+            q[row] = acc;
+            v += pr * acc;
         }
-        q[row] = acc;
-        v += pr * acc;
     }
     double tot;
     if (finish_sum(v, part, ctr, &tot) && threadIdx.x == 0) {
@@ -343,6 +350,8 @@ __global__ void __launch_bounds__(SELL_TPB) k_pcg_spmv(SV<double, double> A, int
 __global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
                              const double* __restrict__ q, double* part, unsigned* ctr, PcgState* st, double* hist,
                              int hist_cap, cudaGraphConditionalHandle cond) {
+    pdl_launch_dependents();
+    pdl_wait();
     const double alpha = st->alpha;
     double v = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -393,12 +402,12 @@ void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
     if (c1 <= c0) return;
     const int g = blocks_for_chunks(c1 - c0);
     if constexpr (std::is_same<VT, double>::value) {
-        k_gs<<<g, SELL_TPB, 0, s>>>(view(L.S, L.S.val.p, L.S.diag.p), c0, c1, f, x);
+        launch(k_gs<double, double, FT, VT>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), c0, c1, f, x);
     } else {
         if (L.vt == VT_BF16)
-            k_gs<<<g, SELL_TPB, 0, s>>>(view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), c0, c1, f, x);
+            launch(k_gs<__nv_bfloat16, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), c0, c1, f, x);
         else
-            k_gs<<<g, SELL_TPB, 0, s>>>(view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), c0, c1, f, x);
+            launch(k_gs<float, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), c0, c1, f, x);
     }
 }
 
@@ -406,14 +415,14 @@ template <class FT, class VT>
 void rec_resid_level(Level& L, const FT* f, const VT* x, VT* r, cudaStream_t s) {
     const int g = blocks_for_chunks(L.S.nchunks);
     if constexpr (std::is_same<VT, double>::value) {
-        k_resid<<<g, SELL_TPB, 0, s>>>(view(L.S, L.S.val.p, L.S.diag.p), L.S.nchunks, f, x, r);
+        launch(k_resid<double, double, FT, VT, VT>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nchunks, f, (const VT*)x, r);
     } else {
         if (L.vt == VT_BF16)
-            k_resid<<<g, SELL_TPB, 0, s>>>(view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p),
-                                           L.S.nchunks, f, x, r);
+            launch(k_resid<__nv_bfloat16, float, FT, VT, VT>, g, SELL_TPB, s,
+                   view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), L.S.nchunks, f, (const VT*)x, r);
         else
-            k_resid<<<g, SELL_TPB, 0, s>>>(view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p),
-                                           L.S.nchunks, f, x, r);
+            launch(k_resid<float, float, FT, VT, VT>, g, SELL_TPB, s,
+                   view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), L.S.nchunks, f, (const VT*)x, r);
     }
 }
 
@@ -429,18 +438,24 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
     const int nl = (int)h.lev.size();
     Level& L = h.lev[l];
     if (l == nl - 1) {                                          // step 2(b): exact coarsest solve
-        k_coarse<<<std::max(1, (L.n + 7) / 8), 256, 0, s>>>(L.n, ainv<VT>(h), f, x);
+        launch(k_coarse<VT, FT, VT>, std::max(1, (L.n + 7) / 8), 256, s, L.n, ainv<VT>(h), f, x);
         return;
     }
     Level& C = h.lev[l + 1];
-    if (zero_guess) k_zero<<<vec_blocks(L.n), VEC_TPB, 0, s>>>(L.n, x);
+    if (zero_guess) launch(k_zero<VT>, vec_blocks(L.n), VEC_TPB, s, (int64_t)L.n, x);
     for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);            // (1) S_l: colours ascending
     rec_resid_level(L, f, x, lr<VT>(L), s);                              // (2a) r = f - A u
-    k_apply_full<<<blocks_for_chunks(L.SR.nchunks), SELL_TPB, 0, s>>>(full_view<VT>(L.SR), L.SR.nchunks,
-                                                                        (const VT*)lr<VT>(L), lf<VT>(C));
-    rec_vcycle<VT, VT>(h, l + 1, lf<VT>(C), lx<VT>(C), true, s);         // (2b) zero initial guess
-    k_prolong<<<blocks_for_chunks(L.SP.nchunks), SELL_TPB, 0, s>>>(full_view<VT>(L.SP), L.SP.nchunks,
-                                                                     (const VT*)lx<VT>(C), x);   // (2c)
+    if (l + 1 >= h.tail_start) {                                         // (2a) f_c = R r, x_c = 0
+        launch(k_restrict_zero<VT, VT>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s, full_view<VT>(L.SR),
+               L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C), lx<VT>(C));
+        record_tail(h, l + 1, lf<VT>(C), lx<VT>(C), s);                  // (2b) the coarser levels, one kernel
+    } else {
+        launch(k_apply_full<VT, VT>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s, full_view<VT>(L.SR),
+               L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C));
+        rec_vcycle<VT, VT>(h, l + 1, lf<VT>(C), lx<VT>(C), true, s);     // (2b) zero initial guess
+    }
+    launch(k_prolong<VT, VT>, blocks_for_chunks(L.SP.nchunks), SELL_TPB, s, full_view<VT>(L.SP), L.SP.nchunks,
+           (const VT*)lx<VT>(C), x);                                     // (2c)
     for (int c = L.ncolours - 1; c >= 0; --c) rec_gs(L, c, f, x, s);     // (3) S_l^T: colours descending
 }
 
@@ -450,9 +465,9 @@ void rec_fine_resid(Handle& h, const double* r, const VT* z, VT* t, cudaStream_t
     const Sell& A = h.Anat;
     const int g = blocks_for_chunks(A.nchunks);
     if constexpr (std::is_same<VT, double>::value)
-        k_resid<<<g, SELL_TPB, 0, s>>>(view(A, A.val.p, A.diag.p), A.nchunks, r, z, t);
+        launch(k_resid<double, double, double, VT, VT>, g, SELL_TPB, s, view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, r, z, t);
     else
-        k_resid<<<g, SELL_TPB, 0, s>>>(view(A, (const float*)A.val32.p, (const float*)A.diag32.p), A.nchunks, r, z, t);
+        launch(k_resid<float, float, double, VT, VT>, g, SELL_TPB, s, view(A, (const float*)A.val32.p, (const float*)A.diag32.p), A.nchunks, r, z, t);
 }
 
 // w = (LU)^{-1} t level by level; with zadd, z += w as well.
@@ -470,11 +485,11 @@ void rec_ic_solve(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s
     }
     for (int g = 0; g + 1 < (int)L.seg.size(); ++g) {
         const int c0 = L.seg[g], c1 = L.seg[g + 1];
-        k_lsolve<<<blocks_for_chunks(c1 - c0), SELL_TPB, 0, s>>>(lv, c0, c1, t, y);
+        launch(k_lsolve<VT, TT, VT>, blocks_for_chunks(c1 - c0), SELL_TPB, s, lv, c0, c1, t, y);
     }
     for (int g = 0; g + 1 < (int)U.seg.size(); ++g) {
         const int c0 = U.seg[g], c1 = U.seg[g + 1];
-        k_usolve<<<blocks_for_chunks(c1 - c0), SELL_TPB, 0, s>>>(uv, c0, c1, (const VT*)y, w, zadd);
+        launch(k_usolve<VT, VT>, blocks_for_chunks(c1 - c0), SELL_TPB, s, uv, c0, c1, (const VT*)y, w, zadd);
     }
 }
 
@@ -510,7 +525,7 @@ void rec_precond_t(Handle& h, int which, const double* r, VT* z, cudaStream_t s)
             rec_ic_solve<double, VT>(h, r, y, t, z, s);
             break;
         default:
-            k_copy<<<vec_blocks(h.n), VEC_TPB, 0, s>>>((int64_t)h.n, r, z);
+            launch(k_copy<double, VT>, vec_blocks(h.n), VEC_TPB, s, (int64_t)h.n, r, z);
             break;
     }
 }
@@ -537,14 +552,14 @@ void apply_precond(Handle& h, int which, const double* r, double* z) {
         rec_precond_t<double>(h, which, r, z, s);
     } else {
         rec_precond_t<float>(h, which, r, h.z32.p, s);
-        k_copy<<<vec_blocks(h.n), VEC_TPB, 0, s>>>((int64_t)h.n, (const float*)h.z32.p, z);
+        launch(k_copy<float, double>, vec_blocks(h.n), VEC_TPB, s, (int64_t)h.n, (const float*)h.z32.p, z);
     }
     CPC_LAUNCH_CK();
 }
 
 void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s) {
     const Sell& A = h.Anat;
-    k_spmv<<<blocks_for_chunks(A.nchunks), SELL_TPB, 0, s>>>(view(A, A.val.p, A.diag.p), A.nchunks, x, y);
+    launch(k_spmv<double, double, double, double>, blocks_for_chunks(A.nchunks), SELL_TPB, s, view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, x, y);
     CPC_LAUNCH_CK();
 }
 
@@ -559,22 +574,27 @@ void level_apply(Handle& h, int l, int op, const double* x, double* y) {
         case 0:
             if (l == 0) spmv_fine(h, x, y, s);
             else if (last) fail(CPC_EINVAL, "coarsest level has no sparse layout");
-            else k_spmv<<<blocks_for_chunks(L.S.nchunks), SELL_TPB, 0, s>>>(view(L.S, L.S.val.p, L.S.diag.p),
-                                                                         L.S.nchunks, x, y);
+            else launch(k_spmv<double, double, double, double>, blocks_for_chunks(L.S.nchunks), SELL_TPB, s,
+                        view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nchunks, x, y);
             break;
         case 1:
         case 2:
             if (last) fail(CPC_EINVAL, "coarsest level has no smoother");
-            k_zero<<<vec_blocks(L.n), VEC_TPB, 0, s>>>(L.n, y);
+            launch(k_zero<double>, vec_blocks(L.n), VEC_TPB, s, (int64_t)L.n, y);
             if (op == 1) for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, x, y, s);
             else for (int c = L.ncolours - 1; c >= 0; --c) rec_gs(L, c, x, y, s);
             break;
         case 3:
             if (!last) fail(CPC_EINVAL, "not the coarsest level");
-            k_coarse<<<std::max(1, (L.n + 7) / 8), 256, 0, s>>>(L.n, h.Ainv.p, x, y);
+            launch(k_coarse<double, double, double>, std::max(1, (L.n + 7) / 8), 256, s, L.n, (const double*)h.Ainv.p, x, y);
             break;
         case 4:
-            rec_vcycle<double, double>(h, l, x, y, true, s);
+            if (l >= h.tail_start) {
+                launch(k_zero<double>, vec_blocks(L.n), VEC_TPB, s, (int64_t)L.n, y);
+                record_tail(h, l, x, y, s);
+            } else {
+                rec_vcycle<double, double>(h, l, x, y, true, s);
+            }
             break;
         default:
             fail(CPC_EINVAL, "unknown level operator");
@@ -603,8 +623,8 @@ static void build_solve_graph(Handle& h, int which) {
     const int n = h.n;
     // init
     CPC_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    k_pcg_init<<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.b.p, h.x.p, h.r.p, h.partial.p, h.counter.p, h.state.p,
-                                                  h.hist.p, cond);
+    launch(k_pcg_init, vec_blocks(n), VEC_TPB, cs, n, (const double*)h.b.p, h.x.p, h.r.p, h.partial.p, h.counter.p,
+           h.state.p, h.hist.p, cond);
     CPC_CK(cudaStreamEndCapture(cs, &g));
     size_t nn = 0;
     CPC_CK(cudaGraphGetNodes(g, nullptr, &nn));
@@ -621,20 +641,21 @@ static void build_solve_graph(Handle& h, int which) {
     // body: one PCG iteration
     CPC_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const Sell& A = h.Anat;
-    k_loop_guard<<<1, 1, 0, cs>>>(cond);
+    launch(k_loop_guard, 1, 32, cs, cond);
     if (fp64(h)) {
         rec_precond_t<double>(h, which, h.r.p, h.z.p, cs);
-        k_pcg_rz<double><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.r.p, h.z.p, h.partial.p, h.counter.p, h.state.p);
-        k_pcg_p<double><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.z.p, h.p.p, h.state.p);
+        launch(k_pcg_rz<double>, vec_blocks(n), VEC_TPB, cs, n, (const double*)h.r.p, (const double*)h.z.p, h.partial.p, h.counter.p, h.state.p);
+        launch(k_pcg_p<double>, vec_blocks(n), VEC_TPB, cs, n, (const double*)h.z.p, h.p.p, (const PcgState*)h.state.p);
     } else {
         rec_precond_t<float>(h, which, h.r.p, h.z32.p, cs);
-        k_pcg_rz<float><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.r.p, h.z32.p, h.partial.p, h.counter.p, h.state.p);
-        k_pcg_p<float><<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.z32.p, h.p.p, h.state.p);
+        launch(k_pcg_rz<float>, vec_blocks(n), VEC_TPB, cs, n, (const double*)h.r.p, (const float*)h.z32.p, h.partial.p, h.counter.p, h.state.p);
+        launch(k_pcg_p<float>, vec_blocks(n), VEC_TPB, cs, n, (const float*)h.z32.p, h.p.p, (const PcgState*)h.state.p);
     }
-    k_pcg_spmv<<<std::min(blocks_for_chunks(A.nchunks), NPART), SELL_TPB, 0, cs>>>(
-        view(A, A.val.p, A.diag.p), A.nchunks, h.p.p, h.q.p, h.partial.p, h.counter.p, h.state.p);
-    k_pcg_update<<<vec_blocks(n), VEC_TPB, 0, cs>>>(n, h.x.p, h.r.p, h.p.p, h.q.p, h.partial.p, h.counter.p, h.state.p,
-                                                    h.hist.p, HIST_CAP, cond);
+    launch(k_pcg_spmv, std::min(blocks_for_chunks(A.nchunks), NPART), SELL_TPB, cs,
+           view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, (const double*)h.p.p, h.q.p,
+           h.partial.p, h.counter.p, h.state.p);
+    launch(k_pcg_update, vec_blocks(n), VEC_TPB, cs, n, h.x.p, h.r.p, (const double*)h.p.p, (const double*)h.q.p,
+           h.partial.p, h.counter.p, h.state.p, h.hist.p, (int)HIST_CAP, cond);
     CPC_CK(cudaStreamEndCapture(cs, &body));
     CPC_LAUNCH_CK();
     size_t nb = 0;

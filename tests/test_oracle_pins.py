@@ -457,3 +457,13 @@ def test_colour_ordered_ic0_is_ic0_of_permuted_matrix(small3d):
     assert rel(LU[pat], Dp[pat]) < 1e-11
     r = orc.pcg(p.rhs(), op=O.BCO, tol=1e-10, maxit=200)
     assert r["status"] == 0
+
+
+def test_fine_grid_colouring_is_red_black(small3d):
+    """The pattern graph of a structured grid is bipartite: colour = (i + j + k) mod 2."""
+    p, _, orc, _ = small3d
+    _, colour = orc.level_cf_colour(0)
+    idx = np.arange(p.n)
+    i, j, k = idx % p.nx, (idx // p.nx) % p.ny, idx // (p.nx * p.ny)
+    assert np.array_equal(colour, (i + j + k) % 2)
+    assert orc.level_sizes(0)["ncolours"] == 2
