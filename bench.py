@@ -233,6 +233,10 @@ def gpu_arm(args, rank, world):
         arms[name]["gbs_solve"] = round(bpi * it[-1] / (np.mean(m) * 1e-3) / 1e9, 1)
         s.close()
 
+    # differentiable solve on the 256 x 256 x 128 channel problem: gradient of the well misfit
+    if world == 1 and not args.no_adjoint:
+        out["adjoint"] = adjoint_arm(dev, stream)
+
     # dominant-kernel roofline: the fine SpMV (SELL-32, FP64), one launch per event pair, L2 flushed
     xv = torch.randn(p.n, dtype=torch.float64, device=dev)
     yv = torch.empty_like(xv)
@@ -263,6 +267,55 @@ def gpu_arm(args, rank, world):
     out["solve_gbs"] = bpi * iters[-1] / (headline_ms * 1e-3) / 1e9
     out["launches"] = s_bco.solve_launches()
     return out
+
+
+def adjoint_arm(dev, stream, tol=1e-8):
+    """dJ/dlog k for J = 1/2 sum_w (mean_w p - d_w)^2 on channels3d_256x256x128: assembly + setup,
+    forward solve, adjoint solve (same handle) and the gradient kernel, each timed with CUDA events."""
+    import torch
+    from paper_1205_6113_gb300 import adjoint, cpc
+    p = inputs.workload("channels3d_256x256x128")
+    grid = adjoint.Grid(p.nx, p.ny, p.nz, p.kz_ratio, p.dirichlet)
+    cells = torch.tensor(inputs.well_columns(p), device=dev, dtype=torch.int64)
+    q = torch.tensor(p.rhs(), device=dev)
+    with torch.no_grad():
+        d = adjoint.well_pressures(adjoint.pressure(torch.tensor(inputs.perturbed_logk(p), device=dev), q, grid,
+                                                    tol=tol), cells)
+    logk = torch.tensor(p.logk, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    rowptr, col, val = cpc.tpfa_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+    s = cpc.Solver(rowptr, col, val, precond="bco", ic_order="colour")
+    ev[1].record(stream)
+    x, it_f, st_f, _ = s.solve(q, tol=tol, maxit=MAXIT, hist=False)
+    ev[2].record(stream)
+    r = adjoint.well_pressures(x, cells) - d
+    dJdp = torch.zeros_like(x)
+    dJdp.index_add_(0, cells.reshape(-1), (r / cells.shape[1]).repeat_interleave(cells.shape[1]))
+    ev[3].record(stream)
+    lam, it_a, st_a, _ = s.solve(dJdp, tol=tol, maxit=MAXIT, hist=False)
+    g = cpc.tpfa_gradient(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet, lam, x)
+    ev[4].record(stream)
+    torch.cuda.synchronize()
+    # the gradient kernel alone (bytes: log k, lambda, p read, g written; neighbours from cache)
+    kms = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cpc.tpfa_gradient(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet, lam, x, g)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms.append(e0.elapsed_time(e1))
+    kbytes = 4 * 8 * p.n
+    res = dict(workload="channels3d_256x256x128", n=p.n, tol=tol, status=(st_f, st_a), iters=(it_f, it_a),
+               setup_ms=round(ev[0].elapsed_time(ev[1]), 2), forward_ms=round(ev[1].elapsed_time(ev[2]), 2),
+               adjoint_and_gradient_ms=round(ev[3].elapsed_time(ev[4]), 2),
+               gradient_kernel_ms=round(float(np.median(kms)), 4),
+               gradient_kernel_gbs=round(kbytes / (np.median(kms) * 1e-3) / 1e9, 1),
+               misfit=float(0.5 * (r * r).sum()), grad_norm=float(g.norm()))
+    s.close()
+    return res
 
 
 def csr_matvec(rowptr, col, val, x):
@@ -327,6 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
@@ -369,6 +423,7 @@ def main():
         "arms": out["arms"],
         "setup_ms": out["setups"],
         "true_res": out["true_res"],
+        "adjoint": out.get("adjoint"),
         "clocks": out["clocks"],
         "gpu_launches": launches,
         "launches_per_iteration": per_it,

@@ -98,6 +98,18 @@ int cpc_tpfa_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, do
                       void* stream);
 
 /*
+ * Adjoint gradient through the assembly above: g_c = -lambda^T (dA/dtheta_c) p with theta = logk.
+ * For A(theta) p = q and a misfit J(p), with A lambda = dJ/dp (A is symmetric, so the solver of
+ * A serves), g = dJ/dtheta.  A face contributes dT/dtheta_c (lambda_c - lambda_j)(p_c - p_j) with
+ * dT/dtheta_c = 2 k_c k_j^2 / (k_c + k_j)^2 (k_z on z faces), a Dirichlet face 2 k_c lambda_c p_c.
+ * Not a passage of the paper: the differentiable-solve extension of its model problem (Section 4).
+ * logk, lambda, p, g: device, n = nx ny nz each.  Asynchronous on `stream`.
+ */
+int cpc_tpfa_gradient(int32_t nx, int32_t ny, int32_t nz, const double* logk, double kz_ratio,
+                      int32_t dirichlet_mask, const double* lambda, const double* p, double* g,
+                      void* stream);
+
+/*
  * Same result as cpc_tpfa_assemble (identical rowptr, colidx and vals) without allocating any
  * device memory: for callers that cannot call cudaMalloc or cudaMallocAsync inside a library
  * call, such as simulators that own every device allocation through their own pool, or loops

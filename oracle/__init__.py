@@ -53,6 +53,8 @@ def lib():
         _lib.orc_tpfa_nnz.argtypes = [i32, i32, i32]
         _lib.orc_tpfa.restype = i32
         _lib.orc_tpfa.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
+        _lib.orc_tpfa_gradient.restype = i32
+        _lib.orc_tpfa_gradient.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
         _lib.orc_create.restype = P
         _lib.orc_create.argtypes = [i32, P, P, P, f64, i32, i32, i32, i32, P]
         _lib.orc_destroy.argtypes = [P]
@@ -122,6 +124,33 @@ def tpfa(nx, ny, nz, logk, kz_ratio, dirichlet) -> Csr:
     if st:
         raise ValueError("orc_tpfa failed: %d" % st)
     return Csr(n, rowptr, col, val)
+
+
+def tpfa_gradient(nx, ny, nz, logk, kz_ratio, dirichlet, lam, p) -> np.ndarray:
+    """g = -lambda^T (dA/dlog k) p for the two-point-flux matrix (adjoint gradient through the assembly)."""
+    logk, lam, p = _f64(logk), _f64(lam), _f64(p)
+    g = np.zeros(nx * ny * nz)
+    if lib().orc_tpfa_gradient(nx, ny, nz, _p(logk), float(kz_ratio), int(dirichlet), _p(lam), _p(p), _p(g)):
+        raise ValueError("orc_tpfa_gradient failed")
+    return g
+
+
+def well_means(p, wells_cells) -> np.ndarray:
+    """Mean pressure over the cells of each well."""
+    return np.array([np.mean(p[np.asarray(c)]) for c in wells_cells])
+
+
+def misfit_gradient(A: Csr, prob, logk, wells_cells, d, orc=None, tol=1e-12):
+    """J = 1/2 sum_w (mean_w p - d_w)^2 with A(logk) p = q, and dJ/dlog k by the adjoint method."""
+    orc = orc or Oracle(A)
+    q = prob.rhs()
+    p = orc.pcg(q, op=BCO, tol=tol, maxit=2000)["x"]
+    r = well_means(p, wells_cells) - d
+    dJdp = np.zeros_like(p)
+    for w, c in enumerate(wells_cells):
+        dJdp[np.asarray(c)] += r[w] / len(c)
+    lam = orc.pcg(dJdp, op=BCO, tol=tol, maxit=2000)["x"]
+    return 0.5 * float(r @ r), tpfa_gradient(prob.nx, prob.ny, prob.nz, logk, prob.kz_ratio, prob.dirichlet, lam, p)
 
 
 def tpfa_problem(prob) -> Csr:

@@ -18,6 +18,7 @@
  *                  coarsest solve.
  *   apply_bco      Algorithm 2.1 with u^{k,0} = 0, giving B_co of Eq. barB.
  *   pcg            textbook preconditioned CG (the Krylov method the paper runs, Section 5).
+ *   tpfa_gradient  -lambda^T (dA/dlog k) p, the adjoint gradient of a misfit through the assembly.
  *
  * Level numbering here is 0 = finest ... L-1 = coarsest (the paper numbers the other way).
  * Pins: tests/test_oracle_*.py.  Table 2 iteration counts: parity unpinned (the paper's
@@ -83,6 +84,41 @@ Csr tpfa_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dm
                 A.ptr[c + 1] = (int)A.col.size();
             }
     return A;
+}
+
+// Derivative of the assembly above with respect to theta = log k, contracted with two vectors:
+// g_c = -lambda^T (dA/dtheta_c) p.  A face between c and j adds T (e_c - e_j)(e_c - e_j)^T to A,
+// with dT/dtheta_c = 2 k_c k_j^2 / (k_c + k_j)^2 (k_z on z faces); a Dirichlet face adds
+// 2 k_c e_c e_c^T, with derivative 2 k_c.  For A p = q and A lambda = dJ/dp this is dJ/dtheta
+// (the adjoint method; A is symmetric).
+void tpfa_gradient(int nx, int ny, int nz, const double* logk, double kzr, int dmask, const double* lam,
+                   const double* p, double* g) {
+    const int n = nx * ny * nz;
+    vector<double> k(n), kz(n);
+    for (int c = 0; c < n; ++c) { k[c] = std::exp(logk[c]); kz[c] = kzr * k[c]; }
+    auto dT = [](double a, double b) { return 2.0 * a * b * b / ((a + b) * (a + b)); };
+    for (int kk = 0; kk < nz; ++kk)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int c = i + nx * (j + ny * kk);
+                double s = 0.0;
+                auto face = [&](int o, double d) { s += d * (lam[c] - lam[o]) * (p[c] - p[o]); };
+                if (kk > 0)      face(c - nx * ny, dT(kz[c], kz[c - nx * ny]));
+                if (j > 0)       face(c - nx, dT(k[c], k[c - nx]));
+                if (i > 0)       face(c - 1, dT(k[c], k[c - 1]));
+                if (i < nx - 1)  face(c + 1, dT(k[c], k[c + 1]));
+                if (j < ny - 1)  face(c + nx, dT(k[c], k[c + nx]));
+                if (kk < nz - 1) face(c + nx * ny, dT(kz[c], kz[c + nx * ny]));
+                double b = 0.0;
+                if ((dmask & 1) && i == 0)        b += 2.0 * k[c];
+                if ((dmask & 2) && i == nx - 1)   b += 2.0 * k[c];
+                if ((dmask & 4) && j == 0)        b += 2.0 * k[c];
+                if ((dmask & 8) && j == ny - 1)   b += 2.0 * k[c];
+                if ((dmask & 16) && kk == 0)      b += 2.0 * kz[c];
+                if ((dmask & 32) && kk == nz - 1) b += 2.0 * kz[c];
+                s += b * lam[c] * p[c];
+                g[c] = -s;
+            }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -660,6 +696,13 @@ int orc_tpfa(int nx, int ny, int nz, const double* logk, double kz_ratio, int dm
     std::memcpy(rowptr, A.ptr.data(), sizeof(int) * (A.n + 1));
     std::memcpy(col, A.col.data(), sizeof(int) * A.nnz());
     std::memcpy(val, A.val.data(), sizeof(double) * A.nnz());
+    return 0;
+}
+
+int orc_tpfa_gradient(int nx, int ny, int nz, const double* logk, double kz_ratio, int dmask, const double* lam,
+                      const double* p, double* g) {
+    if (nx < 1 || ny < 1 || nz < 1) return 1;
+    tpfa_gradient(nx, ny, nz, logk, kz_ratio, dmask, lam, p, g);
     return 0;
 }
 

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("cpc_default_options", _I32, [_P]),
     ("cpc_tpfa_nnz", _I64, [_I32, _I32, _I32]),
     ("cpc_tpfa_assemble", _I32, [_I32, _I32, _I32, _P, _F64, _I32, _P, _P, _P, _P]),
+    ("cpc_tpfa_gradient", _I32, [_I32, _I32, _I32, _P, _F64, _I32, _P, _P, _P, _P]),
     ("cpc_tpfa_assemble_noalloc", _I32, [_I32, _I32, _I32, _P, _F64, _I32, _P, _P, _P, _P]),
     ("cpc_setup", _I32, [_P, _P, _P]),
     ("cpc_destroy", None, [_P]),
@@ -124,6 +125,17 @@ def tpfa_assemble(nx, ny, nz, logk, kz_ratio, dirichlet_mask, stream=None):
                                     _dptr(rowptr, torch.int32), _dptr(col, torch.int32),
                                     _dptr(val, torch.float64), _stream_ptr(stream)))
     return rowptr, col, val
+
+
+def tpfa_gradient(nx, ny, nz, logk, kz_ratio, dirichlet_mask, lam, p, g=None, stream=None):
+    """g = -lambda^T (dA/dlog k) p on the device (cpc_tpfa_gradient)."""
+    torch = _torch()
+    if g is None:
+        g = torch.empty_like(p)
+    _check(load().cpc_tpfa_gradient(nx, ny, nz, _dptr(logk, torch.float64), float(kz_ratio), int(dirichlet_mask),
+                                    _dptr(lam, torch.float64), _dptr(p, torch.float64), _dptr(g, torch.float64),
+                                    _stream_ptr(stream)))
+    return g
 
 
 def tpfa_assemble_noalloc(nx, ny, nz, logk, kz_ratio, dirichlet_mask, rowptr, col, val, stream=None):

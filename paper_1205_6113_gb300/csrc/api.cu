@@ -72,6 +72,15 @@ int cpc_tpfa_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, do
     });
 }
 
+int cpc_tpfa_gradient(int32_t nx, int32_t ny, int32_t nz, const double* logk, double kz_ratio,
+                      int32_t dirichlet_mask, const double* lambda, const double* p, double* g, void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || !logk || !lambda || !p || !g || !(kz_ratio > 0.0)) return CPC_EINVAL;
+    if ((int64_t)nx * ny * nz > INT32_MAX) return CPC_EINVAL;
+    return guarded(nullptr, [&] {
+        cpc::tpfa_gradient(nx, ny, nz, logk, kz_ratio, dirichlet_mask, lambda, p, g, (cudaStream_t)stream);
+    });
+}
+
 int cpc_setup(const cpc_csr* A, const cpc_options* opt, cpc_handle** out) {
     if (!out) return CPC_EINVAL;
     *out = nullptr;

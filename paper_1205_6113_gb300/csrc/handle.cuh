@@ -74,6 +74,10 @@ struct Handle {
     ~Handle();
 };
 
+// adjoint.cu
+void tpfa_gradient(int nx, int ny, int nz, const double* logk, double kzr, int dmask, const double* lam,
+                   const double* p, double* g, cudaStream_t s);
+
 // setup.cu
 void tpfa_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask, int* rowptr,
                    int* col, double* val, cudaStream_t s);

@@ -467,3 +467,47 @@ def test_fine_grid_colouring_is_red_black(small3d):
     i, j, k = idx % p.nx, (idx // p.nx) % p.ny, idx // (p.nx * p.ny)
     assert np.array_equal(colour, (i + j + k) % 2)
     assert orc.level_sizes(0)["ncolours"] == 2
+
+
+# --------------------------------------------------------------------------------------------
+# Adjoint gradient through the assembly: dJ/dlog k = -lambda^T (dA/dlog k) p
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dirichlet", [inputs.FACE_X0, inputs.FACE_X0 | inputs.FACE_Z1])
+def test_adjoint_gradient_matches_central_differences(dirichlet):
+    p = inputs.small_3d(6, 5, 4, seed=31, dirichlet=dirichlet)
+    wells = [[p.idx(1, 1, k) for k in range(p.nz)], [p.idx(4, 3, k) for k in range(p.nz)]]
+    p.wells = [(c, 1.0 / p.nz) for c in wells[0]] + [(c, -1.0 / p.nz) for c in wells[1]]
+    d = np.array([0.3, -0.2])
+    q = p.rhs()
+
+    def J(logk):   # independent of the oracle's solver: dense solve of the oracle's assembly
+        A = O.tpfa(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet).to_dense()
+        x = np.linalg.solve(A, q)
+        r = O.well_means(x, wells) - d
+        return 0.5 * r @ r
+
+    A = O.tpfa_problem(p)
+    j0, g = O.misfit_gradient(A, p, p.logk, wells, d, orc=O.Oracle(A, coarse_max=8))
+    assert abs(j0 - J(p.logk)) <= 1e-10 * abs(j0)
+    h = 1e-5
+    fd = np.zeros(p.n)
+    for c in range(p.n):
+        e = np.zeros(p.n)
+        e[c] = h
+        fd[c] = (J(p.logk + e) - J(p.logk - e)) / (2 * h)
+    assert np.max(np.abs(fd - g)) <= 1e-6 * np.max(np.abs(g))
+
+
+def test_gradient_contraction_is_bilinear_form_of_dA():
+    """g_c = -lambda^T (dA/dtheta_c) p with dA/dtheta_c taken by differencing the dense assembly."""
+    p = inputs.small_3d(4, 3, 3, seed=5)
+    lam = inputs.random_vector(p.n, seed=1)
+    x = inputs.random_vector(p.n, seed=2)
+    g = O.tpfa_gradient(p.nx, p.ny, p.nz, p.logk, p.kz_ratio, p.dirichlet, lam, x)
+    h = 1e-6
+    for c in range(p.n):
+        e = np.zeros(p.n)
+        e[c] = h
+        dA = (O.tpfa(p.nx, p.ny, p.nz, p.logk + e, p.kz_ratio, p.dirichlet).to_dense()
+              - O.tpfa(p.nx, p.ny, p.nz, p.logk - e, p.kz_ratio, p.dirichlet).to_dense()) / (2 * h)
+        assert abs(g[c] + lam @ dA @ x) <= 1e-7 * (1 + abs(g[c]))
