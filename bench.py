@@ -233,6 +233,10 @@ def gpu_arm(args, rank, world):
         arms[name]["gbs_solve"] = round(bpi * it[-1] / (np.mean(m) * 1e-3) / 1e9, 1)
         s.close()
 
+    # batched: 64 right-hand sides and their adjoints in one graph, FP32 preconditioner
+    if world == 1 and not args.no_batched:
+        out["batched"] = batched_arm(rowptr, col, val, p, dev, stream, args)
+
     # differentiable solve on the 256 x 256 x 128 channel problem: gradient of the well misfit
     if world == 1 and not args.no_adjoint:
         out["adjoint"] = adjoint_arm(dev, stream)
@@ -269,6 +273,53 @@ def gpu_arm(args, rank, world):
     return out
 
 
+def batched_arm(rowptr, col, val, p, dev, stream, args, K=64):
+    """64 right-hand sides (rates U[-1,1] at 16 random cells each) plus their adjoints as one
+    graph-captured batched solve, against the same 64 forward solves one at a time."""
+    import torch
+    from paper_1205_6113_gb300 import cpc
+    s = cpc.Solver(rowptr, col, val, precond="bco", precision="fp32", ic_order="colour")
+    B = torch.tensor(np.ascontiguousarray(inputs.batch_rhs(p.n, K, seed=5).T), device=dev)
+    X = torch.empty_like(B)
+    Lam = torch.empty_like(B)
+    s.solve_batched_adjoint(B, tol=TOL, maxit=MAXIT, X=X, Lam=Lam)
+    steps = max(1, min(args.steps, 3))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        _, _, itf, ita = s.solve_batched_adjoint(B, tol=TOL, maxit=MAXIT, X=X, Lam=Lam)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    bat_ms = ev[0].elapsed_time(ev[1]) / steps
+    fwd_only = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.solve_batched(B, tol=TOL, maxit=MAXIT, X=X)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.solve_batched(B, tol=TOL, maxit=MAXIT, X=X)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_batched_ms = e0.elapsed_time(e1)
+    cols = [B[:, k].contiguous() for k in range(K)]
+    s.solve(cols[0], tol=TOL, maxit=MAXIT, hist=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(K):
+        _, it, st, _ = s.solve(cols[k], tol=TOL, maxit=MAXIT, hist=False)
+        fwd_only.append(it)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    s.close()
+    return dict(workload=WORKLOAD + "_64rhs", nrhs=K, precision="fp32 preconditioner",
+                batched_fwd_adj_ms=round(bat_ms, 2), batched_solves_per_s=round(2 * K / (bat_ms * 1e-3), 1),
+                batched_fwd_ms=round(fwd_batched_ms, 2), batched_fwd_solves_per_s=round(K / (fwd_batched_ms * 1e-3), 1),
+                sequential_fwd_ms=round(seq_ms, 2), sequential_solves_per_s=round(K / (seq_ms * 1e-3), 1),
+                iters_fwd=[int(itf.min()), int(itf.max())], iters_adj=[int(ita.min()), int(ita.max())],
+                iters_sequential=[int(min(fwd_only)), int(max(fwd_only))])
+
+
 def adjoint_arm(dev, stream, tol=1e-8):
     """dJ/dlog k for J = 1/2 sum_w (mean_w p - d_w)^2 on channels3d_256x256x128: assembly + setup,
     forward solve, adjoint solve (same handle) and the gradient kernel, each timed with CUDA events."""
@@ -298,7 +349,7 @@ def adjoint_arm(dev, stream, tol=1e-8):
     g = cpc.tpfa_gradient(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet, lam, x)
     ev[4].record(stream)
     torch.cuda.synchronize()
-    # the gradient kernel alone (bytes: log k, lambda, p read, g written; neighbours from cache)
+    # the gradient pass alone (bytes: log k read, k written and read, lambda, p read, g written)
     kms = []
     for _ in range(5):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -307,7 +358,7 @@ def adjoint_arm(dev, stream, tol=1e-8):
         e1.record(stream)
         torch.cuda.synchronize()
         kms.append(e0.elapsed_time(e1))
-    kbytes = 4 * 8 * p.n
+    kbytes = 6 * 8 * p.n
     res = dict(workload="channels3d_256x256x128", n=p.n, tol=tol, status=(st_f, st_a), iters=(it_f, it_a),
                setup_ms=round(ev[0].elapsed_time(ev[1]), 2), forward_ms=round(ev[1].elapsed_time(ev[2]), 2),
                adjoint_and_gradient_ms=round(ev[3].elapsed_time(ev[4]), 2),
@@ -381,6 +432,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
@@ -424,6 +476,7 @@ def main():
         "setup_ms": out["setups"],
         "true_res": out["true_res"],
         "adjoint": out.get("adjoint"),
+        "batched": out.get("batched"),
         "clocks": out["clocks"],
         "gpu_launches": launches,
         "launches_per_iteration": per_it,

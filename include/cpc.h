@@ -156,6 +156,26 @@ int cpc_solve(cpc_handle* h, const double* b, double* x, double tol, int32_t max
 int cpc_solve_host(cpc_handle* h, const double* b_host, double* x_host, double tol,
                    int32_t maxit, int32_t* iters, double* res_hist, int32_t hist_cap);
 
+/*
+ * PCG on K = nrhs independent right-hand sides at once (1 <= nrhs <= 128), same preconditioner and
+ * stopping rule per column as cpc_solve; every matrix and preconditioner pass serves all columns
+ * (one read of the matrix per K solves).  B, X: device, [n][nrhs] row-major (entry (i, k) at
+ * i * nrhs + k).  iters[nrhs] (host) receives each column's iteration count, status[nrhs] (host,
+ * may be NULL) its status code.  The whole loop is one CUDA graph.  Not a passage of the paper:
+ * the many-right-hand-side use of its solver.  Synchronises the stream.
+ */
+int cpc_solve_batched(cpc_handle* h, int32_t nrhs, const double* B, double* X, double tol,
+                      int32_t maxit, int32_t* iters, int32_t* status);
+
+/*
+ * As cpc_solve_batched, then in the same graph the adjoint solves A Lambda = G with
+ * G[i][k] = X[i][k] where B[i][k] != 0 and 0 elsewhere (the gradient of
+ * J_k = 1/2 sum over the source cells of column k of X[i][k]^2).  X receives the forward
+ * solutions, Lambda the adjoint solutions; iters_fwd / iters_adj (host, [nrhs]) the counts.
+ */
+int cpc_solve_batched_adjoint(cpc_handle* h, int32_t nrhs, const double* B, double* X, double* Lambda,
+                              double tol, int32_t maxit, int32_t* iters_fwd, int32_t* iters_adj);
+
 /* z = M r for one application of a preconditioner (which = CPC_PRECOND_*; -1 = the handle's).
  * r[n], z[n] device.  Asynchronous.  cpc_apply_Bcom is which = CPC_PRECOND_BCO. */
 int cpc_apply_precond(cpc_handle* h, int32_t which, const double* r, double* z);

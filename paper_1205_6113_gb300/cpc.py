@@ -54,6 +54,8 @@ SIGNATURES = [
     ("cpc_last_error", ctypes.c_char_p, [_P]),
     ("cpc_solve", _I32, [_P, _P, _P, _F64, _I32, _P, _P, _I32]),
     ("cpc_solve_host", _I32, [_P, _P, _P, _F64, _I32, _P, _P, _I32]),
+    ("cpc_solve_batched", _I32, [_P, _I32, _P, _P, _F64, _I32, _P, _P]),
+    ("cpc_solve_batched_adjoint", _I32, [_P, _I32, _P, _P, _P, _F64, _I32, _P, _P]),
     ("cpc_apply_precond", _I32, [_P, _I32, _P, _P]),
     ("cpc_apply_Bcom", _I32, [_P, _P, _P]),
     ("cpc_spmv", _I32, [_P, _P, _P]),
@@ -226,6 +228,33 @@ class Solver:
         if rc not in (0, 3, 4):
             _check(rc, self._h)
         return it.value, rc
+
+    def solve_batched(self, B, tol=1e-6, maxit=1000, X=None):
+        """PCG on the columns of B ([n, K] CUDA float64, row-major); returns (X, iters[K], status[K])."""
+        torch = _torch()
+        if X is None:
+            X = torch.empty_like(B)
+        K = int(B.shape[1])
+        it = np.zeros(K, np.int32)
+        st = np.zeros(K, np.int32)
+        _check(load().cpc_solve_batched(self._h, K, _dptr(B, torch.float64), _dptr(X, torch.float64), float(tol),
+                                        int(maxit), ctypes.c_void_p(it.ctypes.data), ctypes.c_void_p(st.ctypes.data)),
+               self._h)
+        return X, it, st
+
+    def solve_batched_adjoint(self, B, tol=1e-6, maxit=1000, X=None, Lam=None):
+        """Forward solves of B's columns, then adjoint solves with sources X at B's nonzeros (one graph)."""
+        torch = _torch()
+        X = torch.empty_like(B) if X is None else X
+        Lam = torch.empty_like(B) if Lam is None else Lam
+        K = int(B.shape[1])
+        itf = np.zeros(K, np.int32)
+        ita = np.zeros(K, np.int32)
+        _check(load().cpc_solve_batched_adjoint(self._h, K, _dptr(B, torch.float64), _dptr(X, torch.float64),
+                                                _dptr(Lam, torch.float64), float(tol), int(maxit),
+                                                ctypes.c_void_p(itf.ctypes.data), ctypes.c_void_p(ita.ctypes.data)),
+               self._h)
+        return X, Lam, itf, ita
 
     def apply(self, r, which=None, z=None):
         """z = M r for one preconditioner application (which: name or None for the handle's)."""

@@ -11,7 +11,10 @@ struct cpc_handle {
 };
 
 namespace cpc {
-Handle::~Handle() { destroy_graphs(*this); }
+Handle::~Handle() {
+    destroy_graphs(*this);
+    destroy_batched(*this);
+}
 }  // namespace cpc
 
 namespace {
@@ -144,6 +147,21 @@ int cpc_solve(cpc_handle* h, const double* b, double* x, double tol, int32_t max
 int cpc_solve_host(cpc_handle* h, const double* b_host, double* x_host, double tol, int32_t maxit,
                    int32_t* iters, double* res_hist, int32_t hist_cap) {
     return do_solve(h, b_host, x_host, tol, maxit, iters, res_hist, hist_cap);
+}
+
+int cpc_solve_batched(cpc_handle* h, int32_t nrhs, const double* B, double* X, double tol, int32_t maxit,
+                      int32_t* iters, int32_t* status) {
+    if (!h || nrhs < 1 || nrhs > 128 || !B || !X || !iters || maxit < 0 || !(tol >= 0.0)) return CPC_EINVAL;
+    return guarded(h, [&] { cpc::solve_batched(h->h, nrhs, B, X, nullptr, tol, maxit, iters, status, nullptr, nullptr); });
+}
+
+int cpc_solve_batched_adjoint(cpc_handle* h, int32_t nrhs, const double* B, double* X, double* Lambda, double tol,
+                              int32_t maxit, int32_t* iters_fwd, int32_t* iters_adj) {
+    if (!h || nrhs < 1 || nrhs > 128 || !B || !X || !Lambda || !iters_fwd || !iters_adj || maxit < 0 || !(tol >= 0.0))
+        return CPC_EINVAL;
+    return guarded(h, [&] {
+        cpc::solve_batched(h->h, nrhs, B, X, Lambda, tol, maxit, iters_fwd, nullptr, iters_adj, nullptr);
+    });
 }
 
 int cpc_apply_precond(cpc_handle* h, int32_t which, const double* r, double* z) {

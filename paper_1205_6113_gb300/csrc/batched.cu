@@ -1,0 +1,803 @@
+// batched.cu -- PCG on K right-hand sides at once (independent columns in lockstep).
+//
+// Block vectors are row-major [n][Kp] (Kp = K rounded up to a multiple of 32), so one warp owns a
+// row and its lanes own columns lane, lane + 32, ...: every matrix entry is one broadcast load
+// shared by all K columns, and every gathered vector row is one coalesced load.  The matrix is read
+// once per K solves instead of once per solve (SpMM).  Each column has its own alpha, beta and
+// convergence flag; a converged column is frozen (alpha = 0) while the others continue, so each
+// column reproduces the single-right-hand-side iteration.  Reductions are per column and finish in
+// a fixed order.  The preconditioner is the handle's, applied column-wise by the same algorithms
+// (Algorithm 2.1 with Algorithm 3.2 and the IC(0) solves).
+#include <algorithm>
+#include <type_traits>
+#include <utility>
+
+#include "device.cuh"
+#include "handle.cuh"
+
+namespace cpc {
+
+namespace {
+
+constexpr int BWARPS = 4;                 // rows (warps) per block
+constexpr int BTPB = BWARPS * 32;
+constexpr int NB_STATE = 12;              // per-column scalar slots
+
+// column-state layout: S[slot * Kp + col]
+enum { S_BNORM = 0, S_RZ, S_RZOLD, S_PQ, S_ALPHA, S_BETA, S_RES, S_ACTIVE, S_K, S_STATUS, S_TOL, S_MAXIT };
+
+template <class MT, class DT>
+struct BV {                               // SELL view for the batched kernels
+    int C;
+    const int* __restrict__ perm;
+    const int* __restrict__ cptr;
+    const int* __restrict__ col;
+    const MT* __restrict__ val;
+    const DT* __restrict__ diag;
+};
+
+template <class MT, class DT>
+BV<MT, DT> bview(const Sell& S, const MT* val, const DT* diag) {
+    return BV<MT, DT>{S.C, S.perm.p, S.cptr.p, S.col.p, val, diag};
+}
+
+template <class... KArgs, class... Args>
+void blaunch(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)std::max(1, grid), 1, 1);
+    cfg.blockDim = dim3((unsigned)block, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CPC_CK(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
+}
+
+inline int rows_grid(int nrows) { return (nrows + BWARPS - 1) / BWARPS; }
+
+// acc[j] += sum_w a_w x[col_w][lane + 32 j] over the entries of the row in slot s.  Padding entries
+// (col < 0) sit at the end of a row.  Four entries are loaded before their gathers.
+template <int J, class VT, class MT, class XT>
+__device__ __forceinline__ void brow(const int* __restrict__ col, const MT* __restrict__ val, int C, int base,
+                                     int width, int r, const XT* x, int Kp, int lane, VT (&acc)[J]) {
+    int w = 0;
+    for (; w + 4 <= width; w += 4) {
+        int c[4];
+        VT a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = col[base + (w + u) * C + r];
+            a[u] = Cv<VT>::f(val[base + (w + u) * C + r]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] < 0) continue;
+            const XT* xr = x + (size_t)c[u] * Kp + lane;
+#pragma unroll
+            for (int j = 0; j < J; ++j) acc[j] += a[u] * Cv<VT>::f(xr[32 * j]);
+        }
+    }
+    for (; w < width; ++w) {
+        const int c = col[base + w * C + r];
+        if (c < 0) break;
+        const VT a = Cv<VT>::f(val[base + w * C + r]);
+        const XT* xr = x + (size_t)c * Kp + lane;
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] += a * Cv<VT>::f(xr[32 * j]);
+    }
+}
+
+// Gauss-Seidel over the slots [s0, s1) of one colour, all columns.
+template <int J, class MT, class DT, class FT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, const FT* __restrict__ f, VT* x, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
+    if (s >= s1) return;
+    const int lane = threadIdx.x & 31;
+    const int row = A.perm[s];
+    if (row < 0) return;
+    const int k = s / A.C, r = s % A.C;
+    const int base = A.cptr[k];
+    VT acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = VT(0);
+    brow<J, VT>(A.col, A.val, A.C, base, (A.cptr[k + 1] - base) / A.C, r, x, Kp, lane, acc);
+    const VT d = Cv<VT>::f(A.diag[s]);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const size_t o = (size_t)row * Kp + lane + 32 * j;
+        x[o] = (Cv<VT>::f(f[o]) - acc[j]) / d;
+    }
+}
+
+// out = f - A x (resid) over all slots; with DIAG the split diagonal is included.
+template <int J, class MT, class DT, class FT, class XT, class RT>
+__global__ void __launch_bounds__(BTPB) kb_resid(BV<MT, DT> A, int nslots, const FT* __restrict__ f,
+                                                  const XT* __restrict__ x, RT* __restrict__ out, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    for (int s = blockIdx.x * BWARPS + (threadIdx.x >> 5); s < nslots; s += gridDim.x * BWARPS) {
+        const int row = A.perm[s];
+        if (row < 0) continue;
+        const int k = s / A.C, r = s % A.C;
+        const int base = A.cptr[k];
+        RT acc[J];
+        const RT d = Cv<RT>::f(A.diag[s]);
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = d * Cv<RT>::f(x[(size_t)row * Kp + lane + 32 * j]);
+        brow<J, RT>(A.col, A.val, A.C, base, (A.cptr[k + 1] - base) / A.C, r, x, Kp, lane, acc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)row * Kp + lane + 32 * j;
+            out[o] = Cv<RT>::f(f[o]) - acc[j];
+        }
+    }
+}
+
+// y = M x for full rows (restriction), optionally zeroing yz (the next level's initial guess).
+template <int J, class MT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_apply(BV<MT, MT> M, int nslots, const VT* __restrict__ x,
+                                                  VT* __restrict__ y, VT* __restrict__ yz, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    for (int s = blockIdx.x * BWARPS + (threadIdx.x >> 5); s < nslots; s += gridDim.x * BWARPS) {
+        const int row = M.perm[s];
+        if (row < 0) continue;
+        const int k = s / M.C, r = s % M.C;
+        const int base = M.cptr[k];
+        VT acc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = VT(0);
+        brow<J, VT>(M.col, M.val, M.C, base, (M.cptr[k + 1] - base) / M.C, r, x, Kp, lane, acc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)row * Kp + lane + 32 * j;
+            y[o] = acc[j];
+            if (yz) yz[o] = VT(0);
+        }
+    }
+}
+
+// x += P e
+template <int J, class MT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_prolong(BV<MT, MT> P, int nslots, const VT* __restrict__ e,
+                                                    VT* __restrict__ x, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    for (int s = blockIdx.x * BWARPS + (threadIdx.x >> 5); s < nslots; s += gridDim.x * BWARPS) {
+        const int row = P.perm[s];
+        if (row < 0) continue;
+        const int k = s / P.C, r = s % P.C;
+        const int base = P.cptr[k];
+        VT acc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = VT(0);
+        brow<J, VT>(P.col, P.val, P.C, base, (P.cptr[k + 1] - base) / P.C, r, e, Kp, lane, acc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) x[(size_t)row * Kp + lane + 32 * j] += acc[j];
+    }
+}
+
+// x = A_c^{-1} f (dense), one warp per row, lanes over columns.
+template <int J, class AT, class FT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_coarse(int n, const AT* __restrict__ Ainv, const FT* __restrict__ f,
+                                                   VT* __restrict__ x, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * BWARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * BWARPS) {
+        VT acc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = VT(0);
+        for (int m = 0; m < n; ++m) {
+            const VT a = Cv<VT>::f(Ainv[(size_t)i * n + m]);
+#pragma unroll
+            for (int j = 0; j < J; ++j) acc[j] += a * Cv<VT>::f(f[(size_t)m * Kp + lane + 32 * j]);
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) x[(size_t)i * Kp + lane + 32 * j] = acc[j];
+    }
+}
+
+template <class VT>
+__global__ void kb_zero(int64_t n, VT* x) {
+    pdl_launch_dependents();
+    pdl_wait();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = VT(0);
+}
+
+// Triangular solves of one IC(0) level, all columns: y = t - L y; w = (y - U w) / d, z += w.
+template <int J, class MT, class TT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_lsolve(BV<MT, MT> L, int s0, int s1, const TT* __restrict__ t, VT* y, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
+    if (s >= s1) return;
+    const int lane = threadIdx.x & 31;
+    const int row = L.perm[s];
+    if (row < 0) return;
+    const int k = s / L.C, r = s % L.C;
+    const int base = L.cptr[k];
+    VT acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = VT(0);
+    brow<J, VT>(L.col, L.val, L.C, base, (L.cptr[k + 1] - base) / L.C, r, y, Kp, lane, acc);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const size_t o = (size_t)row * Kp + lane + 32 * j;
+        y[o] = Cv<VT>::f(t[o]) - acc[j];
+    }
+}
+
+template <int J, class MT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_usolve(BV<MT, MT> U, int s0, int s1, const VT* __restrict__ y, VT* w,
+                                                   VT* zadd, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
+    if (s >= s1) return;
+    const int lane = threadIdx.x & 31;
+    const int row = U.perm[s];
+    if (row < 0) return;
+    const int k = s / U.C, r = s % U.C;
+    const int base = U.cptr[k];
+    VT acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = VT(0);
+    brow<J, VT>(U.col, U.val, U.C, base, (U.cptr[k + 1] - base) / U.C, r, w, Kp, lane, acc);
+    const VT d = Cv<VT>::f(U.diag[s]);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const size_t o = (size_t)row * Kp + lane + 32 * j;
+        const VT v = (y[o] - acc[j]) / d;
+        w[o] = v;
+        if (zadd) zadd[o] += v;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-column reductions: each block sums its rows per column (warps, then in order), writes a
+// partial row; the last block sums the partial rows in block order and runs `fin` per column.
+// ---------------------------------------------------------------------------------------------
+template <int J, class Fin>
+__device__ void col_finish(double (&v)[J], double* part, unsigned* ctr, int Kp, Fin fin) {
+    __shared__ double sh[BWARPS][128];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < J; ++j) sh[w][lane + 32 * j] = v[j];
+    __syncthreads();
+    for (int c = threadIdx.x; c < Kp; c += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < BWARPS; ++q) t += sh[q][c];
+        part[(size_t)blockIdx.x * Kp + c] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int c = threadIdx.x; c < Kp; c += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(&part[(size_t)b * Kp + c]);
+        fin(c, t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *ctr = 0u;
+}
+
+template <int J>
+__global__ void __launch_bounds__(BTPB) kb_init(int n, int Kp, const double* __restrict__ b, double* __restrict__ x,
+                                                 double* __restrict__ r, double* part, unsigned* ctr, double* S) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    double v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) v[j] = 0.0;
+    for (int i = blockIdx.x * BWARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * BWARPS) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)i * Kp + lane + 32 * j;
+            const double bi = b[o];
+            x[o] = 0.0;
+            r[o] = bi;
+            v[j] += bi * bi;
+        }
+    }
+    col_finish<J>(v, part, ctr, Kp, [&](int c, double t) {
+        const double bn = sqrt(t);
+        S[S_BNORM * Kp + c] = bn;
+        S[S_K * Kp + c] = 0.0;
+        S[S_RZOLD * Kp + c] = 0.0;
+        S[S_BETA * Kp + c] = 0.0;
+        S[S_ALPHA * Kp + c] = 0.0;
+        S[S_RES * Kp + c] = bn > 0.0 ? 1.0 : 0.0;
+        const bool ok = isfinite(bn);
+        S[S_STATUS * Kp + c] = ok ? (bn > 0.0 && S[S_MAXIT * Kp + c] <= 0.0 ? CPC_ENOCONV : CPC_OK) : CPC_EBREAKDOWN;
+        S[S_ACTIVE * Kp + c] = (ok && bn > 0.0 && S[S_MAXIT * Kp + c] > 0.0) ? 1.0 : 0.0;
+    });
+}
+
+// Any column still active?  Sets the loop condition (one thread).
+__global__ void kb_any_active(int Kp, const double* S, cudaGraphConditionalHandle cond) {
+    pdl_launch_dependents();
+    pdl_wait();
+    unsigned go = 0u;
+    for (int c = 0; c < Kp; ++c) go |= S[S_ACTIVE * Kp + c] > 0.0 ? 1u : 0u;
+    cudaGraphSetConditional(cond, go);
+}
+
+__global__ void kb_guard(cudaGraphConditionalHandle cond) {
+    pdl_launch_dependents();
+    pdl_wait();
+    cudaGraphSetConditional(cond, 0u);
+}
+
+template <int J, class ZT>
+__global__ void __launch_bounds__(BTPB) kb_rz(int n, int Kp, const double* __restrict__ r, const ZT* __restrict__ z,
+                                               double* part, unsigned* ctr, double* S) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    double v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) v[j] = 0.0;
+    for (int i = blockIdx.x * BWARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * BWARPS) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)i * Kp + lane + 32 * j;
+            v[j] += r[o] * cvt_d(z[o]);
+        }
+    }
+    col_finish<J>(v, part, ctr, Kp, [&](int c, double t) {
+        const bool act = S[S_ACTIVE * Kp + c] > 0.0;
+        if (act && (!(t > 0.0) || !isfinite(t))) {
+            S[S_STATUS * Kp + c] = CPC_EBREAKDOWN;
+            S[S_ACTIVE * Kp + c] = 0.0;
+        }
+        S[S_BETA * Kp + c] = (S[S_K * Kp + c] == 0.0 || !act) ? 0.0 : t / S[S_RZOLD * Kp + c];
+        S[S_RZ * Kp + c] = t;
+        S[S_RZOLD * Kp + c] = t;
+    });
+}
+
+template <int J, class ZT>
+__global__ void __launch_bounds__(BTPB) kb_p(int n, int Kp, const ZT* __restrict__ z, double* __restrict__ p,
+                                              const double* S) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    double beta[J];
+    bool first[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        beta[j] = S[S_BETA * Kp + lane + 32 * j];
+        first[j] = S[S_K * Kp + lane + 32 * j] == 0.0;
+    }
+    for (int i = blockIdx.x * BWARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * BWARPS) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)i * Kp + lane + 32 * j;
+            p[o] = first[j] ? cvt_d(z[o]) : cvt_d(z[o]) + beta[j] * p[o];
+        }
+    }
+}
+
+template <int J>
+__global__ void __launch_bounds__(BTPB) kb_spmv_pq(BV<double, double> A, int nslots, int Kp, const double* __restrict__ p,
+                                                    double* __restrict__ q, double* part, unsigned* ctr, double* S) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    double v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) v[j] = 0.0;
+    for (int s = blockIdx.x * BWARPS + (threadIdx.x >> 5); s < nslots; s += gridDim.x * BWARPS) {
+        const int row = A.perm[s];
+        if (row < 0) continue;
+        const int k = s / A.C, r = s % A.C;
+        const int base = A.cptr[k];
+        double acc[J];
+        const double d = A.diag[s];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = d * p[(size_t)row * Kp + lane + 32 * j];
+        brow<J, double>(A.col, A.val, A.C, base, (A.cptr[k + 1] - base) / A.C, r, p, Kp, lane, acc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)row * Kp + lane + 32 * j;
+            q[o] = acc[j];
+            v[j] += p[o] * acc[j];
+        }
+    }
+    col_finish<J>(v, part, ctr, Kp, [&](int c, double t) {
+        const bool act = S[S_ACTIVE * Kp + c] > 0.0;
+        S[S_PQ * Kp + c] = t;
+        if (act && (!(t > 0.0) || !isfinite(t))) {
+            S[S_STATUS * Kp + c] = CPC_EBREAKDOWN;
+            S[S_ACTIVE * Kp + c] = 0.0;
+        }
+        S[S_ALPHA * Kp + c] = S[S_ACTIVE * Kp + c] > 0.0 ? S[S_RZ * Kp + c] / t : 0.0;
+    });
+}
+
+template <int J>
+__global__ void __launch_bounds__(BTPB) kb_update(int n, int Kp, double* __restrict__ x, double* __restrict__ r,
+                                                   const double* __restrict__ p, const double* __restrict__ q,
+                                                   double* part, unsigned* ctr, double* S) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    double alpha[J], v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        alpha[j] = S[S_ALPHA * Kp + lane + 32 * j];
+        v[j] = 0.0;
+    }
+    for (int i = blockIdx.x * BWARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * BWARPS) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)i * Kp + lane + 32 * j;
+            x[o] += alpha[j] * p[o];
+            const double ri = r[o] - alpha[j] * q[o];
+            r[o] = ri;
+            v[j] += ri * ri;
+        }
+    }
+    col_finish<J>(v, part, ctr, Kp, [&](int c, double t) {
+        if (S[S_ACTIVE * Kp + c] <= 0.0) return;
+        const double k = S[S_K * Kp + c] + 1.0;
+        S[S_K * Kp + c] = k;
+        const double res = sqrt(t) / S[S_BNORM * Kp + c];
+        S[S_RES * Kp + c] = res;
+        if (!isfinite(res)) { S[S_STATUS * Kp + c] = CPC_EBREAKDOWN; S[S_ACTIVE * Kp + c] = 0.0; }
+        else if (res < S[S_TOL * Kp + c]) { S[S_STATUS * Kp + c] = CPC_OK; S[S_ACTIVE * Kp + c] = 0.0; }
+        else if (k >= S[S_MAXIT * Kp + c]) { S[S_STATUS * Kp + c] = CPC_ENOCONV; S[S_ACTIVE * Kp + c] = 0.0; }
+    });
+}
+
+// [n][K] user layout <-> [n][Kp] internal layout
+__global__ void kb_pack(int n, int K, int Kp, const double* __restrict__ in, double* __restrict__ out) {
+    pdl_launch_dependents();
+    pdl_wait();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * Kp; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / Kp;
+        const int c = (int)(t % Kp);
+        out[t] = c < K ? in[i * K + c] : 0.0;
+    }
+}
+
+__global__ void kb_unpack(int n, int K, int Kp, const double* __restrict__ in, double* __restrict__ out) {
+    pdl_launch_dependents();
+    pdl_wait();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * K; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / K;
+        const int c = (int)(t % K);
+        out[t] = in[i * Kp + c];
+    }
+}
+
+// Adjoint sources from the forward solutions: b[i][c] = x[i][c] where b[i][c] != 0, else 0
+// (the gradient of J_c = 1/2 sum over the source cells of column c of x^2); also saves x.
+__global__ void kb_adjoint_rhs(int64_t nk, double* __restrict__ b, const double* __restrict__ x, double* __restrict__ xsave) {
+    pdl_launch_dependents();
+    pdl_wait();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nk; t += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = x[t];
+        xsave[t] = xi;
+        b[t] = b[t] != 0.0 ? xi : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Recording (column-wise V-cycle, IC(0), B_co)
+// ---------------------------------------------------------------------------------------------
+template <class VT> VT* bx(Batched& B, int l) { return (VT*)B.lx[l].p; }
+template <class VT> VT* bf(Batched& B, int l) { return (VT*)B.lf[l].p; }
+template <class VT> VT* br(Batched& B, int l) { return (VT*)B.lr[l].p; }
+
+template <int J, class FT, class VT>
+void brec_gs(Level& L, int c, const FT* f, VT* x, int Kp, cudaStream_t s) {
+    const int s0 = L.S.seg[c] * L.S.C, s1 = L.S.seg[c + 1] * L.S.C;
+    if (s1 <= s0) return;
+    const int g = rows_grid(s1 - s0);
+    if constexpr (std::is_same<VT, double>::value)
+        blaunch(kb_gs<J, double, double, FT, VT>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), s0, s1, f, x, Kp);
+    else if (L.vt == VT_BF16)
+        blaunch(kb_gs<J, __nv_bfloat16, float, FT, VT>, g, BTPB, s, bview(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), s0, s1, f, x, Kp);
+    else
+        blaunch(kb_gs<J, float, float, FT, VT>, g, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), s0, s1, f, x, Kp);
+}
+
+template <int J, class FT, class VT>
+void brec_resid(Level& L, const FT* f, const VT* x, VT* r, int Kp, cudaStream_t s) {
+    const int g = std::min(rows_grid(L.S.nslots), 152 * 32);
+    if constexpr (std::is_same<VT, double>::value)
+        blaunch(kb_resid<J, double, double, FT, VT, VT>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nslots, f, x, r, Kp);
+    else if (L.vt == VT_BF16)
+        blaunch(kb_resid<J, __nv_bfloat16, float, FT, VT, VT>, g, BTPB, s, bview(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), L.S.nslots, f, x, r, Kp);
+    else
+        blaunch(kb_resid<J, float, float, FT, VT, VT>, g, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), L.S.nslots, f, x, r, Kp);
+}
+
+template <class VT>
+BV<VT, VT> bfull(const Sell& S) {
+    if constexpr (std::is_same<VT, double>::value) return bview(S, (const double*)S.val.p, (const double*)nullptr);
+    else return bview(S, (const float*)S.val32.p, (const float*)nullptr);
+}
+
+template <int J, class FT, class VT>
+void brec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s) {
+    Batched& B = h.bat;
+    const int Kp = B.Kp;
+    const int nl = (int)h.lev.size();
+    Level& L = h.lev[l];
+    if (l == nl - 1) {
+        const VT* ai = std::is_same<VT, double>::value ? (const VT*)h.Ainv.p : (const VT*)h.Ainv32.p;
+        blaunch(kb_coarse<J, VT, FT, VT>, rows_grid(L.n), BTPB, s, L.n, ai, f, x, Kp);
+        return;
+    }
+    if (zero_guess) blaunch(kb_zero<VT>, 1024, 256, s, (int64_t)L.n * Kp, x);
+    for (int c = 0; c < L.ncolours; ++c) brec_gs<J>(L, c, f, x, Kp, s);
+    brec_resid<J>(L, f, (const VT*)x, br<VT>(B, l), Kp, s);
+    blaunch(kb_apply<J, VT, VT>, std::min(rows_grid(L.SR.nslots), 152 * 32), BTPB, s, bfull<VT>(L.SR), L.SR.nslots,
+            (const VT*)br<VT>(B, l), bf<VT>(B, l + 1), bx<VT>(B, l + 1), Kp);
+    brec_vcycle<J, VT, VT>(h, l + 1, bf<VT>(B, l + 1), bx<VT>(B, l + 1), false, s);
+    blaunch(kb_prolong<J, VT, VT>, std::min(rows_grid(L.SP.nslots), 152 * 32), BTPB, s, bfull<VT>(L.SP), L.SP.nslots,
+            (const VT*)bx<VT>(B, l + 1), x, Kp);
+    for (int c = L.ncolours - 1; c >= 0; --c) brec_gs<J>(L, c, f, x, Kp, s);
+}
+
+template <int J, class TT, class VT>
+void brec_ic(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s) {
+    const int Kp = h.bat.Kp;
+    BV<VT, VT> lv, uv;
+    if constexpr (std::is_same<VT, double>::value) {
+        lv = bview(h.L, (const double*)h.L.val.p, (const double*)nullptr);
+        uv = bview(h.U, (const double*)h.U.val.p, (const double*)h.U.diag.p);
+    } else {
+        lv = bview(h.L, (const float*)h.L.val32.p, (const float*)nullptr);
+        uv = bview(h.U, (const float*)h.U.val32.p, (const float*)h.U.diag32.p);
+    }
+    for (int g = 0; g + 1 < (int)h.L.seg.size(); ++g) {
+        const int s0 = h.L.seg[g] * h.L.C, s1 = h.L.seg[g + 1] * h.L.C;
+        blaunch(kb_lsolve<J, VT, TT, VT>, rows_grid(s1 - s0), BTPB, s, lv, s0, s1, t, y, Kp);
+    }
+    for (int g = 0; g + 1 < (int)h.U.seg.size(); ++g) {
+        const int s0 = h.U.seg[g] * h.U.C, s1 = h.U.seg[g + 1] * h.U.C;
+        blaunch(kb_usolve<J, VT, VT>, rows_grid(s1 - s0), BTPB, s, uv, s0, s1, (const VT*)y, w, zadd, Kp);
+    }
+}
+
+template <int J, class VT>
+void brec_precond(Handle& h, int which, const double* r, VT* z, cudaStream_t s) {
+    Batched& B = h.bat;
+    const int Kp = B.Kp;
+    VT* t = (VT*)B.t.p;
+    VT* y = (VT*)B.y.p;
+    const Sell& A = h.Anat;
+    auto fine_resid = [&]() {
+        const int g = std::min(rows_grid(A.nslots), 152 * 32);
+        if constexpr (std::is_same<VT, double>::value)
+            blaunch(kb_resid<J, double, double, double, VT, VT>, g, BTPB, s, bview(A, (const double*)A.val.p, (const double*)A.diag.p), A.nslots, r, (const VT*)z, t, Kp);
+        else
+            blaunch(kb_resid<J, float, float, double, VT, VT>, g, BTPB, s, bview(A, (const float*)A.val32.p, (const float*)A.diag32.p), A.nslots, r, (const VT*)z, t, Kp);
+    };
+    switch (which) {
+        case CPC_PRECOND_BCO:
+            brec_vcycle<J, double, VT>(h, 0, r, z, true, s);
+            fine_resid();
+            brec_ic<J, VT, VT>(h, t, y, t, z, s);
+            brec_vcycle<J, double, VT>(h, 0, r, z, false, s);
+            break;
+        case CPC_PRECOND_AMG:
+            brec_vcycle<J, double, VT>(h, 0, r, z, true, s);
+            brec_vcycle<J, double, VT>(h, 0, r, z, false, s);
+            break;
+        case CPC_PRECOND_IC0:
+            brec_ic<J, double, VT>(h, r, y, z, (VT*)nullptr, s);
+            break;
+        case CPC_PRECOND_BHAT:
+            brec_vcycle<J, double, VT>(h, 0, r, z, true, s);
+            brec_vcycle<J, double, VT>(h, 0, r, z, false, s);
+            brec_ic<J, double, VT>(h, r, y, t, z, s);
+            break;
+        default:
+            fail(CPC_EINVAL, "batched solve supports B_co, AMG, IC(0) and B^");
+    }
+}
+
+template <int J, class VT>
+void brec_loop(Handle& h, cudaGraph_t g, cudaStream_t cs, cudaGraphNode_t* dep, size_t ndep, cudaGraphNode_t* out_node) {
+    Batched& B = h.bat;
+    const int Kp = B.Kp;
+    const int n = h.n;
+    cudaGraphConditionalHandle cond;
+    CPC_CK(cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CPC_CK(cudaGraphAddNode(out_node, g, dep, nullptr, ndep, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CPC_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    blaunch(kb_guard, 1, 32, cs, cond);
+    VT* z = (VT*)B.z.p;
+    brec_precond<J, VT>(h, h.opt.precond, B.r.p, z, cs);
+    const int vg = std::min(rows_grid(n), 152 * 8);
+    blaunch(kb_rz<J, VT>, vg, BTPB, cs, n, Kp, (const double*)B.r.p, (const VT*)z, B.partial.p, h.counter.p + 1, B.S.p);
+    blaunch(kb_p<J, VT>, vg, BTPB, cs, n, Kp, (const VT*)z, B.p.p, (const double*)B.S.p);
+    const Sell& A = h.Anat;
+    blaunch(kb_spmv_pq<J>, std::min(rows_grid(A.nslots), 152 * 8), BTPB, cs, bview(A, (const double*)A.val.p, (const double*)A.diag.p),
+            A.nslots, Kp, (const double*)B.p.p, B.q.p, B.partial.p, h.counter.p + 1, B.S.p);
+    blaunch(kb_update<J>, vg, BTPB, cs, n, Kp, B.x.p, B.r.p, (const double*)B.p.p, (const double*)B.q.p, B.partial.p,
+            h.counter.p + 1, B.S.p);
+    blaunch(kb_any_active, 1, 32, cs, Kp, (const double*)B.S.p, cond);
+    CPC_CK(cudaStreamEndCapture(cs, &body));
+}
+
+// One graph: pack B, init, while(any active) { iteration }, [adjoint: sources, init, while {...}].
+template <int J, class VT>
+void build_batched_graph(Handle& h, bool with_adjoint) {
+    Batched& B = h.bat;
+    const int Kp = B.Kp;
+    const int n = h.n;
+    cudaStream_t cs;
+    CPC_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{cs};
+    cudaGraph_t g;
+    CPC_CK(cudaGraphCreate(&g, 0));
+    const int vg = std::min(rows_grid(n), 152 * 8);
+    auto capture_into = [&](cudaGraphNode_t* deps, size_t ndeps, auto&& body) -> std::vector<cudaGraphNode_t> {
+        std::vector<cudaGraphNode_t> before;
+        size_t nn = 0;
+        CPC_CK(cudaGraphGetNodes(g, nullptr, &nn));
+        before.resize(nn);
+        CPC_CK(cudaGraphGetNodes(g, before.data(), &nn));
+        CPC_CK(cudaStreamBeginCaptureToGraph(cs, g, deps, nullptr, ndeps, cudaStreamCaptureModeThreadLocal));
+        body();
+        CPC_CK(cudaStreamEndCapture(cs, &g));
+        size_t nn2 = 0;
+        CPC_CK(cudaGraphGetNodes(g, nullptr, &nn2));
+        std::vector<cudaGraphNode_t> all(nn2);
+        CPC_CK(cudaGraphGetNodes(g, all.data(), &nn2));
+        std::vector<cudaGraphNode_t> added;
+        for (auto nd : all) if (std::find(before.begin(), before.end(), nd) == before.end()) added.push_back(nd);
+        // leaves among the added nodes
+        std::vector<cudaGraphNode_t> leaves;
+        for (auto nd : added) {
+            size_t nout = 0;
+            CPC_CK(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nout));
+            if (nout == 0) leaves.push_back(nd);
+        }
+        return leaves;
+    };
+    auto l1 = capture_into(nullptr, 0, [&] {
+        blaunch(kb_pack, 2048, 256, cs, n, B.K, Kp, (const double*)B.user_b, B.b.p);
+        blaunch(kb_init<J>, vg, BTPB, cs, n, Kp, (const double*)B.b.p, B.x.p, B.r.p, B.partial.p, h.counter.p + 1, B.S.p);
+    });
+    cudaGraphNode_t w1;
+    brec_loop<J, VT>(h, g, cs, l1.data(), l1.size(), &w1);
+    cudaGraphNode_t tail = w1;
+    if (with_adjoint) {
+        auto l2 = capture_into(&w1, 1, [&] {
+            blaunch(kb_adjoint_rhs, 2048, 256, cs, (int64_t)n * Kp, B.b.p, (const double*)B.x.p, B.xfwd.p);
+            blaunch(kb_unpack, 2048, 256, cs, n, B.K, Kp, (const double*)B.xfwd.p, B.user_x);
+            CPC_CK(cudaMemcpyAsync(B.kfwd.p, B.S.p + (size_t)S_K * Kp, sizeof(double) * Kp, cudaMemcpyDeviceToDevice, cs));
+            CPC_CK(cudaMemcpyAsync(B.kfwd.p + Kp, B.S.p + (size_t)S_STATUS * Kp, sizeof(double) * Kp, cudaMemcpyDeviceToDevice, cs));
+            blaunch(kb_init<J>, vg, BTPB, cs, n, Kp, (const double*)B.b.p, B.x.p, B.r.p, B.partial.p, h.counter.p + 1, B.S.p);
+        });
+        cudaGraphNode_t w2;
+        brec_loop<J, VT>(h, g, cs, l2.data(), l2.size(), &w2);
+        tail = w2;
+    }
+    capture_into(&tail, 1, [&] {
+        blaunch(kb_unpack, 2048, 256, cs, n, B.K, Kp, (const double*)B.x.p, with_adjoint ? B.user_lambda : B.user_x);
+    });
+    cudaGraphExec_t ge;
+    CPC_CK(cudaGraphInstantiate(&ge, g, 0));
+    B.graph = g;
+    B.gexec = ge;
+}
+
+}  // namespace
+
+void destroy_batched(Handle& h) {
+    Batched& B = h.bat;
+    if (B.gexec) cudaGraphExecDestroy(B.gexec);
+    if (B.graph) cudaGraphDestroy(B.graph);
+    B.gexec = nullptr;
+    B.graph = nullptr;
+}
+
+// Allocate the block vectors for K columns (kept across calls with the same padded width).
+static void ensure_batched(Handle& h, int K, bool adjoint, double* user_b, double* user_x, double* user_lambda) {
+    Batched& B = h.bat;
+    const int Kp = (K + 31) / 32 * 32;
+    if (Kp > 128) fail(CPC_EINVAL, "at most 128 right-hand sides per batched call");
+    const bool fp64 = h.opt.precision == CPC_PREC_FP64;
+    const size_t vsz = fp64 ? sizeof(double) : sizeof(float);
+    if (B.Kp != Kp) {
+        destroy_batched(h);
+        B = Batched{};
+        B.Kp = Kp;
+        const size_t nk = (size_t)h.n * Kp;
+        B.b.alloc(nk); B.x.alloc(nk); B.r.alloc(nk); B.p.alloc(nk); B.q.alloc(nk); B.xfwd.alloc(nk);
+        B.z.alloc(nk * vsz); B.t.alloc(nk * vsz); B.y.alloc(nk * vsz);
+        const int nl = (int)h.lev.size();
+        B.lx.resize(nl); B.lf.resize(nl); B.lr.resize(nl);
+        for (int l = 0; l < nl; ++l) {
+            const size_t m = (size_t)h.lev[l].n * Kp * vsz;
+            B.lx[l].alloc(m); B.lf[l].alloc(m); B.lr[l].alloc(m);
+        }
+        B.S.alloc((size_t)NB_STATE * Kp);
+        B.partial.alloc((size_t)152 * 32 * Kp);
+        B.kfwd.alloc(2 * (size_t)Kp);
+    }
+    if (B.gexec && (B.K != K || B.adjoint != adjoint || B.user_b != user_b || B.user_x != user_x ||
+                    B.user_lambda != user_lambda)) destroy_batched(h);
+    B.K = K;
+    B.adjoint = adjoint;
+    B.user_b = user_b;
+    B.user_x = user_x;
+    B.user_lambda = user_lambda;
+}
+
+void solve_batched(Handle& h, int K, const double* b, double* x, double* lambda, double tol, int maxit,
+                   int* iters, int* status, int* iters_adj, int* status_adj) {
+    ensure_batched(h, K, lambda != nullptr, (double*)b, x, lambda);
+    Batched& B = h.bat;
+    const int Kp = B.Kp;
+    if (!B.gexec) {
+        const bool fp64 = h.opt.precision == CPC_PREC_FP64;
+        const int J = Kp / 32;
+        const bool adj = lambda != nullptr;
+        if (fp64) {
+            if (J == 1) build_batched_graph<1, double>(h, adj);
+            else if (J == 2) build_batched_graph<2, double>(h, adj);
+            else if (J == 3) build_batched_graph<3, double>(h, adj);
+            else build_batched_graph<4, double>(h, adj);
+        } else {
+            if (J == 1) build_batched_graph<1, float>(h, adj);
+            else if (J == 2) build_batched_graph<2, float>(h, adj);
+            else if (J == 3) build_batched_graph<3, float>(h, adj);
+            else build_batched_graph<4, float>(h, adj);
+        }
+    }
+    cudaStream_t s = h.s;
+    std::vector<double> st((size_t)NB_STATE * Kp, 0.0);
+    for (int c = 0; c < Kp; ++c) {
+        st[(size_t)S_TOL * Kp + c] = tol;
+        st[(size_t)S_MAXIT * Kp + c] = c < K ? (double)maxit : 0.0;
+    }
+    CPC_CK(cudaMemcpyAsync(B.S.p, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, s));
+    CPC_CK(cudaGraphLaunch(B.gexec, s));
+    CPC_CK(cudaMemcpyAsync(st.data(), B.S.p, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, s));
+    std::vector<double> kf(2 * (size_t)Kp, 0.0);
+    if (lambda) CPC_CK(cudaMemcpyAsync(kf.data(), B.kfwd.p, sizeof(double) * 2 * Kp, cudaMemcpyDeviceToHost, s));
+    CPC_CK(cudaStreamSynchronize(s));
+    for (int c = 0; c < K; ++c) {
+        const int ki = (int)st[(size_t)S_K * Kp + c];
+        const int si = (int)st[(size_t)S_STATUS * Kp + c];
+        if (lambda) {
+            iters[c] = (int)kf[c];
+            if (status) status[c] = (int)kf[Kp + c];
+            if (iters_adj) iters_adj[c] = ki;
+            if (status_adj) status_adj[c] = si;
+        } else {
+            iters[c] = ki;
+            if (status) status[c] = si;
+        }
+    }
+}
+
+}  // namespace cpc

@@ -26,6 +26,22 @@ struct Level {
     DBuf<float> x32, f32, r32;
 };
 
+// Batched PCG state: block vectors [n][Kp] (Kp = K rounded up to 32), level vectors in the
+// preconditioner's precision (raw bytes), per-column scalars, and the captured graph.
+struct Batched {
+    int K = 0, Kp = 0;
+    bool adjoint = false;
+    DBuf<double> b, x, r, p, q, xfwd;
+    DBuf<char> z, t, y;
+    std::vector<DBuf<char>> lx, lf, lr;
+    DBuf<double> S, partial, kfwd;
+    double* user_b = nullptr;
+    double* user_x = nullptr;
+    double* user_lambda = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
 // Device-side scalars of one PCG run (all reductions finish in fixed order).
 struct PcgState {
     double bnorm, rz, rz_old, pq, alpha, beta, rr, tol, res;
@@ -69,6 +85,7 @@ struct Handle {
     int tail_cluster = 0;
     DBuf<char> tail_desc;
     std::vector<DBuf<int>> tail_seg;
+    Batched bat;
     float ms_ic0 = 0.f, ms_amg = 0.f;
     std::string err;
     ~Handle();
@@ -82,6 +99,11 @@ void tpfa_gradient(int nx, int ny, int nz, const double* logk, double kzr, int d
 void tpfa_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask, int* rowptr,
                    int* col, double* val, cudaStream_t s);
 void setup_handle(Handle& h, const cpc_csr& A);
+
+// batched.cu
+void solve_batched(Handle& h, int K, const double* b, double* x, double* lambda, double tol, int maxit,
+                   int* iters, int* status, int* iters_adj, int* status_adj);
+void destroy_batched(Handle& h);
 
 // tail.cu
 constexpr int64_t TAIL_NNZ_MAX = 1;            // default: only the coarsest solve runs in the cluster kernel
