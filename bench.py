@@ -34,6 +34,9 @@ TOL = 1e-6
 MAXIT = 5000
 METRIC = "PCG ms to 1e-6 rel. residual (combined vs AMG/ILU alone, FP32 vs FP64 prec), %HBM peak"
 L2_FLUSH_BYTES = 512 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one fine-level k_gs launch from the committed ncu
+# capture (profiles/k_gs_fine_correlated3d_128x128x64.md); None until a capture of the current kernel.
+TRAFFIC_K_GS_FINE = 60980480
 
 
 def peaks():
@@ -241,12 +244,30 @@ def gpu_arm(args, rank, world):
     if world == 1 and not args.no_adjoint:
         out["adjoint"] = adjoint_arm(dev, stream)
 
-    # dominant-kernel roofline: the fine SpMV (SELL-32, FP64), one launch per event pair, L2 flushed
+    # dominant kernel (k_gs, the Gauss-Seidel colour sweep: largest share of the ncu launch list):
+    # its fine-level launches timed live -- one red and one black launch per event pair, L2 flushed.
+    # Algorithmic bytes per launch: half of (24 n + 12 nnz) = the colour's rows of A (values,
+    # columns), diagonal, perm, f, x written, and the other colour's x read once.
     xv = torch.randn(p.n, dtype=torch.float64, device=dev)
-    yv = torch.empty_like(xv)
+    yv = torch.zeros_like(xv)
+    info0 = s_bco.level_info(0)
     for _ in range(3):
-        s_bco.spmv(xv, yv)
+        s_bco.level_apply(0, 5, xv, yv)
     kms = []
+    for _ in range(20):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_bco.level_apply(0, 5, xv, yv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms.append(e0.elapsed_time(e1) / info0["ncolours"])
+    kbytes = (24 * info0["n"] + 12 * info0["nnz"]) // info0["ncolours"]
+    peak, peak_kind = peaks()
+    k_avg = float(np.mean(kms))
+    achieved = kbytes / (k_avg * 1e-3) / 1e9
+    # the fine SpMV (same SELL layout), for reference
+    sms = []
     for _ in range(20):
         flush_l2()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -254,18 +275,18 @@ def gpu_arm(args, rank, world):
         s_bco.spmv(xv, yv)
         e1.record(stream)
         torch.cuda.synchronize()
-        kms.append(e0.elapsed_time(e1))
-    info0 = s_bco.level_info(0)
-    kbytes = a_pass_bytes(info0["n"], info0["nnz"])
-    peak, peak_kind = peaks()
-    k_avg = float(np.mean(kms))
-    achieved = kbytes / (k_avg * 1e-3) / 1e9
+        sms.append(e0.elapsed_time(e1))
+    sbytes = a_pass_bytes(info0["n"], info0["nnz"])
+    spmv = dict(kernel="k_spmv (fine A, SELL-32, FP64)", bytes_per_launch=sbytes, avg_launch_ms=round(float(np.mean(sms)), 5),
+                achieved=round(sbytes / (np.mean(sms) * 1e-3) / 1e9, 1))
     bpi = bytes_per_iteration(s_bco, "bco")
     headline_ms = float(np.mean(ms))
     out.update(dict(p=p, arms=arms, clocks=clk, e2e_ms=e2e_ms, true_res=true_res, setups=setups,
                     roofline=dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
-                                  frac=round(achieved / peak, 4), traffic=None, kernel="k_spmv (fine A, SELL-32, FP64)",
-                                  bytes_per_launch=kbytes, avg_launch_ms=round(k_avg, 5), peak_kind=peak_kind),
+                                  frac=round(achieved / peak, 4), traffic=TRAFFIC_K_GS_FINE,
+                                  kernel="k_gs (Gauss-Seidel colour sweep, fine level, red/black, FP64)",
+                                  bytes_per_launch=kbytes, avg_launch_ms=round(k_avg, 5), peak_kind=peak_kind,
+                                  spmv=spmv),
                     headline_ms=headline_ms, bytes_per_iter=bpi, nodes=None, nlevels=s_bco.nlevels,
                     levels=[s_bco.level_info(l) for l in range(s_bco.nlevels)]))
     out["solve_gbs"] = bpi * iters[-1] / (headline_ms * 1e-3) / 1e9
@@ -424,6 +445,53 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """The slowest rank's time (all ranks call this; a no-op for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_ms_per_solve(ms_per_step: float, world: int) -> float:
+    """Independent replicas: every step solves `world` systems, so the job's time per solve is
+    the (slowest) step time over world."""
+    return ms_per_step / world
+
+
+def profile_mode(name):
+    """One preconditioner application plus one fine-level sweep between cudaProfilerStart/Stop
+    (for `ncu --profile-from-start off`), after two untimed warm-up applications."""
+    import torch
+    from paper_1205_6113_gb300 import cpc
+    pre, prec = name.split("_")
+    dev = torch.device("cuda:0")
+    p = inputs.workload(WORKLOAD)
+    logk = torch.tensor(p.logk, device=dev)
+    rowptr, col, val = cpc.tpfa_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+    s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order="colour")
+    r = torch.tensor(p.rhs(), device=dev)
+    z = torch.empty_like(r)
+    y = torch.zeros_like(r)
+    sweep = prec == "fp64"          # level operators are exposed in FP64 mode
+    for _ in range(2):
+        s.apply(r, z=z)
+        if sweep:
+            s.level_apply(0, 5, r, y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    s.apply(r, z=z)
+    if sweep:
+        s.level_apply(0, 5, r, y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profiled": name, "launches_per_iteration": s.solve_launches()[0]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,7 +501,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--profile", default=None, help="e.g. bco_fp64: one application for ncu, then exit")
     args = ap.parse_args()
+    if args.profile:
+        profile_mode(args.profile)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     if world > 1:
@@ -443,18 +515,12 @@ def main():
         reference_arm(args, rank, world)
         return
     out = gpu_arm(args, rank, world)
-    ms_local = float(np.sum(out["headline"]["ms"]))
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([ms_local], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_local = float(t.item())
+    ms_local = max_over_ranks(float(np.sum(out["headline"]["ms"])), world)
     if rank != 0:
         return
     k = args.steps
     ms_per_step = ms_local / k
-    value = ms_per_step / world          # whole job: world solves per step time
+    value = whole_job_ms_per_solve(ms_per_step, world)
     p = out["p"]
     iters = out["headline"]["iters"][-1]
     per_it, fixed = out["launches"]

@@ -73,8 +73,9 @@ typedef struct {
     double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
     int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (256)         */
     int32_t max_levels;     /* at most this many levels                            (20)          */
-    int64_t tail_nnz_max;   /* coarse levels with at most this many nonzeros run as one cluster
-                               kernel; larger levels as separate launches; 0 = library default    */
+    int64_t tail_nnz_max;   /* coarse levels run as one cluster kernel with their operators in
+                               shared memory when they fit and have at most this many nonzeros;
+                               0 = library default (capacity decides), < 0 = never               */
     void* stream;           /* cudaStream_t used by every call on the handle       (NULL)        */
 } cpc_options;
 
@@ -218,7 +219,8 @@ int cpc_ic0_values(const cpc_handle* h, double* lu);
 
 /* Level operators on device vectors, for parity tests: op 0 y = A_l x; 1 y = S_l x (forward
  * Gauss-Seidel sweep, zero guess); 2 y = S_l^T x (backward sweep); 3 y = A_l^{-1} x (coarsest
- * level); 4 y = V-cycle from level l with zero initial guess.  Asynchronous. */
+ * level); 4 y = V-cycle from level l with zero initial guess; 5 one forward Gauss-Seidel sweep on
+ * A_l y = x starting from the given y (one launch per colour, nothing else).  Asynchronous. */
 int cpc_level_apply(cpc_handle* h, int32_t level, int32_t op, const double* x, double* y);
 
 #ifdef __cplusplus

@@ -105,11 +105,11 @@ __global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, cons
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = VT(0);
     brow<J, VT>(A.col, A.val, A.C, base, (A.cptr[k + 1] - base) / A.C, r, x, Kp, lane, acc);
-    const VT d = Cv<VT>::f(A.diag[s]);
+    const VT dinv = Cv<VT>::f(A.diag[s]);        // the view's diagonal field holds 1 / a_ii
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         const size_t o = (size_t)row * Kp + lane + 32 * j;
-        x[o] = (Cv<VT>::f(f[o]) - acc[j]) / d;
+        x[o] = (Cv<VT>::f(f[o]) - acc[j]) * dinv;
     }
 }
 
@@ -252,11 +252,11 @@ __global__ void __launch_bounds__(BTPB) kb_usolve(BV<MT, MT> U, int s0, int s1, 
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = VT(0);
     brow<J, VT>(U.col, U.val, U.C, base, (U.cptr[k + 1] - base) / U.C, r, w, Kp, lane, acc);
-    const VT d = Cv<VT>::f(U.diag[s]);
+    const VT dinv = Cv<VT>::f(U.diag[s]);        // 1 / u_ii
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         const size_t o = (size_t)row * Kp + lane + 32 * j;
-        const VT v = (y[o] - acc[j]) / d;
+        const VT v = (y[o] - acc[j]) * dinv;
         w[o] = v;
         if (zadd) zadd[o] += v;
     }
@@ -510,11 +510,11 @@ void brec_gs(Level& L, int c, const FT* f, VT* x, int Kp, cudaStream_t s) {
     if (s1 <= s0) return;
     const int g = rows_grid(s1 - s0);
     if constexpr (std::is_same<VT, double>::value)
-        blaunch(kb_gs<J, double, double, FT, VT>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), s0, s1, f, x, Kp);
+        blaunch(kb_gs<J, double, double, FT, VT>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), s0, s1, f, x, Kp);
     else if (L.vt == VT_BF16)
-        blaunch(kb_gs<J, __nv_bfloat16, float, FT, VT>, g, BTPB, s, bview(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), s0, s1, f, x, Kp);
+        blaunch(kb_gs<J, __nv_bfloat16, float, FT, VT>, g, BTPB, s, bview(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), s0, s1, f, x, Kp);
     else
-        blaunch(kb_gs<J, float, float, FT, VT>, g, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), s0, s1, f, x, Kp);
+        blaunch(kb_gs<J, float, float, FT, VT>, g, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), s0, s1, f, x, Kp);
 }
 
 template <int J, class FT, class VT>
@@ -562,10 +562,10 @@ void brec_ic(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s) {
     BV<VT, VT> lv, uv;
     if constexpr (std::is_same<VT, double>::value) {
         lv = bview(h.L, (const double*)h.L.val.p, (const double*)nullptr);
-        uv = bview(h.U, (const double*)h.U.val.p, (const double*)h.U.diag.p);
+        uv = bview(h.U, (const double*)h.U.val.p, (const double*)h.U.dinv.p);
     } else {
         lv = bview(h.L, (const float*)h.L.val32.p, (const float*)nullptr);
-        uv = bview(h.U, (const float*)h.U.val32.p, (const float*)h.U.diag32.p);
+        uv = bview(h.U, (const float*)h.U.val32.p, (const float*)h.U.dinv32.p);
     }
     for (int g = 0; g + 1 < (int)h.L.seg.size(); ++g) {
         const int s0 = h.L.seg[g] * h.L.C, s1 = h.L.seg[g + 1] * h.L.C;

@@ -100,8 +100,8 @@ struct Sell {
     int nslots = 0, nchunks = 0;
     int64_t nelem = 0;
     DBuf<int> perm, cptr, col;
-    DBuf<double> val, diag;            // FP64 copy (always)
-    DBuf<float> val32, diag32;         // FP32 copy (mixed precision)
+    DBuf<double> val, diag, dinv;      // FP64 copy (always); dinv = 1 / diag (split diagonal only)
+    DBuf<float> val32, diag32, dinv32; // FP32 copy (mixed precision)
     DBuf<__nv_bfloat16> val16;         // BF16 copy of off-diagonals (coarse levels, mode 2)
     std::vector<int> seg;
 };

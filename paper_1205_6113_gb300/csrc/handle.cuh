@@ -83,7 +83,9 @@ struct Handle {
     // coarse levels >= tail_start run as one cluster kernel (tail.cu)
     int tail_start = 0;
     int tail_cluster = 0;
+    size_t tail_smem = 0;
     DBuf<char> tail_desc;
+    DBuf<char> tail_img;
     std::vector<DBuf<int>> tail_seg;
     Batched bat;
     float ms_ic0 = 0.f, ms_amg = 0.f;
@@ -106,7 +108,7 @@ void solve_batched(Handle& h, int K, const double* b, double* x, double* lambda,
 void destroy_batched(Handle& h);
 
 // tail.cu
-constexpr int64_t TAIL_NNZ_MAX = 1;            // default: only the coarsest solve runs in the cluster kernel
+constexpr int64_t TAIL_NNZ_MAX = int64_t(1) << 40;  // default: shared-memory capacity decides
 void setup_tail(Handle& h, int64_t tail_nnz_max);
 void record_tail(Handle& h, int level, const void* f0, void* x0, cudaStream_t s);
 

@@ -673,6 +673,11 @@ void natural_slots(int n, int C, cudaStream_t s, DBuf<int>& perm, int& nslots, s
     CPC_LAUNCH_CK();
 }
 
+__global__ void k_recip(int n, const double* d, double* r) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = 1.0 / d[i];
+}
+
 // Chunk height for rows of average length avg: 32 / G rows per warp with G lanes sharing a row,
 // G the largest power of two <= avg / 4 (1..8), so that a row costs one round of loads.
 int choose_chunk(double avg) {
@@ -700,6 +705,10 @@ void build_sell(const int* ptr, const int* col, const double* val, const DBuf<in
     if (split_diag) S.diag.alloc(nslots);
     k_sell_fill<<<nblk(nslots), TPB, 0, s>>>(slots.p, nslots, C, ptr, col, val, mode, S.cptr.p, imap, S.perm.p,
                                              S.col.p, S.val.p, split_diag ? S.diag.p : nullptr);
+    if (split_diag) {       // reciprocal diagonal: the sweeps multiply instead of dividing
+        S.dinv.alloc(nslots);
+        k_recip<<<nblk(nslots), TPB, 0, s>>>(nslots, S.diag.p, S.dinv.p);
+    }
     CPC_LAUNCH_CK();
 }
 
@@ -720,6 +729,8 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
     if (S.diag.p) {
         S.diag32.alloc(S.nslots);
         k_to_f32<<<nblk(S.nslots), TPB, 0, s>>>(S.nslots, S.diag.p, S.diag32.p);
+        S.dinv32.alloc(S.nslots);
+        k_to_f32<<<nblk(S.nslots), TPB, 0, s>>>(S.nslots, S.dinv.p, S.dinv32.p);
     }
     if (vt == VT_BF16) {
         S.val16.alloc(S.nelem);
@@ -1162,7 +1173,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         k_to_f32<<<nblk((int64_t)h.nc * h.nc), TPB, 0, s>>>((int64_t)h.nc * h.nc, h.Ainv.p, h.Ainv32.p);
         h.z32.alloc(h.n); h.t32.alloc(h.n); h.y32.alloc(h.n);
     }
-    setup_tail(h, h.opt.tail_nnz_max > 0 ? h.opt.tail_nnz_max : TAIL_NNZ_MAX);
+    setup_tail(h, h.opt.tail_nnz_max == 0 ? TAIL_NNZ_MAX : h.opt.tail_nnz_max);
     // PCG and preconditioner vectors
     const size_t n = h.n;
     h.b.alloc(n); h.x.alloc(n); h.r.alloc(n); h.z.alloc(n); h.p.alloc(n); h.q.alloc(n);

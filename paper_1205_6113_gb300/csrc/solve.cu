@@ -52,7 +52,8 @@ __device__ __forceinline__ VT sub_sum(VT v, int C) {
     return v;
 }
 
-// Gauss-Seidel over the rows of one colour (chunks [c0, c1)): x_i = (f_i - sum_{j!=i} a_ij x_j) / a_ii.
+// Gauss-Seidel over the rows of one colour (chunks [c0, c1)): x_i = (f_i - sum_{j!=i} a_ij x_j) / a_ii,
+// with the view's diagonal field holding 1 / a_ii (a multiply instead of an FP64 division).
 // Rows of one colour are not coupled, so they update in parallel exactly as in sequential order.
 template <class MT, class DT, class FT, class VT>
 __global__ void __launch_bounds__(SELL_TPB) k_gs(SV<MT, DT> A, int c0, int c1, const FT* __restrict__ f, VT* x) {
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(SELL_TPB) k_gs(SV<MT, DT> A, int c0, int c1, c
     const int row = A.perm[s];
     VT dot = sell_dot<VT, true>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], x);
     dot = sub_sum(dot, C);
-    if (g == 0 && row >= 0) x[row] = (Cv<VT>::f(f[row]) - dot) / Cv<VT>::f(A.diag[s]);
+    if (g == 0 && row >= 0) x[row] = (Cv<VT>::f(f[row]) - dot) * Cv<VT>::f(A.diag[s]);
 }
 
 // r = f - A x over all chunks (grid-stride over chunks).
@@ -187,8 +188,8 @@ __global__ void __launch_bounds__(SELL_TPB) k_lsolve(SV<MT, MT> L, int c0, int c
     if (g == 0 && row >= 0) y[row] = Cv<VT>::f(t[row]) - dot;
 }
 
-// Backward solve with U, rows of one level: w_i = (y_i - sum_{j>i} u_ij w_j) / u_ii; optionally
-// z_i += w_i in the same pass.
+// Backward solve with U, rows of one level: w_i = (y_i - sum_{j>i} u_ij w_j) / u_ii (the view's
+// diagonal field holds 1 / u_ii); optionally z_i += w_i in the same pass.
 template <class MT, class VT>
 __global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> U, int c0, int c1, const VT* __restrict__ y, VT* w,
                                                       VT* zadd) {
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> U, int c0, int c
     VT dot = sell_dot<VT, true>(U.col, U.val, U.cptr[k] + g * C + r, U.cptr[k + 1], w);
     dot = sub_sum(dot, C);
     if (g == 0 && row >= 0) {
-        const VT v = (y[row] - dot) / Cv<VT>::f(U.diag[s]);
+        const VT v = (y[row] - dot) * Cv<VT>::f(U.diag[s]);
         w[row] = v;
         if (zadd) zadd[row] += v;
     }
@@ -402,12 +403,12 @@ void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
     if (c1 <= c0) return;
     const int g = blocks_for_chunks(c1 - c0);
     if constexpr (std::is_same<VT, double>::value) {
-        launch(k_gs<double, double, FT, VT>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), c0, c1, f, x);
+        launch(k_gs<double, double, FT, VT>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), c0, c1, f, x);
     } else {
         if (L.vt == VT_BF16)
-            launch(k_gs<__nv_bfloat16, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), c0, c1, f, x);
+            launch(k_gs<__nv_bfloat16, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
         else
-            launch(k_gs<float, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), c0, c1, f, x);
+            launch(k_gs<float, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
     }
 }
 
@@ -478,10 +479,10 @@ void rec_ic_solve(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s
     SV<VT, VT> lv, uv;
     if constexpr (std::is_same<VT, double>::value) {
         lv = view(L, L.val.p, (const double*)nullptr);
-        uv = view(U, U.val.p, U.diag.p);
+        uv = view(U, U.val.p, U.dinv.p);
     } else {
         lv = view(L, (const float*)L.val32.p, (const float*)nullptr);
-        uv = view(U, (const float*)U.val32.p, (const float*)U.diag32.p);
+        uv = view(U, (const float*)U.val32.p, (const float*)U.dinv32.p);
     }
     for (int g = 0; g + 1 < (int)L.seg.size(); ++g) {
         const int c0 = L.seg[g], c1 = L.seg[g + 1];
@@ -587,6 +588,10 @@ void level_apply(Handle& h, int l, int op, const double* x, double* y) {
         case 3:
             if (!last) fail(CPC_EINVAL, "not the coarsest level");
             launch(k_coarse<double, double, double>, std::max(1, (L.n + 7) / 8), 256, s, L.n, (const double*)h.Ainv.p, x, y);
+            break;
+        case 5:                                                   // sweep from the given y (no zeroing)
+            if (last) fail(CPC_EINVAL, "coarsest level has no smoother");
+            for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, x, y, s);
             break;
         case 4:
             if (l >= h.tail_start) {
