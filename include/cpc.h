@@ -71,7 +71,7 @@ typedef struct {
     int32_t ic_order;       /* 0: natural order (level-scheduled); 1: multicolour order of the
                                finest level's Gauss-Seidel colouring                (default 0)   */
     double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
-    int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (256)         */
+    int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (512)         */
     int32_t max_levels;     /* at most this many levels                            (20)          */
     int64_t tail_nnz_max;   /* coarse levels run as one cluster kernel with their operators in
                                shared memory when they fit and have at most this many nonzeros;

@@ -158,7 +158,7 @@ class Solver:
     """
 
     def __init__(self, rowptr, col, val, precond="bco", precision="fp64", ic_order="natural", theta=0.25,
-                 coarse_max=256, max_levels=20, tail_nnz_max=0, stream=None):
+                 coarse_max=512, max_levels=20, tail_nnz_max=0, stream=None):
         torch = _torch()
         lib = load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()

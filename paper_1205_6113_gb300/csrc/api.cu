@@ -52,7 +52,7 @@ int cpc_default_options(cpc_options* opt) {
     opt->precision = CPC_PREC_FP64;
     opt->ic_order = 0;
     opt->theta = 0.25;
-    opt->coarse_max = 256;
+    opt->coarse_max = 512;
     opt->max_levels = 20;
     opt->tail_nnz_max = 0;
     opt->stream = nullptr;

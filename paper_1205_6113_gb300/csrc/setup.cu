@@ -740,51 +740,97 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 }
 
 // ============================================================================================
-// Coarsest level: dense Cholesky and explicit inverse, one block.
+// Coarsest level: dense Cholesky A_c = L L^T and the explicit inverse (Algorithm 3.2, step 2(b)).
+// Right-looking factorisation, one launch per column j over all SMs; then one warp per column of
+// A_c^{-1} = L^{-T} L^{-1}.
 // ============================================================================================
-__global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const double* val, double* M) {
+__global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const double* val, double* M, double* c0) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p) M[(size_t)i * n + col[p]] = val[p];
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        M[(size_t)i * n + col[p]] = val[p];
+        if (col[p] == 0) c0[i] = val[p];
+    }
 }
 
-__global__ void k_dense_chol_inverse(int n, double* M, double* Ainv, int* fail) {
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
+// Step j.  cj = column j of the current trailing matrix (contiguous copy, rows >= j); l_jj = sqrt(a_jj),
+// l_ij = a_ij / l_jj.  One warp per row i > j updates a_ik -= l_ij l_kj for j < k <= i and writes the
+// updated a_{i,j+1} into cn, the copy of column j + 1 for the next step.  Column j of M keeps the
+// unscaled a_ij; k_chol_finish scales it.
+__global__ void k_chol_step(int n, int j, double* __restrict__ M, const double* __restrict__ cj,
+                            double* __restrict__ cn, double* __restrict__ Ld, int* fail) {
+    if (*(volatile int*)fail) return;
+    const double d = cj[j];
+    if (!(d > 0.0) || !isfinite(d)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *fail = 1;
+        return;
+    }
+    const double s = sqrt(d);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ld[j] = s;
+        if (j + 1 < n) cn[j + 1] = M[(size_t)(j + 1) * n + j + 1] - (cj[j + 1] / s) * (cj[j + 1] / s);
+    }
+    const int i = j + 2 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const double lij = cj[i] / s;
+    double* row = M + (size_t)i * n;
+    for (int k = j + 1 + lane; k <= i; k += 32) {
+        const double v = row[k] - lij * (cj[k] / s);
+        row[k] = v;
+        if (k == j + 1) cn[i] = v;
+    }
+}
+
+// L into the lower triangle (diagonal included) and L^T into the strict upper triangle.
+__global__ void k_chol_finish(int n, double* __restrict__ M, const double* __restrict__ Ld) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    const int i = (int)(t / n), k = (int)(t % n);
+    if (k < i) {
+        const double l = M[t] / Ld[k];
+        M[t] = l;
+        M[(size_t)k * n + i] = l;
+    } else if (k == i) {
+        M[t] = Ld[i];
+    }
+}
+
+// Column c of A^{-1} (stored as row c; A^{-1} is symmetric): L y = e_c, then L^T x = y, in place.
+__global__ void k_chol_inverse(int n, const double* __restrict__ L, double* __restrict__ Ainv) {
+    const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= n) return;
+    double* x = Ainv + (size_t)c * n;
+    for (int r = lane; r < c; r += 32) x[r] = 0.0;
+    for (int r = c; r < n; ++r) {                      // forward: rows of L are contiguous
+        const double* lr = L + (size_t)r * n;
+        double acc = 0.0;
+        for (int k = c + lane; k < r; k += 32) acc += lr[k] * x[k];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) x[r] = ((r == c ? 1.0 : 0.0) - acc) / lr[r];
+        __syncwarp();
+    }
+    for (int r = n - 1; r >= 0; --r) {                 // backward: column r of L = row r of the upper part
+        const double* ur = L + (size_t)r * n;
+        double acc = 0.0;
+        for (int k = r + 1 + lane; k < n; k += 32) acc += ur[k] * x[k];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) x[r] = (x[r] - acc) / ur[r];
+        __syncwarp();
+    }
+}
+
+void dense_chol_inverse(int n, double* M, double* c0, double* Ainv, int* fail, cudaStream_t s) {
+    Tmp<double> c1(n, s), Ld(n, s);
+    double* col[2] = {c0, c1.get()};
     for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = M[(size_t)j * n + j];
-            if (!(d > 0.0) || !isfinite(d)) bad = 1;
-            else M[(size_t)j * n + j] = sqrt(d);
-        }
-        __syncthreads();
-        if (bad) break;
-        const double djj = M[(size_t)j * n + j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(size_t)i * n + j] /= djj;
-        __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            const double lij = M[(size_t)i * n + j];
-            for (int k = j + 1; k <= i; ++k) M[(size_t)i * n + k] -= lij * M[(size_t)k * n + j];
-        }
-        __syncthreads();
+        const int rows = std::max(n - j - 2, 1);
+        k_chol_step<<<(rows + 7) / 8, 256, 0, s>>>(n, j, M, col[j & 1], col[(j + 1) & 1], Ld.get(), fail);
     }
-    if (bad) { if (threadIdx.x == 0) *fail = 1; return; }
-    // columns of A^{-1} = L^{-T} L^{-1} e_c, one per thread (A^{-1} symmetric: stored as row c)
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        double* x = Ainv + (size_t)c * n;
-        for (int r = 0; r < c; ++r) x[r] = 0.0;
-        for (int r = c; r < n; ++r) {
-            double sacc = (r == c) ? 1.0 : 0.0;
-            for (int k = c; k < r; ++k) sacc -= M[(size_t)r * n + k] * x[k];
-            x[r] = sacc / M[(size_t)r * n + r];
-        }
-        for (int r = n - 1; r >= 0; --r) {
-            double sacc = x[r];
-            for (int k = r + 1; k < n; ++k) sacc -= M[(size_t)k * n + r] * x[k];
-            x[r] = sacc / M[(size_t)r * n + r];
-        }
-    }
+    k_chol_finish<<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, M, Ld.get());
+    k_chol_inverse<<<(n + 7) / 8, 256, 0, s>>>(n, M, Ainv);
+    CPC_LAUNCH_CK();
 }
 
 // ============================================================================================
@@ -1087,12 +1133,13 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         if (h.nc > DENSE_MAX) fail(CPC_ESETUP, "coarsest level too large for the dense solve");
         Tmp<double> M((size_t)h.nc * h.nc, s);
         CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s));
-        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
+        Tmp<double> c0(h.nc, s);
+        CPC_CK(cudaMemsetAsync(c0.get(), 0, sizeof(double) * h.nc, s));
+        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get(), c0.get());
         h.Ainv.alloc((size_t)h.nc * h.nc);
         Tmp<int> f(1, s);
         CPC_CK(cudaMemsetAsync(f.get(), 0, sizeof(int), s));
-        k_dense_chol_inverse<<<1, 1024, 0, s>>>(h.nc, M.get(), h.Ainv.p, f.get());
-        CPC_LAUNCH_CK();
+        dense_chol_inverse(h.nc, M.get(), c0.get(), h.Ainv.p, f.get(), s);
         if (d2h(f.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
     }
     for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1);

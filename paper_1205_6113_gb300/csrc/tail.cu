@@ -29,7 +29,7 @@ namespace {
 constexpr int TAIL_TPB = 512;
 constexpr int TAIL_MAXL = 16;
 constexpr int TAIL_MAXCTA = 16;
-constexpr size_t TAIL_SMEM = 200 * 1024;      // dynamic shared memory budget per CTA
+constexpr size_t TAIL_SMEM = 224 * 1024;      // dynamic shared memory budget per CTA (227 KB maximum)
 
 enum { A_CPTR, A_PERM, A_COL, A_DIAG, A_DINV, A_VAL, P_CPTR, P_PERM, P_COL, P_VAL, R_CPTR, R_PERM, R_COL, R_VAL, NSEC };
 
