@@ -27,6 +27,7 @@
  * Compile with -ffp-contract=off so that results do not depend on the host's FMA contraction.
  */
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -271,10 +272,12 @@ Csr permute_sym(const Csr& A, const vector<int>& order) {   // order[new] = old
 //  Galerkin   A_c = R (A P) with R = P^T (explicit transpose);
 //  stop       n_l <= coarse_max, max_levels reached, or no coarsening; coarsest solved exactly;
 //  colouring  if the pattern graph of A_l is bipartite: breadth-first parity from the smallest
-//             index of each component (red-black on a structured grid); otherwise
-//             Jones-Plassmann: each round, uncoloured points whose fmix32(i ^ COLOUR_SEED) beats
-//             all uncoloured neighbours take the smallest colour unused by their coloured
-//             neighbours.
+//             index of each component (red-black on a structured grid); otherwise greedy
+//             colouring in decreasing priority (peel round, fmix32(i ^ COLOUR_SEED)): each point
+//             takes the smallest colour unused by its neighbours of higher priority.  Peel
+//             rounds: while points remain, those with at most twice the smallest remaining
+//             degree (off-diagonal count, reduced by the entries to earlier rounds) take the
+//             round number (a smallest-last style ordering: fewer colours than random order).
 // ---------------------------------------------------------------------------------------------
 struct Level {
     Csr A, P, R;
@@ -407,8 +410,33 @@ bool colour_bipartite(const Csr& A, vector<int>& colour) {
     return true;
 }
 
+// Peel rounds (a smallest-last style ordering): deg_i = number of off-diagonal entries of row i;
+// while points remain, every remaining point with deg_i <= 2 min_{remaining} deg takes the current
+// round number, then each remaining point loses one degree per entry of its row in that round.
+vector<int> peel_rounds(const Csr& A) {
+    const int n = A.n;
+    vector<int> deg(n, 0), rnd(n, -1);
+    for (int i = 0; i < n; ++i)
+        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+            if (A.col[p] != i) ++deg[i];
+    int left = n;
+    for (int r = 0; left > 0; ++r) {
+        int dmin = INT_MAX;
+        for (int i = 0; i < n; ++i) if (rnd[i] < 0) dmin = std::min(dmin, deg[i]);
+        for (int i = 0; i < n; ++i)
+            if (rnd[i] < 0 && deg[i] <= 2 * dmin) { rnd[i] = r; --left; }
+        for (int i = 0; i < n; ++i) {
+            if (rnd[i] >= 0) continue;
+            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+                if (A.col[p] != i && rnd[A.col[p]] == r) --deg[i];
+        }
+    }
+    return rnd;
+}
+
 // Smoothing colours of a level: the breadth-first 2-colouring when the graph is bipartite (the
-// red-black colouring of a structured grid), otherwise Jones-Plassmann.
+// red-black colouring of a structured grid); otherwise greedy colouring (smallest colour unused by
+// the neighbours coloured before) in decreasing priority (peel round, fmix32(i ^ COLOUR_SEED)).
 void colour_jp(const Csr& A, vector<int>& colour, int& ncol, vector<int>& order) {
     const int n = A.n;
     if (colour_bipartite(A, colour)) {
@@ -419,34 +447,24 @@ void colour_jp(const Csr& A, vector<int>& colour, int& ncol, vector<int>& order)
             for (int i = 0; i < n; ++i) if (colour[i] == c) order.push_back(i);
         return;
     }
+    const vector<int> rnd = peel_rounds(A);
+    vector<int> seq(n);
+    for (int i = 0; i < n; ++i) seq[i] = i;
+    std::sort(seq.begin(), seq.end(), [&](int a, int b) {
+        if (rnd[a] != rnd[b]) return rnd[a] > rnd[b];
+        return fmix32((uint32_t)a ^ COLOUR_SEED) > fmix32((uint32_t)b ^ COLOUR_SEED);
+    });
     colour.assign(n, -1);
-    vector<int> sel;
     vector<char> used;
-    for (;;) {
-        sel.clear();
-        bool any = false;
-        for (int i = 0; i < n; ++i) {
-            if (colour[i] >= 0) continue;
-            any = true;
-            const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
-            bool best = true;
-            for (int p = A.ptr[i]; p < A.ptr[i + 1] && best; ++p) {
-                const int j = A.col[p];
-                if (j != i && colour[j] < 0 && fmix32((uint32_t)j ^ COLOUR_SEED) > hi) best = false;
-            }
-            if (best) sel.push_back(i);
+    for (int i : seq) {
+        used.assign(A.ptr[i + 1] - A.ptr[i] + 2, 0);
+        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+            const int c = colour[A.col[p]];
+            if (A.col[p] != i && c >= 0 && c < (int)used.size()) used[c] = 1;
         }
-        if (!any) break;
-        for (int i : sel) {
-            used.assign(A.ptr[i + 1] - A.ptr[i] + 2, 0);
-            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-                const int c = colour[A.col[p]];
-                if (A.col[p] != i && c >= 0 && c < (int)used.size()) used[c] = 1;
-            }
-            int c = 0;
-            while (used[c]) ++c;
-            colour[i] = c;
-        }
+        int c = 0;
+        while (used[c]) ++c;
+        colour[i] = c;
     }
     ncol = 0;
     for (int i = 0; i < n; ++i) ncol = std::max(ncol, colour[i] + 1);

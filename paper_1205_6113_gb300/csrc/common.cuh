@@ -99,6 +99,7 @@ struct Sell {
     int C = 32;                        // chunk height (rows per warp); 32 / C lanes share a row
     int nslots = 0, nchunks = 0;
     int64_t nelem = 0;
+    int lanes = 0;                     // most entries one lane holds: ceil(widest chunk / 32)
     DBuf<int> perm, cptr, col;
     DBuf<double> val, diag, dinv;      // FP64 copy (always); dinv = 1 / diag (split diagonal only)
     DBuf<float> val32, diag32, dinv32; // FP32 copy (mixed precision)

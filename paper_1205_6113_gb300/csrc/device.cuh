@@ -43,15 +43,21 @@ inline SV<MT, DT> view(const Sell& S, const MT* val, const DT* diag) {
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// sum_w val[o_w] * x[col[o_w]] over one SELL row (entries o = o0, o0+32, ... < e).  Eight column
-// indices and values are loaded first, then the eight gathers, so that each thread keeps eight
-// independent loads in flight instead of a chain of dependent ones.  Padding (col < 0) is skipped
-// without a load.  Products are added in entry order.  With WAIT, the first batch of the matrix
-// row is loaded before pdl_wait() and the vector only after it.
-template <class VT, bool WAIT = false, class MT, class XT>
+// sum_w val[o_w] * x[col[o_w]] over one SELL row (entries o = o0, o0+32, ... < e).  U column
+// indices and values are loaded first, then the U gathers, so that each thread keeps U independent
+// loads in flight instead of a chain of dependent ones.  Padding (col < 0) is skipped without a
+// load.  Products are added in entry order.  The caller picks U >= the most entries a lane holds
+// (4, 6 or 8; Sell::lanes), so one batch covers a row and no product is spent on padding beyond
+// the chunk width -- FP64 issue rate is scarce on this part.  With WAIT, the first batch of the
+// matrix row is loaded before pdl_wait() and the vector only after it; after_wait() runs right
+// after the wait, so that loads the caller issues there overlap the gathers.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <class VT, bool WAIT = false, int U = 8, class MT, class XT, class H = NoHook>
 __device__ __forceinline__ VT sell_dot(const int* __restrict__ col, const MT* __restrict__ val, int o, int e,
-                                       const XT* x) {
-    constexpr int U = 8;
+                                       const XT* x, H&& after_wait = H{}) {
     VT acc = VT(0);
     if (WAIT) {
         int c[U];
@@ -63,6 +69,7 @@ __device__ __forceinline__ VT sell_dot(const int* __restrict__ col, const MT* __
             v[u] = oo < e ? Cv<VT>::f(val[oo]) : VT(0);
         }
         pdl_wait();
+        after_wait();           // the caller's own loads of predecessor data, in flight with the gathers
 #pragma unroll
         for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? Cv<VT>::f(x[c[u]]) : VT(0);
 #pragma unroll
@@ -80,33 +87,6 @@ __device__ __forceinline__ VT sell_dot(const int* __restrict__ col, const MT* __
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? Cv<VT>::f(x[c[u]]) : VT(0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc += v[u] * xv[u];
-    }
-    return acc;
-}
-
-// As sell_dot, with the gathered vector read through L2 only (ld.global.cg): for vectors written
-// earlier in the same kernel by other thread blocks of the cluster.
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
-
-template <class VT, class MT, class XT>
-__device__ __forceinline__ VT sell_dot_cg(const int* __restrict__ col, const MT* __restrict__ val, int o, int e,
-                                          const XT* x) {
-    constexpr int U = 8;
-    VT acc = VT(0);
-    for (; o < e; o += U * 32) {
-        int c[U];
-        VT v[U], xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int oo = o + u * 32;
-            c[u] = oo < e ? col[oo] : -1;
-            v[u] = oo < e ? Cv<VT>::f(val[oo]) : VT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? Cv<VT>::f(ldcg(x + c[u])) : VT(0);
 #pragma unroll
         for (int u = 0; u < U; ++u) acc += v[u] * xv[u];
     }

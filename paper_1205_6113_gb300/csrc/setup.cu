@@ -7,8 +7,9 @@
 //   AMG     strength theta, PMIS splitting with weight (|S^T_i|, fmix32(i)), direct
 //           interpolation, R = P^T, Galerkin A_c = R (A P) (Section 3.2);
 //   colour  breadth-first parity 2-colouring when the level graph is bipartite (red-black on a
-//           structured grid), else Jones-Plassmann with weight fmix32(i ^ 0x5bd1e995) and the
-//           smallest free colour.
+//           structured grid), else Jones-Plassmann with priority (peel round, fmix32(i ^
+//           0x5bd1e995)) and the smallest free colour; peel rounds are a smallest-last style
+//           ordering that needs fewer colours than a random one.
 // Sums that define matrix entries are accumulated in a fixed order (the order the products are
 // generated in), so results do not depend on thread scheduling.
 #include <cub/cub.cuh>
@@ -16,6 +17,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <memory>
 
 #include "handle.cuh"
 
@@ -413,34 +415,75 @@ __global__ void k_interp_fill(int n, const int* ptr, const int* col, const doubl
 }
 
 // ============================================================================================
-// Jones-Plassmann colouring
+// Colouring priority: peel rounds (a smallest-last style ordering).  deg_i = off-diagonal count of
+// row i; in round r every remaining point with deg_i <= 2 min_{remaining} deg takes round r, then
+// each remaining point loses one degree per entry of its row taken in round r.  Two dmin slots
+// alternate: round r reads slot r % 2 and the update fills slot (r + 1) % 2.
 // ============================================================================================
-__global__ void k_jp_select(int n, const int* ptr, const int* col, const int* colour, uint8_t* sel) {
+__global__ void k_peel_init(int n, const int* ptr, const int* col, int* deg, int* rnd, int* dmin) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint8_t best = 0;
-    if (colour[i] < 0) {
-        best = 1;
-        const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
-        for (int p = ptr[i]; p < ptr[i + 1] && best; ++p) {
-            const int j = col[p];
-            if (j != i && colour[j] < 0 && fmix32((uint32_t)j ^ COLOUR_SEED) > hi) best = 0;
-        }
-    }
-    sel[i] = best;
+    int d = 0;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) d += col[p] != i;
+    deg[i] = d;
+    rnd[i] = -1;
+    atomicMin(dmin, d);
 }
 
-__global__ void k_jp_assign(int n, const int* ptr, const int* col, const uint8_t* sel, int* colour, int* done) {
+__global__ void k_peel_mark(int n, const int* deg, int* rnd, int* dmin, int r, int* left) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !sel[i]) return;
+    const int dm = dmin[r & 1];
+    if (i == 0) dmin[(r + 1) & 1] = INT_MAX;
+    if (i >= n || dm == INT_MAX) return;
+    if (rnd[i] < 0 && deg[i] <= 2 * dm) {
+        rnd[i] = r;
+        atomicSub(left, 1);
+    }
+}
+
+__global__ void k_peel_update(int n, const int* ptr, const int* col, int* deg, const int* rnd, int r, int* dmin) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || rnd[i] >= 0) return;
+    int c = 0;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) c += col[p] != i && rnd[col[p]] == r;
+    const int d = deg[i] - c;
+    deg[i] = d;
+    atomicMin(&dmin[(r + 1) & 1], d);
+}
+
+// ============================================================================================
+// Jones-Plassmann colouring with priority (peel round, fmix32(i ^ COLOUR_SEED)): a point whose
+// neighbours of higher priority are all coloured takes the smallest colour they leave free.  Its
+// neighbours of lower priority cannot be coloured before it, so the result is the greedy colouring
+// in decreasing priority.  Colours written during a round by other threads may or may not be seen
+// (volatile reads): seeing one only lets a point finish in an earlier round, with the same colour.
+// ============================================================================================
+__device__ __forceinline__ bool jp_beats(int rj, int j, int ri, uint32_t hi) {
+    return rj > ri || (rj == ri && fmix32((uint32_t)j ^ COLOUR_SEED) > hi);
+}
+
+__global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd, int* colour, int* done) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    volatile int* vc = colour;
+    if (vc[i] >= 0) return;
+    const int ri = rnd[i];
+    const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
+    const int p0 = ptr[i], p1 = ptr[i + 1];
+    for (int p = p0; p < p1; ++p) {
+        const int j = col[p];
+        if (j != i && jp_beats(rnd[j], j, ri, hi) && vc[j] < 0) return;
+    }
     for (int base = 0;; base += 64) {
         unsigned long long used = 0ull;
-        for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
-            const int c = colour[col[p]];
-            if (col[p] != i && c >= base && c < base + 64) used |= 1ull << (c - base);
+        for (int p = p0; p < p1; ++p) {
+            const int j = col[p];
+            if (j == i || !jp_beats(rnd[j], j, ri, hi)) continue;
+            const int c = vc[j];
+            if (c >= base && c < base + 64) used |= 1ull << (c - base);
         }
         if (used != ~0ull) {
-            colour[i] = base + __ffsll((long long)~used) - 1;
+            vc[i] = base + __ffsll((long long)~used) - 1;
             break;
         }
     }
@@ -579,6 +622,11 @@ __global__ void k_sell_width(const int* perm, int nchunks, int C, const int* ptr
     width[k] = w * C;
 }
 
+__global__ void k_max_int(const int* a, int n, int* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, a[i]);
+}
+
 // Slots refer to rows of the CSR; imap (optional) renames rows and columns on output
 // (IC factor stored in its own ordering but applied to naturally ordered vectors).
 __global__ void k_sell_fill(const int* perm, int nslots, int C, const int* ptr, const int* col, const double* val,
@@ -696,6 +744,12 @@ void build_sell(const int* ptr, const int* col, const double* val, const DBuf<in
     S.seg = seg;
     Tmp<int> width(S.nchunks + 1, s);
     k_sell_width<<<nblk(S.nchunks + 1), TPB, 0, s>>>(slots.p, S.nchunks, C, ptr, col, mode, width.get());
+    {
+        Tmp<int> wmax(1, s);
+        CPC_CK(cudaMemsetAsync(wmax.get(), 0, sizeof(int), s));
+        k_max_int<<<nblk(S.nchunks + 1), TPB, 0, s>>>(width.get(), S.nchunks + 1, wmax.get());
+        S.lanes = (d2h(wmax.get(), s) + 31) / 32;
+    }
     S.cptr.alloc(S.nchunks + 1);
     exclusive_scan(width.get(), S.cptr.p, S.nchunks + 1, s);
     S.nelem = d2h(S.cptr.p + S.nchunks, s);
@@ -950,31 +1004,189 @@ void setup_level_sells(Level& L, cudaStream_t s, bool last) {
     }
 }
 
-// Two-colouring by propagated breadth-first parity; returns false if the graph is not bipartite.
-bool colour_bipartite(const Csr& A, int* colour, cudaStream_t s) {
-    const int n = A.n;
-    Tmp<int> r0(n, s), r1(n, s), p0(n, s), p1(n, s), changed(1, s);
-    k_iota<<<nblk(n), TPB, 0, s>>>(r0.get(), n);
-    CPC_CK(cudaMemsetAsync(p0.get(), 0, sizeof(int) * n, s));
-    int* ra = r0.get(); int* rb = r1.get(); int* pa = p0.get(); int* pb = p1.get();
-    for (int round = 0;; round += 16) {
-        CPC_CK(cudaMemsetAsync(changed.get(), 0, sizeof(int), s));
-        for (int k = 0; k < 16; ++k) {
-            k_bip_round<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, A.col.p, ra, pa, rb, pb, changed.get());
-            std::swap(ra, rb);
-            std::swap(pa, pb);
+// Triangle probe: point i with adjacent neighbours j, k (among its first 8 entries) proves the
+// graph is not bipartite.  Finding none proves nothing; the parity propagation then decides.
+__global__ void k_tri_probe(int n, const int* ptr, const int* col, int* found) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p0 = ptr[i], p1 = min(ptr[i + 1], ptr[i] + 8);
+    for (int a = p0; a < p1; ++a) {
+        const int j = col[a];
+        if (j == i) continue;
+        for (int b = a + 1; b < p1; ++b) {
+            const int k = col[b];
+            if (k == i) continue;
+            int lo = ptr[j], hi = ptr[j + 1] - 1;        // columns ascending: binary search for k
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int c = col[mid];
+                if (c == k) { atomicOr(found, 1); return; }
+                if (c < k) lo = mid + 1; else hi = mid - 1;
+            }
         }
-        CPC_LAUNCH_CK();
-        if (d2h(changed.get(), s) == 0) break;
-        if (round > n + 16) fail(CPC_ESETUP, "parity propagation did not converge");
     }
-    Tmp<int> bad(1, s);
-    CPC_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
-    k_bip_check<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, A.col.p, pa, bad.get());
-    if (d2h(bad.get(), s)) return false;
-    CPC_CK(cudaMemcpyAsync(colour, pa, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+}
+
+// Smoothing colours of levels [0, nl - 1): the breadth-first parity 2-colouring if the pattern
+// graph is bipartite, else Jones-Plassmann with peel-round priority.  Every level is a small state
+// machine of round loops on its own stream; all levels advance one batch of launches at a time and
+// then read their counters, so the setup waits for the longest chain of rounds, not their sum.
+struct ColourJob {
+    enum Phase { TRI, BIP, BIP_CHECK, PEEL, JP, MAX, DONE };
+    int l = 0, n = 0, phase = TRI, rounds = 0;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    int* pin = nullptr;                                         // pinned counter read back per batch
+    std::unique_ptr<Tmp<int>> a0, a1, a2, a3, cnt;              // phase buffers
+    std::unique_ptr<Tmp<int>> rnd, dmin;
+};
+
+void colour_levels(Handle& h, cudaStream_t s) {
+    const int nl = (int)h.lev.size();
+    if (nl < 2) return;
     CPC_CK(cudaStreamSynchronize(s));
-    return true;
+    const int nj = nl - 1;
+    struct Res {
+        std::vector<cudaStream_t> st;
+        std::vector<cudaEvent_t> ev;
+        int* pin = nullptr;
+        ~Res() {
+            for (auto e : ev) cudaEventDestroy(e);
+            for (auto q : st) { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
+            if (pin) cudaFreeHost(pin);
+        }
+    } res;                                                      // outlives the jobs' buffers
+    CPC_CK(cudaMallocHost(&res.pin, sizeof(int) * nj));
+    std::vector<ColourJob> jobs(nj);
+    for (int l = 0; l < nj; ++l) {
+        cudaStream_t q;
+        cudaEvent_t e;
+        CPC_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+        res.st.push_back(q);
+        CPC_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        res.ev.push_back(e);
+        ColourJob& J = jobs[l];
+        J.l = l;
+        J.n = h.lev[l].n;
+        J.st = q;
+        J.ev = e;
+        J.pin = res.pin + l;
+        h.lev[l].colour.alloc(J.n);
+    }
+    auto mk = [](int count, cudaStream_t q) { return std::make_unique<Tmp<int>>((size_t)count, q); };
+    auto readback = [](ColourJob& J) {
+        CPC_CK(cudaMemcpyAsync(J.pin, J.cnt->get(), sizeof(int), cudaMemcpyDeviceToHost, J.st));
+        CPC_CK(cudaEventRecord(J.ev, J.st));
+    };
+    auto enter = [&](ColourJob& J, int phase) {                 // allocate and initialise a phase
+        const Level& L = h.lev[J.l];
+        const int n = J.n;
+        cudaStream_t q = J.st;
+        J.phase = phase;
+        J.rounds = 0;
+        if (phase == ColourJob::BIP) {
+            J.a0 = mk(n, q); J.a1 = mk(n, q); J.a2 = mk(n, q); J.a3 = mk(n, q);
+            k_iota<<<nblk(n), TPB, 0, q>>>(J.a0->get(), n);
+            CPC_CK(cudaMemsetAsync(J.a2->get(), 0, sizeof(int) * n, q));
+        } else if (phase == ColourJob::PEEL) {
+            J.a0 = mk(n, q);                                     // degrees
+            J.rnd = mk(n, q);
+            J.dmin = mk(2, q);
+            k_fill_int<<<1, 32, 0, q>>>(J.dmin->get(), 2, INT_MAX);
+            k_fill_int<<<1, 32, 0, q>>>(J.cnt->get(), 1, n);     // points left
+            k_peel_init<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(), J.dmin->get());
+        } else if (phase == ColourJob::JP) {
+            k_fill_int<<<nblk(n), TPB, 0, q>>>(L.colour.p, n, -1);
+            CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));   // points coloured
+        }
+    };
+    for (auto& J : jobs) J.cnt = mk(1, J.st);
+    for (int active = nj; active > 0;) {
+        for (auto& J : jobs) {                                  // one batch per unfinished level
+            if (J.phase == ColourJob::DONE) continue;
+            const Level& L = h.lev[J.l];
+            const int n = J.n;
+            cudaStream_t q = J.st;
+            switch (J.phase) {
+                case ColourJob::TRI:
+                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
+                    k_tri_probe<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.cnt->get());
+                    break;
+                case ColourJob::BIP:
+                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
+                    for (int k = 0; k < 16; ++k) {
+                        k_bip_round<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.a2->get(),
+                                                            J.a1->get(), J.a3->get(), J.cnt->get());
+                        std::swap(J.a0, J.a1);
+                        std::swap(J.a2, J.a3);
+                    }
+                    J.rounds += 16;
+                    break;
+                case ColourJob::BIP_CHECK:
+                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
+                    k_bip_check<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a2->get(), J.cnt->get());
+                    break;
+                case ColourJob::PEEL:
+                    for (int k = 0; k < 8; ++k, ++J.rounds) {
+                        k_peel_mark<<<nblk(n), TPB, 0, q>>>(n, J.a0->get(), J.rnd->get(), J.dmin->get(), J.rounds,
+                                                            J.cnt->get());
+                        k_peel_update<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(),
+                                                              J.rounds, J.dmin->get());
+                    }
+                    break;
+                case ColourJob::JP:
+                    for (int k = 0; k < 8; ++k)
+                        k_jp_round<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.rnd->get(), L.colour.p,
+                                                           J.cnt->get());
+                    J.rounds += 8;
+                    break;
+                case ColourJob::MAX:
+                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
+                    k_max_int<<<nblk(n), TPB, 0, q>>>(L.colour.p, n, J.cnt->get());
+                    break;
+            }
+            CPC_LAUNCH_CK();
+            readback(J);
+        }
+        for (auto& J : jobs) {                                  // read the counters, advance phases
+            if (J.phase == ColourJob::DONE) continue;
+            CPC_CK(cudaEventSynchronize(J.ev));
+            const int v = *J.pin;
+            Level& L = h.lev[J.l];
+            switch (J.phase) {
+                case ColourJob::TRI:
+                    enter(J, v ? ColourJob::PEEL : ColourJob::BIP);
+                    break;
+                case ColourJob::BIP:
+                    if (v == 0) enter(J, ColourJob::BIP_CHECK);
+                    else if (J.rounds > J.n + 16) fail(CPC_ESETUP, "parity propagation did not converge");
+                    break;
+                case ColourJob::BIP_CHECK:
+                    if (v == 0) {
+                        CPC_CK(cudaMemcpyAsync(L.colour.p, J.a2->get(), sizeof(int) * J.n, cudaMemcpyDeviceToDevice,
+                                               J.st));
+                        enter(J, ColourJob::MAX);
+                    } else {
+                        enter(J, ColourJob::PEEL);
+                    }
+                    break;
+                case ColourJob::PEEL:
+                    if (v == 0) enter(J, ColourJob::JP);
+                    else if (J.rounds > J.n + 8) fail(CPC_ESETUP, "peel rounds did not terminate");
+                    break;
+                case ColourJob::JP:
+                    if (v == J.n) enter(J, ColourJob::MAX);
+                    else if (J.rounds > J.n + 8) fail(CPC_ESETUP, "colouring did not terminate");
+                    break;
+                case ColourJob::MAX:
+                    L.ncolours = v + 1;
+                    J.phase = ColourJob::DONE;
+                    --active;
+                    break;
+            }
+        }
+    }
+    for (auto& J : jobs) CPC_CK(cudaStreamSynchronize(J.st));
 }
 
 // One coarsening step on level l; returns false when l becomes the coarsest level.
@@ -1027,28 +1239,6 @@ bool coarsen(Handle& h, int l, cudaStream_t s) {
                                           P.ptr.p, P.col.p, P.val.p);
     CPC_LAUNCH_CK();
     transpose(P, L.R, s);
-    // colouring of A_l: breadth-first parity if the graph is bipartite, else Jones-Plassmann
-    L.colour.alloc(n);
-    if (!colour_bipartite(L.A, L.colour.p, s)) {
-        k_fill_int<<<nblk(n), TPB, 0, s>>>(L.colour.p, n, -1);
-        Tmp<int> done(1, s);
-        CPC_CK(cudaMemsetAsync(done.get(), 0, sizeof(int), s));
-        for (int round = 0;; ++round) {
-            k_jp_select<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, L.colour.p, sel.get());
-            k_jp_assign<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, sel.get(), L.colour.p, done.get());
-            CPC_LAUNCH_CK();
-            if (d2h(done.get(), s) == n) break;
-            if (round > n) fail(CPC_ESETUP, "colouring did not terminate");
-        }
-    }
-    {
-        size_t tmp = 0;
-        Tmp<int> mx(1, s);
-        CPC_CK(cub::DeviceReduce::Max(nullptr, tmp, L.colour.p, mx.get(), n, s));
-        Tmp<char> t(tmp, s);
-        CPC_CK(cub::DeviceReduce::Max(t.get(), tmp, L.colour.p, mx.get(), n, s));
-        L.ncolours = d2h(mx.get(), s) + 1;
-    }
     // Galerkin coarse operator A_c = R (A P)
     Csr AP;
     spgemm(L.A, P, AP, s);
@@ -1126,6 +1316,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         const bool stop = h.lev[l].n <= h.opt.coarse_max || (int)h.lev.size() >= h.opt.max_levels;
         if (stop || !coarsen(h, l, s)) break;
     }
+    colour_levels(h, s);
     const int nl = (int)h.lev.size();
     {
         Level& Lc = h.lev[nl - 1];

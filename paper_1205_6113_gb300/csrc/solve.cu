@@ -38,6 +38,15 @@ void launch(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args&&... 
     CPC_CK(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
 }
 
+// Calls f(std::integral_constant<int, U>{}) with the sell_dot batch width for an operator whose
+// lanes hold at most `lanes` entries.
+template <class F>
+void with_u(int lanes, F&& f) {
+    if (lanes <= 4) f(std::integral_constant<int, 4>{});
+    else if (lanes <= 6) f(std::integral_constant<int, 6>{});
+    else f(std::integral_constant<int, 8>{});
+}
+
 inline int blocks_for_chunks(int nchunks) { return std::max(1, (nchunks + WPB - 1) / WPB); }
 inline int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + VEC_TPB - 1) / VEC_TPB, NPART)); }
 
@@ -55,7 +64,7 @@ __device__ __forceinline__ VT sub_sum(VT v, int C) {
 // Gauss-Seidel over the rows of one colour (chunks [c0, c1)): x_i = (f_i - sum_{j!=i} a_ij x_j) / a_ii,
 // with the view's diagonal field holding 1 / a_ii (a multiply instead of an FP64 division).
 // Rows of one colour are not coupled, so they update in parallel exactly as in sequential order.
-template <class MT, class DT, class FT, class VT>
+template <class MT, class DT, class FT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_gs(SV<MT, DT> A, int c0, int c1, const FT* __restrict__ f, VT* x) {
     const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
     if (k >= c1) return;
@@ -63,13 +72,17 @@ __global__ void __launch_bounds__(SELL_TPB) k_gs(SV<MT, DT> A, int c0, int c1, c
     const int lane = threadIdx.x & 31, C = A.C, r = lane & (C - 1), g = lane / C;
     const int s = k * C + r;
     const int row = A.perm[s];
-    VT dot = sell_dot<VT, true>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], x);
+    const bool own = g == 0 && row >= 0;
+    const VT dinv = own ? Cv<VT>::f(A.diag[s]) : VT(0);
+    VT fr = VT(0);
+    VT dot = sell_dot<VT, true, U>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], x,
+                                   [&] { if (own) fr = Cv<VT>::f(f[row]); });
     dot = sub_sum(dot, C);
-    if (g == 0 && row >= 0) x[row] = (Cv<VT>::f(f[row]) - dot) * Cv<VT>::f(A.diag[s]);
+    if (own) x[row] = (fr - dot) * dinv;
 }
 
 // r = f - A x over all chunks (grid-stride over chunks).
-template <class MT, class DT, class FT, class XT, class RT>
+template <class MT, class DT, class FT, class XT, class RT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_resid(SV<MT, DT> A, int nchunks, const FT* __restrict__ f,
                                                      const XT* __restrict__ x, RT* __restrict__ r) {
     pdl_launch_dependents();
@@ -78,14 +91,20 @@ __global__ void __launch_bounds__(SELL_TPB) k_resid(SV<MT, DT> A, int nchunks, c
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
         const int s = k * C + rr;
         const int row = A.perm[s];
-        RT dot = sell_dot<RT>(A.col, A.val, A.cptr[k] + g * C + rr, A.cptr[k + 1], x);
+        const bool own = g == 0 && row >= 0;
+        RT fr = RT(0), dx = RT(0);
+        if (own) {
+            fr = Cv<RT>::f(f[row]);
+            dx = Cv<RT>::f(A.diag[s]) * Cv<RT>::f(x[row]);
+        }
+        RT dot = sell_dot<RT, false, U>(A.col, A.val, A.cptr[k] + g * C + rr, A.cptr[k + 1], x);
         dot = sub_sum(dot, C);
-        if (g == 0 && row >= 0) r[row] = Cv<RT>::f(f[row]) - (Cv<RT>::f(A.diag[s]) * Cv<RT>::f(x[row]) + dot);
+        if (own) r[row] = fr - (dx + dot);
     }
 }
 
 // y = A x (diagonal split) over all chunks.
-template <class MT, class DT, class XT, class YT>
+template <class MT, class DT, class XT, class YT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_spmv(SV<MT, DT> A, int nchunks, const XT* __restrict__ x,
                                                     YT* __restrict__ y) {
     pdl_launch_dependents();
@@ -94,14 +113,16 @@ __global__ void __launch_bounds__(SELL_TPB) k_spmv(SV<MT, DT> A, int nchunks, co
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
         const int s = k * C + r;
         const int row = A.perm[s];
-        YT dot = sell_dot<YT>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], x);
+        const bool own = g == 0 && row >= 0;
+        const YT dx = own ? Cv<YT>::f(A.diag[s]) * Cv<YT>::f(x[row]) : YT(0);
+        YT dot = sell_dot<YT, false, U>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], x);
         dot = sub_sum(dot, C);
-        if (g == 0 && row >= 0) y[row] = Cv<YT>::f(A.diag[s]) * Cv<YT>::f(x[row]) + dot;
+        if (own) y[row] = dx + dot;
     }
 }
 
 // y = M x (full rows, no split diagonal): restriction f_c = R r.
-template <class MT, class VT>
+template <class MT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_apply_full(SV<MT, MT> M, int nchunks, const VT* __restrict__ x,
                                                           VT* __restrict__ y) {
     pdl_launch_dependents();
@@ -109,14 +130,14 @@ __global__ void __launch_bounds__(SELL_TPB) k_apply_full(SV<MT, MT> M, int nchun
     const int lane = threadIdx.x & 31, C = M.C, r = lane & (C - 1), g = lane / C;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
         const int row = M.perm[k * C + r];
-        VT dot = sell_dot<VT>(M.col, M.val, M.cptr[k] + g * C + r, M.cptr[k + 1], x);
+        VT dot = sell_dot<VT, false, U>(M.col, M.val, M.cptr[k] + g * C + r, M.cptr[k + 1], x);
         dot = sub_sum(dot, C);
         if (g == 0 && row >= 0) y[row] = dot;
     }
 }
 
 // f_c = R r and x_c = 0 (the next level starts from a zero guess).
-template <class MT, class VT>
+template <class MT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_restrict_zero(SV<MT, MT> M, int nchunks, const VT* __restrict__ x,
                                                              VT* __restrict__ y, VT* __restrict__ yz) {
     pdl_launch_dependents();
@@ -124,14 +145,14 @@ __global__ void __launch_bounds__(SELL_TPB) k_restrict_zero(SV<MT, MT> M, int nc
     const int lane = threadIdx.x & 31, C = M.C, r = lane & (C - 1), g = lane / C;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
         const int row = M.perm[k * C + r];
-        VT dot = sell_dot<VT>(M.col, M.val, M.cptr[k] + g * C + r, M.cptr[k + 1], x);
+        VT dot = sell_dot<VT, false, U>(M.col, M.val, M.cptr[k] + g * C + r, M.cptr[k + 1], x);
         dot = sub_sum(dot, C);
         if (g == 0 && row >= 0) { y[row] = dot; yz[row] = VT(0); }
     }
 }
 
 // x += P e (prolongation and correction).
-template <class MT, class VT>
+template <class MT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_prolong(SV<MT, MT> P, int nchunks, const VT* __restrict__ e,
                                                        VT* __restrict__ x) {
     pdl_launch_dependents();
@@ -139,9 +160,11 @@ __global__ void __launch_bounds__(SELL_TPB) k_prolong(SV<MT, MT> P, int nchunks,
     const int lane = threadIdx.x & 31, C = P.C, r = lane & (C - 1), g = lane / C;
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
         const int row = P.perm[k * C + r];
-        VT dot = sell_dot<VT>(P.col, P.val, P.cptr[k] + g * C + r, P.cptr[k + 1], e);
+        const bool own = g == 0 && row >= 0;
+        const VT xr = own ? x[row] : VT(0);
+        VT dot = sell_dot<VT, false, U>(P.col, P.val, P.cptr[k] + g * C + r, P.cptr[k + 1], e);
         dot = sub_sum(dot, C);
-        if (g == 0 && row >= 0) x[row] += dot;
+        if (own) x[row] = xr + dot;
     }
 }
 
@@ -176,35 +199,46 @@ __global__ void k_copy(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
 }
 
 // Forward solve with the unit lower factor, rows of one level: y_i = t_i - sum_{j<i} l_ij y_j.
-template <class MT, class TT, class VT>
+template <class MT, class TT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_lsolve(SV<MT, MT> L, int c0, int c1, const TT* __restrict__ t, VT* y) {
     const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
     if (k >= c1) return;
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, C = L.C, r = lane & (C - 1), g = lane / C;
     const int row = L.perm[k * C + r];
-    VT dot = sell_dot<VT, true>(L.col, L.val, L.cptr[k] + g * C + r, L.cptr[k + 1], y);
+    const bool own = g == 0 && row >= 0;
+    VT tr = VT(0);
+    VT dot = sell_dot<VT, true, U>(L.col, L.val, L.cptr[k] + g * C + r, L.cptr[k + 1], y,
+                                   [&] { if (own) tr = Cv<VT>::f(t[row]); });
     dot = sub_sum(dot, C);
-    if (g == 0 && row >= 0) y[row] = Cv<VT>::f(t[row]) - dot;
+    if (own) y[row] = tr - dot;
 }
 
 // Backward solve with U, rows of one level: w_i = (y_i - sum_{j>i} u_ij w_j) / u_ii (the view's
 // diagonal field holds 1 / u_ii); optionally z_i += w_i in the same pass.
-template <class MT, class VT>
-__global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> U, int c0, int c1, const VT* __restrict__ y, VT* w,
+template <class MT, class VT, int U>
+__global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> Uf, int c0, int c1, const VT* __restrict__ y, VT* w,
                                                       VT* zadd) {
     const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
     if (k >= c1) return;
     pdl_launch_dependents();
-    const int lane = threadIdx.x & 31, C = U.C, r = lane & (C - 1), g = lane / C;
+    const int lane = threadIdx.x & 31, C = Uf.C, r = lane & (C - 1), g = lane / C;
     const int s = k * C + r;
-    const int row = U.perm[s];
-    VT dot = sell_dot<VT, true>(U.col, U.val, U.cptr[k] + g * C + r, U.cptr[k + 1], w);
+    const int row = Uf.perm[s];
+    const bool own = g == 0 && row >= 0;
+    const VT dinv = own ? Cv<VT>::f(Uf.diag[s]) : VT(0);
+    VT yr = VT(0), zr = VT(0);
+    VT dot = sell_dot<VT, true, U>(Uf.col, Uf.val, Uf.cptr[k] + g * C + r, Uf.cptr[k + 1], w, [&] {
+        if (own) {
+            yr = y[row];
+            if (zadd) zr = zadd[row];
+        }
+    });
     dot = sub_sum(dot, C);
-    if (g == 0 && row >= 0) {
-        const VT v = (y[row] - dot) * Cv<VT>::f(U.diag[s]);
+    if (own) {
+        const VT v = (yr - dot) * dinv;
         w[row] = v;
-        if (zadd) zadd[row] += v;
+        if (zadd) zadd[row] = zr + v;
     }
 }
 
@@ -319,6 +353,7 @@ __global__ void k_pcg_p(int n, const ZT* __restrict__ z, double* __restrict__ p,
 }
 
 // q = A p and p.q; the last block forms alpha = (r.z) / (p.q).
+template <int U>
 __global__ void __launch_bounds__(SELL_TPB) k_pcg_spmv(SV<double, double> A, int nchunks, const double* __restrict__ p,
                                                         double* __restrict__ q, double* part, unsigned* ctr,
                                                         PcgState* st) {
@@ -329,11 +364,13 @@ __global__ void __launch_bounds__(SELL_TPB) k_pcg_spmv(SV<double, double> A, int
     for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
         const int s = k * C + r;
         const int row = A.perm[s];
-        double dot = sell_dot<double>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], p);
+        const bool own = g == 0 && row >= 0;
+        const double pr = own ? p[row] : 0.0;
+        const double dp = own ? A.diag[s] * pr : 0.0;
+        double dot = sell_dot<double, false, U>(A.col, A.val, A.cptr[k] + g * C + r, A.cptr[k + 1], p);
         dot = sub_sum(dot, C);
-        if (g == 0 && row >= 0) {
-            const double pr = p[row];
-            const double acc = A.diag[s] * pr + dot;
+        if (own) {
+            const double acc = dp + dot;
             q[row] = acc;
             v += pr * acc;
         }
@@ -402,29 +439,35 @@ void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
     const int c0 = L.S.seg[c], c1 = L.S.seg[c + 1];
     if (c1 <= c0) return;
     const int g = blocks_for_chunks(c1 - c0);
-    if constexpr (std::is_same<VT, double>::value) {
-        launch(k_gs<double, double, FT, VT>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), c0, c1, f, x);
-    } else {
-        if (L.vt == VT_BF16)
-            launch(k_gs<__nv_bfloat16, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
-        else
-            launch(k_gs<float, float, FT, VT>, g, SELL_TPB, s, view(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
-    }
+    with_u(L.S.lanes, [&](auto u) {
+        constexpr int U = decltype(u)::value;
+        if constexpr (std::is_same<VT, double>::value) {
+            launch(k_gs<double, double, FT, VT, U>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), c0, c1, f, x);
+        } else {
+            if (L.vt == VT_BF16)
+                launch(k_gs<__nv_bfloat16, float, FT, VT, U>, g, SELL_TPB, s, view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
+            else
+                launch(k_gs<float, float, FT, VT, U>, g, SELL_TPB, s, view(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
+        }
+    });
 }
 
 template <class FT, class VT>
 void rec_resid_level(Level& L, const FT* f, const VT* x, VT* r, cudaStream_t s) {
     const int g = blocks_for_chunks(L.S.nchunks);
-    if constexpr (std::is_same<VT, double>::value) {
-        launch(k_resid<double, double, FT, VT, VT>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nchunks, f, (const VT*)x, r);
-    } else {
-        if (L.vt == VT_BF16)
-            launch(k_resid<__nv_bfloat16, float, FT, VT, VT>, g, SELL_TPB, s,
-                   view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), L.S.nchunks, f, (const VT*)x, r);
-        else
-            launch(k_resid<float, float, FT, VT, VT>, g, SELL_TPB, s,
-                   view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), L.S.nchunks, f, (const VT*)x, r);
-    }
+    with_u(L.S.lanes, [&](auto u) {
+        constexpr int U = decltype(u)::value;
+        if constexpr (std::is_same<VT, double>::value) {
+            launch(k_resid<double, double, FT, VT, VT, U>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nchunks, f, (const VT*)x, r);
+        } else {
+            if (L.vt == VT_BF16)
+                launch(k_resid<__nv_bfloat16, float, FT, VT, VT, U>, g, SELL_TPB, s,
+                       view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.diag32.p), L.S.nchunks, f, (const VT*)x, r);
+            else
+                launch(k_resid<float, float, FT, VT, VT, U>, g, SELL_TPB, s,
+                       view(L.S, (const float*)L.S.val32.p, (const float*)L.S.diag32.p), L.S.nchunks, f, (const VT*)x, r);
+        }
+    });
 }
 
 template <class VT>
@@ -447,16 +490,22 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
     for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);            // (1) S_l: colours ascending
     rec_resid_level(L, f, x, lr<VT>(L), s);                              // (2a) r = f - A u
     if (l + 1 >= h.tail_start) {                                         // (2a) f_c = R r, x_c = 0
-        launch(k_restrict_zero<VT, VT>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s, full_view<VT>(L.SR),
-               L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C), lx<VT>(C));
+        with_u(L.SR.lanes, [&](auto u) {
+            launch(k_restrict_zero<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s,
+                   full_view<VT>(L.SR), L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C), lx<VT>(C));
+        });
         record_tail(h, l + 1, lf<VT>(C), lx<VT>(C), s);                  // (2b) the coarser levels, one kernel
     } else {
-        launch(k_apply_full<VT, VT>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s, full_view<VT>(L.SR),
-               L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C));
+        with_u(L.SR.lanes, [&](auto u) {
+            launch(k_apply_full<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s,
+                   full_view<VT>(L.SR), L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C));
+        });
         rec_vcycle<VT, VT>(h, l + 1, lf<VT>(C), lx<VT>(C), true, s);     // (2b) zero initial guess
     }
-    launch(k_prolong<VT, VT>, blocks_for_chunks(L.SP.nchunks), SELL_TPB, s, full_view<VT>(L.SP), L.SP.nchunks,
-           (const VT*)lx<VT>(C), x);                                     // (2c)
+    with_u(L.SP.lanes, [&](auto u) {                                     // (2c)
+        launch(k_prolong<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SP.nchunks), SELL_TPB, s,
+               full_view<VT>(L.SP), L.SP.nchunks, (const VT*)lx<VT>(C), x);
+    });
     for (int c = L.ncolours - 1; c >= 0; --c) rec_gs(L, c, f, x, s);     // (3) S_l^T: colours descending
 }
 
@@ -465,10 +514,13 @@ template <class VT>
 void rec_fine_resid(Handle& h, const double* r, const VT* z, VT* t, cudaStream_t s) {
     const Sell& A = h.Anat;
     const int g = blocks_for_chunks(A.nchunks);
-    if constexpr (std::is_same<VT, double>::value)
-        launch(k_resid<double, double, double, VT, VT>, g, SELL_TPB, s, view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, r, z, t);
-    else
-        launch(k_resid<float, float, double, VT, VT>, g, SELL_TPB, s, view(A, (const float*)A.val32.p, (const float*)A.diag32.p), A.nchunks, r, z, t);
+    with_u(A.lanes, [&](auto u) {
+        constexpr int U = decltype(u)::value;
+        if constexpr (std::is_same<VT, double>::value)
+            launch(k_resid<double, double, double, VT, VT, U>, g, SELL_TPB, s, view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, r, z, t);
+        else
+            launch(k_resid<float, float, double, VT, VT, U>, g, SELL_TPB, s, view(A, (const float*)A.val32.p, (const float*)A.diag32.p), A.nchunks, r, z, t);
+    });
 }
 
 // w = (LU)^{-1} t level by level; with zadd, z += w as well.
@@ -486,11 +538,16 @@ void rec_ic_solve(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s
     }
     for (int g = 0; g + 1 < (int)L.seg.size(); ++g) {
         const int c0 = L.seg[g], c1 = L.seg[g + 1];
-        launch(k_lsolve<VT, TT, VT>, blocks_for_chunks(c1 - c0), SELL_TPB, s, lv, c0, c1, t, y);
+        with_u(L.lanes, [&](auto u) {
+            launch(k_lsolve<VT, TT, VT, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB, s, lv, c0, c1, t, y);
+        });
     }
     for (int g = 0; g + 1 < (int)U.seg.size(); ++g) {
         const int c0 = U.seg[g], c1 = U.seg[g + 1];
-        launch(k_usolve<VT, VT>, blocks_for_chunks(c1 - c0), SELL_TPB, s, uv, c0, c1, (const VT*)y, w, zadd);
+        with_u(U.lanes, [&](auto u) {
+            launch(k_usolve<VT, VT, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB, s, uv, c0, c1,
+                   (const VT*)y, w, zadd);
+        });
     }
 }
 
@@ -560,7 +617,10 @@ void apply_precond(Handle& h, int which, const double* r, double* z) {
 
 void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s) {
     const Sell& A = h.Anat;
-    launch(k_spmv<double, double, double, double>, blocks_for_chunks(A.nchunks), SELL_TPB, s, view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, x, y);
+    with_u(A.lanes, [&](auto u) {
+        launch(k_spmv<double, double, double, double, decltype(u)::value>, blocks_for_chunks(A.nchunks), SELL_TPB, s,
+               view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, x, y);
+    });
     CPC_LAUNCH_CK();
 }
 
@@ -575,8 +635,10 @@ void level_apply(Handle& h, int l, int op, const double* x, double* y) {
         case 0:
             if (l == 0) spmv_fine(h, x, y, s);
             else if (last) fail(CPC_EINVAL, "coarsest level has no sparse layout");
-            else launch(k_spmv<double, double, double, double>, blocks_for_chunks(L.S.nchunks), SELL_TPB, s,
-                        view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nchunks, x, y);
+            else with_u(L.S.lanes, [&](auto u) {
+                launch(k_spmv<double, double, double, double, decltype(u)::value>, blocks_for_chunks(L.S.nchunks),
+                       SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nchunks, x, y);
+            });
             break;
         case 1:
         case 2:
@@ -656,9 +718,11 @@ static void build_solve_graph(Handle& h, int which) {
         launch(k_pcg_rz<float>, vec_blocks(n), VEC_TPB, cs, n, (const double*)h.r.p, (const float*)h.z32.p, h.partial.p, h.counter.p, h.state.p);
         launch(k_pcg_p<float>, vec_blocks(n), VEC_TPB, cs, n, (const float*)h.z32.p, h.p.p, (const PcgState*)h.state.p);
     }
-    launch(k_pcg_spmv, std::min(blocks_for_chunks(A.nchunks), NPART), SELL_TPB, cs,
-           view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, (const double*)h.p.p, h.q.p,
-           h.partial.p, h.counter.p, h.state.p);
+    with_u(A.lanes, [&](auto u) {
+        launch(k_pcg_spmv<decltype(u)::value>, std::min(blocks_for_chunks(A.nchunks), NPART), SELL_TPB, cs,
+               view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, (const double*)h.p.p, h.q.p,
+               h.partial.p, h.counter.p, h.state.p);
+    });
     launch(k_pcg_update, vec_blocks(n), VEC_TPB, cs, n, h.x.p, h.r.p, (const double*)h.p.p, (const double*)h.q.p,
            h.partial.p, h.counter.p, h.state.p, h.hist.p, (int)HIST_CAP, cond);
     CPC_CK(cudaStreamEndCapture(cs, &body));

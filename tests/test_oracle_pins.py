@@ -226,6 +226,71 @@ def test_colouring_is_proper(small3d):
         assert colour.min() == 0 and orc.level_sizes(l)["ncolours"] == colour.max() + 1
 
 
+def test_colouring_is_a_greedy_colouring(small3d):
+    """Every point of colour c has a neighbour of each colour c' < c (true of any greedy colouring,
+    whatever its order), so no colour class can be merged into a smaller one point by point."""
+    _, _, orc, _ = small3d
+    for l in range(orc.nlevels - 1):
+        A = orc.level_A(l)
+        _, colour = orc.level_cf_colour(l)
+        for i in range(A.n):
+            nb = {int(colour[j]) for j in A.col[A.rowptr[i]:A.rowptr[i + 1]] if j != i}
+            assert set(range(colour[i])) <= nb, (l, i)
+
+
+def fan_matrix(m):
+    """Hub 0 joined to the path 1 - 2 - ... - m: max degree m, degeneracy 2 (odd triangles, so
+    not bipartite).  Unit off-diagonal couplings, diagonal degree + 1 (SPD)."""
+    n = m + 1
+    D = np.zeros((n, n))
+    for j in range(1, n):
+        D[0, j] = D[j, 0] = -1.0
+    for j in range(1, m):
+        D[j, j + 1] = D[j + 1, j] = -1.0
+    D += np.diag(1.0 - D.sum(axis=1))
+    return D
+
+
+def dense_to_csr(D):
+    n = D.shape[0]
+    rowptr, col, val = [0], [], []
+    for i in range(n):
+        nz = np.nonzero(D[i])[0]
+        col += nz.tolist()
+        val += D[i, nz].tolist()
+        rowptr.append(len(col))
+    return O.Csr(n, np.array(rowptr, np.int32), np.array(col, np.int32), np.array(val))
+
+
+def test_colouring_bounded_by_degeneracy():
+    """Peel rounds take points of degree <= 2 d_min, and d_min of any subgraph is at most the
+    degeneracy k, so a point sees at most 2k neighbours of higher priority: <= 2k + 1 colours.
+    The fan graph has k = 2 but a hub of degree 40, so a colouring that ignores the peel order
+    would be allowed up to 41 colours by the plain greedy bound."""
+    A = dense_to_csr(fan_matrix(40))
+    orc = O.Oracle(A, coarse_max=4)
+    assert orc.nlevels >= 2
+    _, colour = orc.level_cf_colour(0)
+    D = A.to_dense()
+    ii, jj = np.nonzero(D)
+    off = ii != jj
+    assert np.all(colour[ii[off]] != colour[jj[off]])
+    assert 3 <= colour.max() + 1 <= 5
+
+
+def test_colouring_bound_on_amg_levels(small3d):
+    nx = pytest.importorskip("networkx")
+    _, _, orc, _ = small3d
+    for l in range(1, orc.nlevels - 1):
+        A = orc.level_A(l)
+        G = nx.Graph()
+        G.add_nodes_from(range(A.n))
+        for i in range(A.n):
+            G.add_edges_from((i, int(j)) for j in A.col[A.rowptr[i]:A.rowptr[i + 1]] if j != i)
+        k = max(nx.core_number(G).values())
+        assert orc.level_sizes(l)["ncolours"] <= 2 * k + 1, l
+
+
 def gs_dense(D, colour, backward):
     n = D.shape[0]
     M = np.diag(np.diag(D)).copy()
