@@ -9,7 +9,9 @@ CUDA library.
 Operator codes for :meth:`Oracle.apply` / :meth:`Oracle.pcg`:
 ``BCO`` (Algorithm 2.1, Eq. barB), ``S`` (one V-cycle, Algorithm 3.2), ``ST`` (its
 adjoint), ``B`` (IC(0), Algorithm 3.1 with k = 0), ``STILDE`` (two cycles,
-S~ = S + S^T - S^T A S), ``BHAT`` (additive S~ + B, Eq. Ba), ``A``, ``I``.
+S~ = S + S^T - S^T A S), ``BHAT`` (additive S~ + B, Eq. Ba), ``A``, ``I``,
+``S_ILU`` (one V-cycle with IC(0) as the finest smoother) and ``AMG_ILU`` (two such
+cycles: AMG(ILU(0)) of Section 5).
 """
 from __future__ import annotations
 
@@ -23,8 +25,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.cpp")
 LIB = os.path.join(HERE, "_liboracle.so")
 
-BCO, S, ST, B, STILDE, BHAT, A, I = range(8)
-OPS = {"bco": BCO, "amg": STILDE, "ilu": B, "bhat": BHAT, "none": I}
+BCO, S, ST, B, STILDE, BHAT, A, I, S_ILU, AMG_ILU = range(10)
+OPS = {"bco": BCO, "amg": STILDE, "ilu": B, "bhat": BHAT, "none": I, "amg_ilu": AMG_ILU}
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "IC(0) breakdown", 3: "not converged",
           4: "CG breakdown", 7: "AMG setup failure"}

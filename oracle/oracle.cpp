@@ -17,6 +17,8 @@
  *   vcycle         Algorithm 3.2 with Gauss-Seidel smoothers S_l (multicolour order), exact
  *                  coarsest solve.
  *   apply_bco      Algorithm 2.1 with u^{k,0} = 0, giving B_co of Eq. barB.
+ *   apply_stilde   two V-cycles (AMG(GS) of Section 5); with the IC(0) preconditioner as the
+ *                  finest-level smoother, AMG(ILU(0)) of Section 5.
  *   pcg            textbook preconditioned CG (the Krylov method the paper runs, Section 5).
  *   tpfa_gradient  -lambda^T (dA/dlog k) p, the adjoint gradient of a misfit through the assembly.
  *
@@ -593,9 +595,21 @@ struct Oracle {
 // pre-smoother N^T and post-smoother M^T (take the A-adjoint of the error propagation of
 // Section 3.3 factor by factor); transpose_cycle() builds it that way.  With M = S_l and
 // N = S_l^T it is the same cycle, so S^T = S.
-struct Cycle { bool pre_bwd = false, post_bwd = true; };
+//
+// AMG(ILU(0)) of Section 5 replaces the smoother on the finest level by the IC(0) preconditioner
+// B: one smoothing step is u <- u + B (f - A u) both before and after the coarse correction.  B is
+// symmetric, so that cycle is its own transpose as well.
+struct Cycle { bool pre_bwd = false, post_bwd = true, ilu_fine = false; };
 
-Cycle transpose_cycle(Cycle c) { Cycle t; t.pre_bwd = !c.post_bwd; t.post_bwd = !c.pre_bwd; return t; }
+Cycle transpose_cycle(Cycle c) {
+    Cycle t;
+    t.pre_bwd = !c.post_bwd;
+    t.post_bwd = !c.pre_bwd;
+    t.ilu_fine = c.ilu_fine;
+    return t;
+}
+
+void apply_B(const struct Oracle& O, const double* r, double* z);
 
 void vcycle(const Oracle& O, int l, const double* f, double* u, Cycle cy) {
     const Level& L = O.H.lev[l];
@@ -604,9 +618,11 @@ void vcycle(const Oracle& O, int l, const double* f, double* u, Cycle cy) {
         dense_cholesky_solve(O.H.chol, n, f, u);
         return;
     }
+    const bool ilu = cy.ilu_fine && l == 0;
     vector<double> r(n), d(n);
     residual(L.A, f, u, r.data());                              // (1) pre-smoothing
-    gs_apply(L, O.gs_natural, cy.pre_bwd, r.data(), d.data());
+    if (ilu) apply_B(O, r.data(), d.data());
+    else gs_apply(L, O.gs_natural, cy.pre_bwd, r.data(), d.data());
     for (int i = 0; i < n; ++i) u[i] += d[i];
     residual(L.A, f, u, r.data());                              // (2a) restriction
     const int nc = L.P.m;
@@ -617,15 +633,18 @@ void vcycle(const Oracle& O, int l, const double* f, double* u, Cycle cy) {
     spmv(L.P, e.data(), pe.data());                             // (2c) prolongation
     for (int i = 0; i < n; ++i) u[i] += pe[i];
     residual(L.A, f, u, r.data());                              // (3) post-smoothing
-    gs_apply(L, O.gs_natural, cy.post_bwd, r.data(), d.data());
+    if (ilu) apply_B(O, r.data(), d.data());
+    else gs_apply(L, O.gs_natural, cy.post_bwd, r.data(), d.data());
     for (int i = 0; i < n; ++i) u[i] += d[i];
 }
 
-// z = S r (transpose = false) or z = S^T r (transpose = true), zero initial guess.
-void apply_S(const Oracle& O, const double* r, double* z, bool transpose) {
+// z = S r (transpose = false) or z = S^T r (transpose = true), zero initial guess; with ilu_fine
+// the cycle of AMG(ILU(0)).
+void apply_S(const Oracle& O, const double* r, double* z, bool transpose, bool ilu_fine = false) {
     const int n = O.A.n;
     for (int i = 0; i < n; ++i) z[i] = 0.0;
     Cycle cy;
+    cy.ilu_fine = ilu_fine;
     vcycle(O, 0, r, z, transpose ? transpose_cycle(cy) : cy);
 }
 
@@ -651,13 +670,14 @@ void apply_bco(const Oracle& O, const double* r, double* z) {
     for (int i = 0; i < n; ++i) z[i] = u2[i] + c[i];
 }
 
-// S~ = S + S^T - S^T A S: two cycles, I - S~A = (I - S^T A)(I - S A) (the "AMG alone" preconditioner).
-void apply_stilde(const Oracle& O, const double* r, double* z) {
+// S~ = S + S^T - S^T A S: two cycles, I - S~A = (I - S^T A)(I - S A) (the "AMG alone" preconditioner
+// AMG(GS) of Section 5; with ilu_fine, AMG(ILU(0)): the same two cycles with B as finest smoother).
+void apply_stilde(const Oracle& O, const double* r, double* z, bool ilu_fine = false) {
     const int n = O.A.n;
     vector<double> u1(n), t(n), c(n);
-    apply_S(O, r, u1.data(), false);
+    apply_S(O, r, u1.data(), false, ilu_fine);
     residual(O.A, r, u1.data(), t.data());
-    apply_S(O, t.data(), c.data(), true);
+    apply_S(O, t.data(), c.data(), true, ilu_fine);
     for (int i = 0; i < n; ++i) z[i] = u1[i] + c[i];
 }
 
@@ -670,7 +690,8 @@ void apply_bhat(const Oracle& O, const double* r, double* z) {
     for (int i = 0; i < n; ++i) z[i] = a[i] + b[i];
 }
 
-enum Op { OP_BCO = 0, OP_S = 1, OP_ST = 2, OP_B = 3, OP_STILDE = 4, OP_BHAT = 5, OP_A = 6, OP_I = 7 };
+enum Op { OP_BCO = 0, OP_S = 1, OP_ST = 2, OP_B = 3, OP_STILDE = 4, OP_BHAT = 5, OP_A = 6, OP_I = 7,
+          OP_S_ILU = 8, OP_AMG_ILU = 9 };
 
 int apply_op(const Oracle& O, int op, const double* r, double* z) {
     const int n = O.A.n;
@@ -683,6 +704,8 @@ int apply_op(const Oracle& O, int op, const double* r, double* z) {
         case OP_BHAT: apply_bhat(O, r, z); return 0;
         case OP_A: spmv(O.A, r, z); return 0;
         case OP_I: for (int i = 0; i < n; ++i) z[i] = r[i]; return 0;
+        case OP_S_ILU: apply_S(O, r, z, false, true); return 0;
+        case OP_AMG_ILU: apply_stilde(O, r, z, true); return 0;
     }
     return 1;
 }

@@ -339,6 +339,26 @@ def test_vcycle_matches_recursion(small3d):
         Bnext = B
 
 
+def test_amg_ilu_cycle_matches_error_propagation(small3d):
+    """AMG(ILU(0)) of Section 5: the V-cycle with the IC(0) preconditioner B as the finest smoother,
+    I - S A = (I - B A)(I - P B_1 P^T A)(I - B A) with B_1 the GS V-cycle of level 1 (pinned by the
+    recursion test) and B the IC(0) solve (pinned by the IC tests), applied as two cycles:
+    I - S~ A = (I - S A)^2 (S is symmetric since B is)."""
+    _, A, orc, D = small3d
+    n = D.shape[0]
+    I = np.eye(n)
+    B = dense_op(lambda v: orc.apply(O.B, v), n)
+    P = orc.level_P(0).to_dense()
+    B1 = dense_op(lambda v: orc.level_apply(1, 4, v), P.shape[1])
+    E = (I - B @ D) @ (I - P @ B1 @ P.T @ D) @ (I - B @ D)
+    Ainv = np.linalg.inv(D)
+    S = dense_op(lambda v: orc.apply(O.S_ILU, v), n)
+    assert rel(S, (I - E) @ Ainv) < 1e-11
+    St = dense_op(lambda v: orc.apply(O.AMG_ILU, v), n)
+    assert rel(St, (I - E @ E) @ Ainv) < 1e-11
+    assert rel(St, St.T) < 1e-11
+
+
 def test_vcycle_symmetric_and_adjoint(small3d):
     _, A, orc, D = small3d
     n = A.n
