@@ -45,7 +45,10 @@ enum {
     CPC_PRECOND_AMG = 1,    /* S~ = S + S^T - S^T A S: two V-cycles ("AMG(GS)", Section 5)       */
     CPC_PRECOND_IC0 = 2,    /* B = IC(0) alone ("ILU(0)", Section 5)                             */
     CPC_PRECOND_BHAT = 3,   /* additive B^ = S~ + B, Eq. Ba with W_1 = V, Pi_1 = I, A_1^{-1} = B  */
-    CPC_PRECOND_NONE = 4    /* identity (plain CG)                                               */
+    CPC_PRECOND_NONE = 4,   /* identity (plain CG)                                               */
+    CPC_PRECOND_AMG_ILU = 5 /* "AMG(ILU(0))", Section 5: two V-cycles whose finest smoother is one  */
+                            /* IC(0) step u += B (f - A u) before and after the coarse correction    */
+                            /* (GS on the other levels).  Single right-hand side only.               */
 };
 
 /* Precision of the preconditioner (the outer PCG is always FP64). */

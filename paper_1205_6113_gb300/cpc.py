@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcpc.so")
 
-PRECOND = {"bco": 0, "amg": 1, "ic0": 2, "ilu": 2, "bhat": 3, "none": 4}
+PRECOND = {"bco": 0, "amg": 1, "ic0": 2, "ilu": 2, "bhat": 3, "none": 4, "amg_ilu": 5}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_bf16": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "IC(0) breakdown", 3: "not converged", 4: "CG breakdown",
           5: "CUDA error", 6: "device wait timeout", 7: "AMG setup failure"}

@@ -9,7 +9,7 @@ constexpr int CHUNK = 32;            // SELL chunk height = warp width
 constexpr int DENSE_MAX = 4096;      // largest coarsest level solved by the dense inverse
 constexpr int HIST_CAP = 100001;     // residual-history capacity on the device
 constexpr int NPART = 1024;          // partial-sum slots for deterministic reductions
-constexpr int NPRECOND = 5;          // CPC_PRECOND_* values
+constexpr int NPRECOND = 6;          // CPC_PRECOND_* values
 
 // One AMG level (0 = finest).
 struct Level {

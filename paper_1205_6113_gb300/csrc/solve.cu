@@ -476,9 +476,27 @@ SV<VT, VT> full_view(const Sell& S) {
     else return view(S, (const float*)S.val32.p, (const float*)nullptr);
 }
 
-// Algorithm 3.2 from level l: x <- V-cycle(f, initial guess x) (zero guess when zero_guess).
+template <class VT> void rec_fine_resid(Handle& h, const double* r, const VT* z, VT* t, cudaStream_t s);
+template <class TT, class VT> void rec_ic_solve(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s);
+template <class VT> VT* ft(Handle& h);
+template <class VT> VT* fy(Handle& h);
+
+// One IC(0) smoothing step on the finest level, x <- x + B (f - A x) (AMG(ILU(0)), Section 5).
+template <class VT>
+void rec_ic_smooth(Handle& h, const double* f, VT* x, bool zero_guess, cudaStream_t s) {
+    if (zero_guess) {
+        rec_ic_solve<double, VT>(h, f, fy<VT>(h), x, (VT*)nullptr, s);      // x = B f
+    } else {
+        VT* t = ft<VT>(h);
+        rec_fine_resid<VT>(h, f, x, t, s);
+        rec_ic_solve<VT, VT>(h, t, fy<VT>(h), t, x, s);
+    }
+}
+
+// Algorithm 3.2 from level l: x <- V-cycle(f, initial guess x) (zero guess when zero_guess).  With
+// ilu, the finest level is smoothed by IC(0) steps instead of Gauss-Seidel sweeps.
 template <class FT, class VT>
-void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s) {
+void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s, bool ilu = false) {
     const int nl = (int)h.lev.size();
     Level& L = h.lev[l];
     if (l == nl - 1) {                                          // step 2(b): exact coarsest solve
@@ -486,8 +504,14 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
         return;
     }
     Level& C = h.lev[l + 1];
-    if (zero_guess) launch(k_zero<VT>, vec_blocks(L.n), VEC_TPB, s, (int64_t)L.n, x);
-    for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);            // (1) S_l: colours ascending
+    const bool ilu_here = ilu && l == 0;
+    if constexpr (std::is_same<FT, double>::value) {
+        if (ilu_here) rec_ic_smooth<VT>(h, f, x, zero_guess, s);          // (1) IC(0) step
+    }
+    if (!ilu_here) {
+        if (zero_guess) launch(k_zero<VT>, vec_blocks(L.n), VEC_TPB, s, (int64_t)L.n, x);
+        for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);        // (1) S_l: colours ascending
+    }
     rec_resid_level(L, f, x, lr<VT>(L), s);                              // (2a) r = f - A u
     if (l + 1 >= h.tail_start) {                                         // (2a) f_c = R r, x_c = 0
         with_u(L.SR.lanes, [&](auto u) {
@@ -506,6 +530,12 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
         launch(k_prolong<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SP.nchunks), SELL_TPB, s,
                full_view<VT>(L.SP), L.SP.nchunks, (const VT*)lx<VT>(C), x);
     });
+    if constexpr (std::is_same<FT, double>::value) {
+        if (ilu_here) {
+            rec_ic_smooth<VT>(h, f, x, false, s);                          // (3) IC(0) step (B = B^T)
+            return;
+        }
+    }
     for (int c = L.ncolours - 1; c >= 0; --c) rec_gs(L, c, f, x, s);     // (3) S_l^T: colours descending
 }
 
@@ -576,6 +606,10 @@ void rec_precond_t(Handle& h, int which, const double* r, VT* z, cudaStream_t s)
             break;
         case CPC_PRECOND_IC0:
             rec_ic_solve<double, VT>(h, r, y, z, (VT*)nullptr, s);
+            break;
+        case CPC_PRECOND_AMG_ILU:                     // two cycles with IC(0) as the finest smoother
+            rec_vcycle<double, VT>(h, 0, r, z, true, s, true);
+            rec_vcycle<double, VT>(h, 0, r, z, false, s, true);
             break;
         case CPC_PRECOND_BHAT:                        // S~ r + B r
             rec_vcycle<double, VT>(h, 0, r, z, true, s);

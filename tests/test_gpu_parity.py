@@ -108,7 +108,8 @@ def test_level_operators_match_oracle(case):
             assert rel(y, orc.level_apply(l, op, x)) < 1e-11, (l, op)
 
 
-@pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT)])
+@pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT),
+                                      ("amg_ilu", O.AMG_ILU)])
 def test_preconditioner_matches_oracle(case, which, op):
     _, A, orc, s = case
     r = inputs.random_vector(A.n, seed=7)
@@ -116,7 +117,8 @@ def test_preconditioner_matches_oracle(case, which, op):
     assert rel(z, orc.apply(op, r)) < 1e-11
 
 
-@pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT)])
+@pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT),
+                                      ("amg_ilu", O.AMG_ILU)])
 def test_pcg_matches_oracle(case, which, op):
     p, A, orc, _ = case
     s = cpc.Solver(A.rowptr, A.col, A.val, precond=which, coarse_max=64)
