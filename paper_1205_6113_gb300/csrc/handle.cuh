@@ -22,6 +22,8 @@ struct Level {
     Sell S;                 // rows grouped by colour, diagonal split: Gauss-Seidel and residual
     Sell SP, SR;            // P and R, natural row order
     VType vt = VT_F64;      // storage type of this level's operators in the preconditioner
+    DBuf<double> dnat64;    // 1 / a_ii in natural row order (first colour step from a zero guess)
+    DBuf<float> dnat32;
     DBuf<double> x64, f64, r64;
     DBuf<float> x32, f32, r32;
 };

@@ -622,6 +622,12 @@ __global__ void k_sell_width(const int* perm, int nchunks, int C, const int* ptr
     width[k] = w * C;
 }
 
+template <class T>
+__global__ void k_slot_to_nat(int nslots, const int* perm, const T* v, T* out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nslots && perm[s] >= 0) out[perm[s]] = v[s];
+}
+
 __global__ void k_max_int(const int* a, int n, int* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicMax(out, a[i]);
@@ -1398,6 +1404,14 @@ void setup_handle(Handle& h, const cpc_csr& in) {
             sell_lowp(L.S, L.vt, s);
             sell_lowp(L.SP, L.vt == VT_BF16 ? VT_F32 : L.vt, s);
             sell_lowp(L.SR, L.vt == VT_BF16 ? VT_F32 : L.vt, s);
+            if (L.vt == VT_F64) {
+                L.dnat64.alloc(L.n);
+                k_slot_to_nat<<<nblk(L.S.nslots), TPB, 0, s>>>(L.S.nslots, L.S.perm.p, L.S.dinv.p, L.dnat64.p);
+            } else {
+                L.dnat32.alloc(L.n);
+                k_slot_to_nat<<<nblk(L.S.nslots), TPB, 0, s>>>(L.S.nslots, L.S.perm.p, L.S.dinv32.p, L.dnat32.p);
+            }
+            CPC_LAUNCH_CK();
         }
         const size_t n = L.n;
         if (L.vt == VT_F64) { L.x64.alloc(n); L.f64.alloc(n); L.r64.alloc(n); }

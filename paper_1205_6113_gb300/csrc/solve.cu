@@ -151,6 +151,44 @@ __global__ void __launch_bounds__(SELL_TPB) k_restrict_zero(SV<MT, MT> M, int nc
     }
 }
 
+// f_c = R r, and the first colour step of the coarse sweep from a zero guess fused with the zero
+// fill: x_c = f_c / a_ii on colour 0 (its rows see only zeros), 0 elsewhere.
+template <class MT, class VT, int U>
+__global__ void __launch_bounds__(SELL_TPB) k_restrict_first(SV<MT, MT> M, int nchunks, const VT* __restrict__ x,
+                                                              VT* __restrict__ y, VT* __restrict__ yx,
+                                                              const int* __restrict__ colour,
+                                                              const VT* __restrict__ dnat) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, C = M.C, r = lane & (C - 1), g = lane / C;
+    for (int k = blockIdx.x * WPB + (threadIdx.x >> 5); k < nchunks; k += gridDim.x * WPB) {
+        const int row = M.perm[k * C + r];
+        const bool own = g == 0 && row >= 0;
+        int cr = 1;
+        VT dr = VT(0);
+        if (own) {
+            cr = colour[row];
+            dr = dnat[row];
+        }
+        VT dot = sell_dot<VT, false, U>(M.col, M.val, M.cptr[k] + g * C + r, M.cptr[k + 1], x);
+        dot = sub_sum(dot, C);
+        if (own) {
+            y[row] = dot;
+            yx[row] = cr == 0 ? dot * dr : VT(0);
+        }
+    }
+}
+
+// The same on the finest level (f given): x = f / a_ii on colour 0, 0 elsewhere.
+template <class FT, class VT>
+__global__ void k_zero_first(int64_t n, const FT* __restrict__ f, const int* __restrict__ colour,
+                             const VT* __restrict__ dnat, VT* __restrict__ x) {
+    pdl_launch_dependents();
+    pdl_wait();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = colour[i] == 0 ? Cv<VT>::f(f[i]) * dnat[i] : VT(0);
+}
+
 // x += P e (prolongation and correction).
 template <class MT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_prolong(SV<MT, MT> P, int nchunks, const VT* __restrict__ e,
@@ -493,10 +531,18 @@ void rec_ic_smooth(Handle& h, const double* f, VT* x, bool zero_guess, cudaStrea
     }
 }
 
+template <class VT> const VT* dnat(const Level& L);
+template <> const double* dnat<double>(const Level& L) { return L.dnat64.p; }
+template <> const float* dnat<float>(const Level& L) { return L.dnat32.p; }
+
 // Algorithm 3.2 from level l: x <- V-cycle(f, initial guess x) (zero guess when zero_guess).  With
-// ilu, the finest level is smoothed by IC(0) steps instead of Gauss-Seidel sweeps.
+// ilu, the finest level is smoothed by IC(0) steps instead of Gauss-Seidel sweeps.  With
+// first_done the caller has already applied the first colour step from the zero guess (and
+// zeroed the other rows), so the forward sweep starts at colour 1.  A Gauss-Seidel step from
+// zero on colour 0 reads only zeros, so x_i = (f_i - 0) / a_ii = f_i / a_ii exactly.
 template <class FT, class VT>
-void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s, bool ilu = false) {
+void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s, bool ilu = false,
+                bool first_done = false) {
     const int nl = (int)h.lev.size();
     Level& L = h.lev[l];
     if (l == nl - 1) {                                          // step 2(b): exact coarsest solve
@@ -509,8 +555,15 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
         if (ilu_here) rec_ic_smooth<VT>(h, f, x, zero_guess, s);          // (1) IC(0) step
     }
     if (!ilu_here) {
-        if (zero_guess) launch(k_zero<VT>, vec_blocks(L.n), VEC_TPB, s, (int64_t)L.n, x);
-        for (int c = 0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);        // (1) S_l: colours ascending
+        int c0 = 0;
+        if (first_done) {
+            c0 = 1;
+        } else if (zero_guess) {
+            launch(k_zero_first<FT, VT>, vec_blocks(L.n), VEC_TPB, s, (int64_t)L.n, f, (const int*)L.colour.p,
+                   dnat<VT>(L), x);
+            c0 = 1;
+        }
+        for (int c = c0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);       // (1) S_l: colours ascending
     }
     rec_resid_level(L, f, x, lr<VT>(L), s);                              // (2a) r = f - A u
     if (l + 1 >= h.tail_start) {                                         // (2a) f_c = R r, x_c = 0
@@ -519,12 +572,19 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
                    full_view<VT>(L.SR), L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C), lx<VT>(C));
         });
         record_tail(h, l + 1, lf<VT>(C), lx<VT>(C), s);                  // (2b) the coarser levels, one kernel
-    } else {
+    } else if (l + 1 == nl - 1) {                                       // (2a) f_c = R r
         with_u(L.SR.lanes, [&](auto u) {
             launch(k_apply_full<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s,
                    full_view<VT>(L.SR), L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C));
         });
-        rec_vcycle<VT, VT>(h, l + 1, lf<VT>(C), lx<VT>(C), true, s);     // (2b) zero initial guess
+        rec_vcycle<VT, VT>(h, l + 1, lf<VT>(C), lx<VT>(C), true, s);     // (2b) exact coarsest solve
+    } else {                                                             // (2a) f_c = R r, first colour step
+        with_u(L.SR.lanes, [&](auto u) {
+            launch(k_restrict_first<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s,
+                   full_view<VT>(L.SR), L.SR.nchunks, (const VT*)lr<VT>(L), lf<VT>(C), lx<VT>(C),
+                   (const int*)C.colour.p, dnat<VT>(C));
+        });
+        rec_vcycle<VT, VT>(h, l + 1, lf<VT>(C), lx<VT>(C), true, s, false, true);   // (2b) zero initial guess
     }
     with_u(L.SP.lanes, [&](auto u) {                                     // (2c)
         launch(k_prolong<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SP.nchunks), SELL_TPB, s,
