@@ -63,6 +63,12 @@ struct Handle {
     DBuf<int> lu_diag;      // position of the diagonal in each row of Aic
     DBuf<int> ic_order;     // ic row q <- original row ic_order[q] (empty: natural)
     int ic_levels_L = 0, ic_levels_U = 0;
+    // Red-black IC(0) in B_co: black rows of L (chunks [ic_black_c0, ic_black_c1)) and 1 / u_ii in
+    // natural order, when the IC order is the fine 2-colouring with every black row coupled.
+    bool ic_rb = false;
+    int ic_rows_L1 = 0, ic_black_c0 = 0, ic_black_c1 = 0;
+    DBuf<double> ic_uinv64;
+    DBuf<float> ic_uinv32;
     Sell L, U;              // strictly-lower rows by forward level; upper rows by backward level
     // coarsest level: dense inverse
     int nc = 0;

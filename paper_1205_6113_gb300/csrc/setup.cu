@@ -960,6 +960,7 @@ void setup_ic0(Handle& h, cudaStream_t s) {
         CPC_CK(cudaMemcpyAsync(hc.data(), cnt.get(), sizeof(int) * h.ic_levels_L, cudaMemcpyDeviceToHost, s));
         CPC_CK(cudaStreamSynchronize(s));
     }
+    h.ic_rows_L1 = h.ic_levels_L > 1 ? hc[1] : 0;
     Tmp<int> failrow(1, s);
     k_fill_int<<<1, 1, 0, s>>>(failrow.get(), 1, INT_MAX);
     int off = 0;
@@ -983,6 +984,40 @@ void setup_ic0(Handle& h, cudaStream_t s) {
     grouped_slots(n, lvl.get(), h.ic_levels_U, CHUNK, s, slotsU, nslotsU, segU);
     build_sell(A.ptr.p, A.col.p, h.lu.p, slotsU, nslotsU, segU, CHUNK, SELL_UPPER, true, imap, h.U, s);
     CPC_CK(cudaStreamSynchronize(s));
+}
+
+__global__ void k_count_eq(int n, const int* a, int v, int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && a[i] == v) atomicAdd(cnt, 1);
+}
+
+// Red-black IC(0) in B_co.  With the IC order = (fine colour, index) of a 2-colouring, red rows
+// (colour 0, first) have no entries in L and black rows none in U.  Black rows with at least one
+// neighbour form the second forward level; when that is every black row, step (2) of B_co reduces
+// to one pass over them: z_b += (t_b - sum_{j red} l_bj t_j) / u_bb.  The red rows' backward step
+// is left out: step (3) starts with a Gauss-Seidel step on the red rows, which overwrites z there
+// without reading it.
+void setup_ic_rb(Handle& h, bool colour_ic, cudaStream_t s) {
+    h.ic_rb = false;
+    if (!colour_ic || h.lev.size() < 2 || h.lev[0].ncolours != 2 || h.ic_levels_L != 2 || h.ic_levels_U != 2) return;
+    const Level& L0 = h.lev[0];
+    Tmp<int> cnt(1, s);
+    CPC_CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int), s));
+    k_count_eq<<<nblk(L0.n), TPB, 0, s>>>(L0.n, L0.colour.p, 1, cnt.get());
+    const int black = d2h(cnt.get(), s);
+    if (black != h.ic_rows_L1) return;
+    h.ic_black_c0 = h.L.seg[1];
+    h.ic_black_c1 = h.L.seg[2];
+    if (h.opt.precision == CPC_PREC_FP64) {
+        h.ic_uinv64.alloc(h.n);
+        k_slot_to_nat<<<nblk(h.U.nslots), TPB, 0, s>>>(h.U.nslots, h.U.perm.p, h.U.dinv.p, h.ic_uinv64.p);
+    } else {
+        h.ic_uinv32.alloc(h.n);
+        k_slot_to_nat<<<nblk(h.U.nslots), TPB, 0, s>>>(h.U.nslots, h.U.perm.p, h.U.dinv32.p, h.ic_uinv32.p);
+    }
+    CPC_LAUNCH_CK();
+    CPC_CK(cudaStreamSynchronize(s));
+    h.ic_rb = true;
 }
 
 void setup_level_sells(Level& L, cudaStream_t s, bool last) {
@@ -1425,6 +1460,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         k_to_f32<<<nblk((int64_t)h.nc * h.nc), TPB, 0, s>>>((int64_t)h.nc * h.nc, h.Ainv.p, h.Ainv32.p);
         h.z32.alloc(h.n); h.t32.alloc(h.n); h.y32.alloc(h.n);
     }
+    setup_ic_rb(h, colour_ic, s);
     setup_tail(h, h.opt.tail_nnz_max == 0 ? TAIL_NNZ_MAX : h.opt.tail_nnz_max);
     // PCG and preconditioner vectors
     const size_t n = h.n;

@@ -280,6 +280,33 @@ __global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> Uf, int c0, int 
     }
 }
 
+// B_co step (2) right after step (1) with red-black IC(0): step (1) ends with a Gauss-Seidel step on
+// the red rows, which leaves their residual t_r = 0 (up to rounding), so the forward solve gives
+// y_b = t_b and z_b += (r_b - (A z)_b) / u_bb on the black rows (fine colour 1, chunks [c0, c1) of
+// the colour-grouped A) is the whole step; the red rows' part is overwritten by step (3).
+template <class MT, class DT, class VT, int U>
+__global__ void __launch_bounds__(SELL_TPB) k_bco_black(SV<MT, DT> A, int c0, int c1, const double* __restrict__ r,
+                                                         const VT* __restrict__ uinv, VT* __restrict__ z) {
+    const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (k >= c1) return;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31, C = A.C, rr = lane & (C - 1), g = lane / C;
+    const int s = k * C + rr;
+    const int row = A.perm[s];
+    const bool own = g == 0 && row >= 0;
+    const VT ui = own ? uinv[row] : VT(0);
+    const VT dg = own ? Cv<VT>::f(A.diag[s]) : VT(0);
+    VT fr = VT(0), zr = VT(0);
+    VT dot = sell_dot<VT, true, U>(A.col, A.val, A.cptr[k] + g * C + rr, A.cptr[k + 1], z, [&] {
+        if (own) {
+            fr = Cv<VT>::f(r[row]);
+            zr = z[row];
+        }
+    });
+    dot = sub_sum(dot, C);
+    if (own) z[row] = zr + (fr - (dg * zr + dot)) * ui;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Deterministic reductions: block tree, then the last block to finish sums the partials in order.
 // ---------------------------------------------------------------------------------------------
@@ -641,6 +668,23 @@ void rec_ic_solve(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s
     }
 }
 
+// B_co step (2) with red-black IC(0), right after step (1): black rows only (k_bco_black).
+template <class VT>
+void rec_bco_black(Handle& h, const double* r, VT* z, cudaStream_t s) {
+    const Level& L0 = h.lev[0];
+    const Sell& S = L0.S;
+    const int c0 = S.seg[1], c1 = S.seg[2];
+    if (c1 <= c0) return;
+    with_u(S.lanes, [&](auto u) {
+        if constexpr (std::is_same<VT, double>::value)
+            launch(k_bco_black<double, double, double, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB, s,
+                   view(S, (const double*)S.val.p, (const double*)S.diag.p), c0, c1, r, (const double*)h.ic_uinv64.p, z);
+        else
+            launch(k_bco_black<float, float, float, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB, s,
+                   view(S, (const float*)S.val32.p, (const float*)S.diag32.p), c0, c1, r, (const float*)h.ic_uinv32.p, z);
+    });
+}
+
 template <class VT> VT* ft(Handle& h);
 template <> double* ft<double>(Handle& h) { return h.t.p; }
 template <> float* ft<float>(Handle& h) { return h.t32.p; }
@@ -656,8 +700,12 @@ void rec_precond_t(Handle& h, int which, const double* r, VT* z, cudaStream_t s)
     switch (which) {
         case CPC_PRECOND_BCO:                         // Algorithm 2.1 with u^{k,0} = 0
             rec_vcycle<double, VT>(h, 0, r, z, true, s);        // (1) z = S r
-            rec_fine_resid<VT>(h, r, z, t, s);                  // (2) z += B (r - A z)
-            rec_ic_solve<VT, VT>(h, t, y, t, z, s);
+            if (h.ic_rb) {                                      // (2) z += B (r - A z)
+                rec_bco_black<VT>(h, r, z, s);
+            } else {
+                rec_fine_resid<VT>(h, r, z, t, s);
+                rec_ic_solve<VT, VT>(h, t, y, t, z, s);
+            }
             rec_vcycle<double, VT>(h, 0, r, z, false, s);       // (3) z += S^T (r - A z), S^T = S
             break;
         case CPC_PRECOND_AMG:                         // S~: two cycles
