@@ -34,9 +34,10 @@ TOL = 1e-6
 MAXIT = 5000
 METRIC = "PCG ms to 1e-6 rel. residual (combined vs AMG/ILU alone, FP32 vs FP64 prec), %HBM peak"
 L2_FLUSH_BYTES = 512 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one fine-level k_gs launch from the committed ncu
-# capture (profiles/k_gs_fine_correlated3d_128x128x64.md); None until a capture of the current kernel.
-TRAFFIC_K_GS_FINE = 60980480
+# dram__bytes_read.sum + dram__bytes_write.sum of one fine-level Gauss-Seidel launch from the
+# committed ncu capture (profiles/k_gs_dia_fine_correlated3d_128x128x64.md); None until a capture
+# of the current kernel exists.
+TRAFFIC_K_GS_FINE = 48349184
 
 
 def peaks():
@@ -107,17 +108,29 @@ def a_pass_bytes(n, nnz, sv=8, sx=8):
     return nnz * (sv + 4) + 4 * (n + 1) + 2 * n * sx
 
 
+def dia_pass_bytes(n, nd, sv=8, sx=8):
+    """One sweep over a matrix in diagonal form: nd stored diagonals + the diagonal, read x, write y."""
+    return n * (nd * sv + sv + 2 * sx)
+
+
 def bytes_per_iteration(s, precond, sv=8, sx=8, sv_coarse=None):
     sv_coarse = sv if sv_coarse is None else sv_coarse
     nl = s.nlevels
     info = [s.level_info(l) for l in range(nl)]
+    lay0 = s.level_layout(0)
+
+    def a_pass(l, svl):
+        i = info[l]
+        if l == 0 and lay0["ndiag"]:
+            return dia_pass_bytes(i["n"], lay0["ndiag"], svl, sx)
+        return a_pass_bytes(i["n"], i["nnz"], svl, sx)
 
     def vcycle(ilu_fine=False):
         b = 0
         for l in range(nl - 1):
             i = info[l]
             svl = sv if l == 0 else sv_coarse
-            b += 3 * a_pass_bytes(i["n"], i["nnz"], svl, sx)          # pre sweep, residual, post sweep
+            b += 3 * a_pass(l, svl)                                     # pre sweep, residual, post sweep
             if l == 0 and ilu_fine:                                     # + the two IC(0) solves
                 b += 2 * a_pass_bytes(i["n"], i["nnz"], svl, sx)
             b += 2 * a_pass_bytes(i["n"], i["nnzP"], 4 if sx == 4 else 8, sx)   # restriction, prolongation
@@ -127,8 +140,11 @@ def bytes_per_iteration(s, precond, sv=8, sx=8, sv_coarse=None):
 
     n, nnz = info[0]["n"], info[0]["nnz"]
     ic = a_pass_bytes(n, nnz, sv, sx)                                   # L and U together touch A's pattern once
-    pcg = a_pass_bytes(n, nnz, 8, 8) + 12 * n * 8                       # q = A p plus the vector updates
+    nat = dia_pass_bytes(n, lay0["nat_ndiag"], 8, 8) if lay0["nat_ndiag"] else a_pass_bytes(n, nnz, 8, 8)
+    pcg = nat + 12 * n * 8                                              # q = A p plus the vector updates
     if precond == "bco":
+        if lay0["ndiag"] and s.ic_order == "colour":                    # step (2): one pass over the black rows
+            return pcg + 2 * vcycle() + dia_pass_bytes(n // 2, lay0["ndiag"], sv, sx) + n // 2 * sx
         return pcg + 2 * vcycle() + a_pass_bytes(n, nnz, sv, sx) + ic
     if precond == "amg":
         return pcg + 2 * vcycle()
@@ -282,7 +298,13 @@ def gpu_arm(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         kms.append(e0.elapsed_time(e1) / info0["ncolours"])
-    kbytes = (24 * info0["n"] + 12 * info0["nnz"]) // info0["ncolours"]
+    lay0 = s_bco.level_layout(0)
+    if lay0["ndiag"]:       # per row: nd diagonals, 1/a_ii, slot -> row, f_i, x_i written, the other colour's x once
+        kbytes = info0["n"] * (8 * lay0["ndiag"] + 36) // info0["ncolours"]
+        kname = "k_gs_dia (Gauss-Seidel colour sweep, fine level, red/black, diagonal form, FP64)"
+    else:                   # per row / entry: SELL values + columns, 1/a_ii, f_i, x_i
+        kbytes = (24 * info0["n"] + 12 * info0["nnz"]) // info0["ncolours"]
+        kname = "k_gs (Gauss-Seidel colour sweep, fine level, red/black, SELL, FP64)"
     peak, peak_kind = peaks()
     k_avg = float(np.mean(kms))
     achieved = kbytes / (k_avg * 1e-3) / 1e9
@@ -296,15 +318,20 @@ def gpu_arm(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         sms.append(e0.elapsed_time(e1))
-    sbytes = a_pass_bytes(info0["n"], info0["nnz"])
-    spmv = dict(kernel="k_spmv (fine A, SELL-32, FP64)", bytes_per_launch=sbytes, avg_launch_ms=round(float(np.mean(sms)), 5),
+    if lay0["nat_ndiag"]:
+        sbytes = dia_pass_bytes(info0["n"], lay0["nat_ndiag"])
+        sname = "k_spmv_dia (fine A, natural order, diagonal form, FP64)"
+    else:
+        sbytes = a_pass_bytes(info0["n"], info0["nnz"])
+        sname = "k_spmv (fine A, SELL-32, FP64)"
+    spmv = dict(kernel=sname, bytes_per_launch=sbytes, avg_launch_ms=round(float(np.mean(sms)), 5),
                 achieved=round(sbytes / (np.mean(sms) * 1e-3) / 1e9, 1))
     bpi = bytes_per_iteration(s_bco, "bco")
     headline_ms = float(np.mean(ms))
     out.update(dict(p=p, arms=arms, clocks=clk, e2e_ms=e2e_ms, true_res=true_res, setups=setups,
                     roofline=dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
                                   frac=round(achieved / peak, 4), traffic=TRAFFIC_K_GS_FINE,
-                                  kernel="k_gs (Gauss-Seidel colour sweep, fine level, red/black, FP64)",
+                                  kernel=kname,
                                   bytes_per_launch=kbytes, avg_launch_ms=round(k_avg, 5), peak_kind=peak_kind,
                                   spmv=spmv),
                     headline_ms=headline_ms, bytes_per_iter=bpi, nodes=None, nlevels=s_bco.nlevels,

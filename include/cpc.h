@@ -205,6 +205,13 @@ int cpc_num_levels(const cpc_handle* h);
  * nnz(P_l), number of IC(0) levels (level 0 only, else 0). */
 int cpc_level_info(const cpc_handle* h, int32_t level, int64_t* info);
 
+/* Storage of the smoother's copy of A_l: info[0] = rows per chunk C, info[1] = number of stored
+ * diagonals (0 = SELL with column indices; 4, 6 or 8 = the diagonal form used when every
+ * off-diagonal entry lies on at most 8 offsets col - row, as on a structured grid), info[2] =
+ * slots (rows padded to chunks).  Level 0 reports the same for the natural-order copy of A in
+ * info[3..5].  Returns CPC_EINVAL for a bad level; the coarsest level reports zeros. */
+int cpc_level_layout(const cpc_handle* h, int32_t level, int64_t* info);
+
 /* Copy A_l (CSR, natural order) to host arrays sized from cpc_level_info. */
 int cpc_level_matrix(const cpc_handle* h, int32_t level, int32_t* rowptr, int32_t* colidx,
                      double* vals);

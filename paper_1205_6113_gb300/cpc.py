@@ -63,6 +63,7 @@ SIGNATURES = [
     ("cpc_solve_launches", _I32, [_P, _P, _P]),
     ("cpc_num_levels", _I32, [_P]),
     ("cpc_level_info", _I32, [_P, _I32, _P]),
+    ("cpc_level_layout", _I32, [_P, _I32, _P]),
     ("cpc_level_matrix", _I32, [_P, _I32, _P, _P, _P]),
     ("cpc_level_interp", _I32, [_P, _I32, _P, _P, _P]),
     ("cpc_level_splitting", _I32, [_P, _I32, _P, _P]),
@@ -190,6 +191,7 @@ class Solver:
         self.nnz = nnz
         self.precond = precond
         self.precision = precision
+        self.ic_order = ic_order
 
     def close(self):
         if getattr(self, "_h", None):
@@ -300,6 +302,14 @@ class Solver:
         _check(load().cpc_level_info(self._h, l, ctypes.c_void_p(info.ctypes.data)), self._h)
         return dict(n=int(info[0]), nnz=int(info[1]), ncolours=int(info[2]), nc=int(info[3]), nnzP=int(info[4]),
                     ic_levels=int(info[5]))
+
+    def level_layout(self, l):
+        """Smoother storage of A_l: chunk height, stored diagonals (0 = SELL), slots; level 0 also
+        the natural-order copy (nat_*)."""
+        info = np.zeros(6, np.int64)
+        _check(load().cpc_level_layout(self._h, l, ctypes.c_void_p(info.ctypes.data)), self._h)
+        return dict(C=int(info[0]), ndiag=int(info[1]), nslots=int(info[2]), nat_C=int(info[3]),
+                    nat_ndiag=int(info[4]), nat_nslots=int(info[5]))
 
     def level_matrix(self, l):
         i = self.level_info(l)

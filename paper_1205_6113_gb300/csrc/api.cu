@@ -209,6 +209,20 @@ int cpc_level_info(const cpc_handle* h, int32_t level, int64_t* info) {
     return CPC_OK;
 }
 
+int cpc_level_layout(const cpc_handle* h, int32_t level, int64_t* info) {
+    if (!h || !info || level < 0 || level >= (int)h->h.lev.size()) return CPC_EINVAL;
+    const cpc::Level& L = h->h.lev[level];
+    const bool last = level == (int)h->h.lev.size() - 1;
+    info[0] = last ? 0 : L.S.C;
+    info[1] = last ? 0 : L.S.ndiag;
+    info[2] = last ? 0 : L.S.nslots;
+    const cpc::Sell& A = h->h.Anat;
+    info[3] = level == 0 ? A.C : 0;
+    info[4] = level == 0 ? A.ndiag : 0;
+    info[5] = level == 0 ? A.nslots : 0;
+    return CPC_OK;
+}
+
 static int copy_csr_out(cpc_handle* hh, const cpc::Csr& A, int32_t* rowptr, int32_t* colidx, double* vals) {
     return guarded(hh, [&] {
         CPC_CK(cudaStreamSynchronize(hh->h.s));

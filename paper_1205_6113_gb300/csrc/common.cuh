@@ -87,6 +87,10 @@ struct Csr {
 // Value storage types of the preconditioner data.
 enum VType { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2 };
 
+struct DiaOff {
+    int o[8];
+};
+
 // SELL-C storage of a set of matrix rows in a chosen slot order (C in {32, 16, 8, 4}).
 //   slot s holds row perm[s] (or -1 for padding); chunk k = slots [Ck, Ck+C) is processed by one
 //   warp with G = 32/C lanes per row; entry w of the row in slot Ck + r lives at
@@ -105,6 +109,14 @@ struct Sell {
     DBuf<float> val32, diag32, dinv32; // FP32 copy (mixed precision)
     DBuf<__nv_bfloat16> val16;         // BF16 copy of off-diagonals (coarse levels, mode 2)
     std::vector<int> seg;
+    // Diagonal storage (structured grids): when every off-diagonal entry lies on one of ndiag <= 8
+    // offsets col - row (ascending, padded with 0), entry d of slot s is dval[d * nslots + s], 0 where
+    // the row has no such entry.  Kernels for this form read no column indices and no chunk
+    // pointers; the SELL arrays above are kept for the other kernels.
+    int ndiag = 0;
+    DiaOff doff{};
+    DBuf<double> dval;
+    DBuf<float> dval32;
 };
 
 }  // namespace cpc

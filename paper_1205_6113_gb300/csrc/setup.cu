@@ -772,6 +772,68 @@ void build_sell(const int* ptr, const int* col, const double* val, const DBuf<in
     CPC_LAUNCH_CK();
 }
 
+// Distinct off-diagonal offsets col - row of the rows, into a table of 8 (EMPTY = INT_MIN: no offset
+// can be INT_MIN); *over = 1 when there are more than 8.
+__global__ void k_dia_offsets(int n, const int* ptr, const int* col, int* table, int* over) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    volatile int* vt = table;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int j = col[p];
+        if (j == i) continue;
+        const int off = j - i;
+        bool found = false;
+        for (int t = 0; t < 8 && !found; ++t) {
+            int cur = vt[t];
+            if (cur == INT_MIN) cur = atomicCAS(table + t, INT_MIN, off);
+            found = cur == INT_MIN || cur == off;
+        }
+        if (!found) *over = 1;
+    }
+}
+
+// dval[d * nslots + s] = a_{i, i + off_d} for slot s = row i (0 where absent or padding).
+__global__ void k_dia_fill(int nslots, const int* perm, const int* ptr, const int* col, const double* val, int nd,
+                           DiaOff off, double* dval) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    const int i = perm[s];
+    for (int d = 0; d < nd; ++d) {
+        double v = 0.0;
+        if (i >= 0 && off.o[d] != 0)
+            for (int p = ptr[i]; p < ptr[i + 1]; ++p)
+                if (col[p] == i + off.o[d]) v = val[p];
+        dval[(size_t)d * nslots + s] = v;
+    }
+}
+
+// Adds the diagonal form to S (built from the same CSR rows, diagonal split) when the off-diagonal
+// entries lie on at most 8 offsets; ndiag is rounded up to 4, 6 or 8 with zero diagonals.
+void build_dia(int n, const int* ptr, const int* col, const double* val, Sell& S, cudaStream_t s) {
+    Tmp<int> table(8, s), over(1, s);
+    k_fill_int<<<1, 32, 0, s>>>(table.get(), 8, INT_MIN);
+    CPC_CK(cudaMemsetAsync(over.get(), 0, sizeof(int), s));
+    k_dia_offsets<<<nblk(n), TPB, 0, s>>>(n, ptr, col, table.get(), over.get());
+    CPC_LAUNCH_CK();
+    int t[8];
+    CPC_CK(cudaMemcpyAsync(t, table.get(), sizeof(t), cudaMemcpyDeviceToHost, s));
+    const int ov = d2h(over.get(), s);
+    if (ov) return;
+    std::vector<int> offs;
+    for (int q = 0; q < 8; ++q) if (t[q] != INT_MIN) offs.push_back(t[q]);
+    if (offs.empty()) return;
+    std::sort(offs.begin(), offs.end());
+    const int nd = offs.size() <= 4 ? 4 : (offs.size() <= 6 ? 6 : 8);
+    DiaOff o{};
+    for (int q = 0; q < nd; ++q) o.o[q] = q < (int)offs.size() ? offs[q] : 0;
+    // padding diagonals (offset 0, value 0) go last; the real ones stay in ascending column order
+    S.dval.alloc((size_t)nd * S.nslots);
+    k_dia_fill<<<nblk(S.nslots), TPB, 0, s>>>(S.nslots, S.perm.p, ptr, col, val, nd, o, S.dval.p);
+    CPC_LAUNCH_CK();
+    S.ndiag = nd;
+    S.doff = o;
+}
+
 __global__ void k_to_f32(int64_t n, const double* a, float* b) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -784,6 +846,11 @@ __global__ void k_to_bf16(int64_t n, const double* a, __nv_bfloat16* b) {
 
 void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
     if (vt == VT_F64) return;
+    if (S.ndiag) {
+        const int64_t m = (int64_t)S.ndiag * S.nslots;
+        S.dval32.alloc(m);
+        k_to_f32<<<nblk(m), TPB, 0, s>>>(m, S.dval.p, S.dval32.p);
+    }
     S.val32.alloc(S.nelem);
     k_to_f32<<<nblk(S.nelem), TPB, 0, s>>>(S.nelem, S.val.p, S.val32.p);
     if (S.diag.p) {
@@ -1382,6 +1449,8 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         natural_slots(h.n, CHUNK, s, slots, nslots, seg);
         build_sell(h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, slots, nslots, seg, CHUNK, SELL_OFFDIAG,
                    true, nullptr, h.Anat, s);
+        build_dia(h.n, h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, h.Anat, s);
+        if (nl > 1) build_dia(h.n, h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, h.lev[0].S, s);
         CPC_CK(cudaStreamSynchronize(s));
     }
     CPC_CK(cudaEventRecord(e2, s));

@@ -47,6 +47,16 @@ void with_u(int lanes, F&& f) {
     else f(std::integral_constant<int, 8>{});
 }
 
+// Calls f(std::integral_constant<int, ND>{}) with the padded diagonal count (4, 6 or 8).
+template <class F>
+void with_nd(int nd, F&& f) {
+    if (nd <= 4) f(std::integral_constant<int, 4>{});
+    else if (nd <= 6) f(std::integral_constant<int, 6>{});
+    else f(std::integral_constant<int, 8>{});
+}
+
+inline int slot_blocks(int64_t nslots) { return (int)std::max<int64_t>(1, (nslots + SELL_TPB - 1) / SELL_TPB); }
+
 inline int blocks_for_chunks(int nchunks) { return std::max(1, (nchunks + WPB - 1) / WPB); }
 inline int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + VEC_TPB - 1) / VEC_TPB, NPART)); }
 
@@ -59,6 +69,105 @@ template <class VT>
 __device__ __forceinline__ VT sub_sum(VT v, int C) {
     for (int o = C; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Diagonal form (structured grids, Sell::ndiag > 0): one thread per slot; the matrix values of a
+// slot are ND coalesced loads (no column indices, no chunk pointers), the gathers are x[i + off_d]
+// with the index clamped into range (the value is 0 wherever the row has no such entry).  The
+// products are added in ascending column order, as in the SELL kernels.
+// ---------------------------------------------------------------------------------------------
+template <class MT, class DT>
+struct DV {
+    int n, nslots;
+    const int* __restrict__ perm;      // nullptr: natural order, row = slot
+    const MT* __restrict__ val;        // [ND][nslots]
+    const DT* __restrict__ diag;
+    DiaOff off;
+};
+
+template <class MT, class DT>
+inline DV<MT, DT> dview(const Sell& S, int n, const MT* val, const DT* diag, bool natural) {
+    return DV<MT, DT>{n, S.nslots, natural ? nullptr : S.perm.p, val, diag, S.doff};
+}
+
+template <class MT, class DT>
+__device__ __forceinline__ int dia_row(const DV<MT, DT>& A, int s) {
+    return A.perm ? A.perm[s] : (s < A.n ? s : -1);
+}
+
+template <int ND, class VT, class MT, class DT>
+__device__ __forceinline__ void dia_load(const DV<MT, DT>& A, int s, VT (&v)[ND]) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) v[d] = Cv<VT>::f(A.val[(size_t)d * A.nslots + s]);
+}
+
+template <int ND, class VT, class XT>
+__device__ __forceinline__ VT dia_dot(const VT (&v)[ND], const DiaOff& off, int row, int n, const XT* x) {
+    VT xv[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        int j = row + off.o[d];
+        j = j < 0 ? 0 : (j >= n ? n - 1 : j);
+        xv[d] = Cv<VT>::f(x[j]);
+    }
+    VT acc = VT(0);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) acc += v[d] * xv[d];
+    return acc;
+}
+
+// Gauss-Seidel on slots [s0, s1) (one colour), diagonal form; A.diag holds 1 / a_ii.
+template <class MT, class DT, class FT, class VT, int ND>
+__global__ void __launch_bounds__(SELL_TPB) k_gs_dia(DV<MT, DT> A, int s0, int s1, const FT* __restrict__ f, VT* x) {
+    const int s = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= s1) return;
+    pdl_launch_dependents();
+    const int row = dia_row(A, s);
+    VT v[ND];
+    dia_load<ND, VT>(A, s, v);
+    const VT dinv = Cv<VT>::f(A.diag[s]);
+    pdl_wait();
+    if (row < 0) return;
+    const VT fr = Cv<VT>::f(f[row]);
+    const VT dot = dia_dot<ND, VT>(v, A.off, row, A.n, x);
+    x[row] = (fr - dot) * dinv;
+}
+
+// r = f - A x on slots [s0, s1), diagonal form.
+template <class MT, class DT, class FT, class XT, class RT, int ND>
+__global__ void __launch_bounds__(SELL_TPB) k_resid_dia(DV<MT, DT> A, int s0, int s1, const FT* __restrict__ f,
+                                                         const XT* __restrict__ x, RT* __restrict__ r) {
+    const int s = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= s1) return;
+    pdl_launch_dependents();
+    const int row = dia_row(A, s);
+    RT v[ND];
+    dia_load<ND, RT>(A, s, v);
+    const RT dg = Cv<RT>::f(A.diag[s]);
+    pdl_wait();
+    if (row < 0) return;
+    const RT fr = Cv<RT>::f(f[row]);
+    const RT dx = dg * Cv<RT>::f(x[row]);
+    const RT dot = dia_dot<ND, RT>(v, A.off, row, A.n, x);
+    r[row] = fr - (dx + dot);
+}
+
+// y = A x, diagonal form.
+template <class MT, class DT, class XT, class YT, int ND>
+__global__ void __launch_bounds__(SELL_TPB) k_spmv_dia(DV<MT, DT> A, const XT* __restrict__ x, YT* __restrict__ y) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= A.nslots) return;
+    pdl_launch_dependents();
+    const int row = dia_row(A, s);
+    YT v[ND];
+    dia_load<ND, YT>(A, s, v);
+    const YT dg = Cv<YT>::f(A.diag[s]);
+    pdl_wait();
+    if (row < 0) return;
+    const YT dx = dg * Cv<YT>::f(x[row]);
+    const YT dot = dia_dot<ND, YT>(v, A.off, row, A.n, x);
+    y[row] = dx + dot;
 }
 
 // Gauss-Seidel over the rows of one colour (chunks [c0, c1)): x_i = (f_i - sum_{j!=i} a_ij x_j) / a_ii,
@@ -307,6 +416,26 @@ __global__ void __launch_bounds__(SELL_TPB) k_bco_black(SV<MT, DT> A, int c0, in
     if (own) z[row] = zr + (fr - (dg * zr + dot)) * ui;
 }
 
+// k_bco_black in diagonal form: slots [s0, s1) of the fine colour 1.
+template <class MT, class DT, class VT, int ND>
+__global__ void __launch_bounds__(SELL_TPB) k_bco_black_dia(DV<MT, DT> A, int s0, int s1, const double* __restrict__ r,
+                                                             const VT* __restrict__ uinv, VT* __restrict__ z) {
+    const int s = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= s1) return;
+    pdl_launch_dependents();
+    const int row = dia_row(A, s);
+    VT v[ND];
+    dia_load<ND, VT>(A, s, v);
+    const VT dg = Cv<VT>::f(A.diag[s]);
+    pdl_wait();
+    if (row < 0) return;
+    const VT ui = uinv[row];
+    const VT fr = Cv<VT>::f(r[row]);
+    const VT zr = z[row];
+    const VT dot = dia_dot<ND, VT>(v, A.off, row, A.n, z);
+    z[row] = zr + (fr - (dg * zr + dot)) * ui;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Deterministic reductions: block tree, then the last block to finish sums the partials in order.
 // ---------------------------------------------------------------------------------------------
@@ -448,6 +577,32 @@ __global__ void __launch_bounds__(SELL_TPB) k_pcg_spmv(SV<double, double> A, int
     }
 }
 
+// k_pcg_spmv in diagonal form (grid-stride over the slots).
+template <int ND>
+__global__ void __launch_bounds__(SELL_TPB) k_pcg_spmv_dia(DV<double, double> A, const double* __restrict__ p,
+                                                            double* __restrict__ q, double* part, unsigned* ctr,
+                                                            PcgState* st) {
+    pdl_launch_dependents();
+    pdl_wait();
+    double v = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.nslots; s += gridDim.x * blockDim.x) {
+        const int row = dia_row(A, s);
+        if (row < 0) continue;
+        double w[ND];
+        dia_load<ND, double>(A, s, w);
+        const double pr = p[row];
+        const double acc = A.diag[s] * pr + dia_dot<ND, double>(w, A.off, row, A.n, p);
+        q[row] = acc;
+        v += pr * acc;
+    }
+    double tot;
+    if (finish_sum(v, part, ctr, &tot) && threadIdx.x == 0) {
+        st->pq = tot;
+        if (!(tot > 0.0) || !isfinite(tot)) { if (st->status == CPC_OK) st->status = CPC_EBREAKDOWN; }
+        st->alpha = st->status == CPC_OK ? st->rz / tot : 0.0;
+    }
+}
+
 // x += alpha p, r -= alpha q, ||r||; the last block updates the iteration count, the residual
 // history and the loop condition.
 __global__ void k_pcg_update(int n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
@@ -503,6 +658,19 @@ template <class FT, class VT>
 void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
     const int c0 = L.S.seg[c], c1 = L.S.seg[c + 1];
     if (c1 <= c0) return;
+    if (L.S.ndiag) {
+        const int s0 = c0 * L.S.C, s1 = c1 * L.S.C;
+        with_nd(L.S.ndiag, [&](auto nd) {
+            constexpr int ND = decltype(nd)::value;
+            if constexpr (std::is_same<VT, double>::value)
+                launch(k_gs_dia<double, double, FT, VT, ND>, slot_blocks(s1 - s0), SELL_TPB, s,
+                       dview(L.S, L.n, (const double*)L.S.dval.p, (const double*)L.S.dinv.p, false), s0, s1, f, x);
+            else
+                launch(k_gs_dia<float, float, FT, VT, ND>, slot_blocks(s1 - s0), SELL_TPB, s,
+                       dview(L.S, L.n, (const float*)L.S.dval32.p, (const float*)L.S.dinv32.p, false), s0, s1, f, x);
+        });
+        return;
+    }
     const int g = blocks_for_chunks(c1 - c0);
     with_u(L.S.lanes, [&](auto u) {
         constexpr int U = decltype(u)::value;
@@ -519,6 +687,20 @@ void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
 
 template <class FT, class VT>
 void rec_resid_level(Level& L, const FT* f, const VT* x, VT* r, cudaStream_t s) {
+    if (L.S.ndiag) {
+        with_nd(L.S.ndiag, [&](auto nd) {
+            constexpr int ND = decltype(nd)::value;
+            if constexpr (std::is_same<VT, double>::value)
+                launch(k_resid_dia<double, double, FT, VT, VT, ND>, slot_blocks(L.S.nslots), SELL_TPB, s,
+                       dview(L.S, L.n, (const double*)L.S.dval.p, (const double*)L.S.diag.p, false), 0, L.S.nslots,
+                       f, x, r);
+            else
+                launch(k_resid_dia<float, float, FT, VT, VT, ND>, slot_blocks(L.S.nslots), SELL_TPB, s,
+                       dview(L.S, L.n, (const float*)L.S.dval32.p, (const float*)L.S.diag32.p, false), 0, L.S.nslots,
+                       f, x, r);
+        });
+        return;
+    }
     const int g = blocks_for_chunks(L.S.nchunks);
     with_u(L.S.lanes, [&](auto u) {
         constexpr int U = decltype(u)::value;
@@ -630,6 +812,18 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
 template <class VT>
 void rec_fine_resid(Handle& h, const double* r, const VT* z, VT* t, cudaStream_t s) {
     const Sell& A = h.Anat;
+    if (A.ndiag) {
+        with_nd(A.ndiag, [&](auto nd) {
+            constexpr int ND = decltype(nd)::value;
+            if constexpr (std::is_same<VT, double>::value)
+                launch(k_resid_dia<double, double, double, VT, VT, ND>, slot_blocks(A.nslots), SELL_TPB, s,
+                       dview(A, h.n, (const double*)A.dval.p, (const double*)A.diag.p, true), 0, A.nslots, r, z, t);
+            else
+                launch(k_resid_dia<float, float, double, VT, VT, ND>, slot_blocks(A.nslots), SELL_TPB, s,
+                       dview(A, h.n, (const float*)A.dval32.p, (const float*)A.diag32.p, true), 0, A.nslots, r, z, t);
+        });
+        return;
+    }
     const int g = blocks_for_chunks(A.nchunks);
     with_u(A.lanes, [&](auto u) {
         constexpr int U = decltype(u)::value;
@@ -675,6 +869,21 @@ void rec_bco_black(Handle& h, const double* r, VT* z, cudaStream_t s) {
     const Sell& S = L0.S;
     const int c0 = S.seg[1], c1 = S.seg[2];
     if (c1 <= c0) return;
+    if (S.ndiag) {
+        const int s0 = c0 * S.C, s1 = c1 * S.C;
+        with_nd(S.ndiag, [&](auto nd) {
+            constexpr int ND = decltype(nd)::value;
+            if constexpr (std::is_same<VT, double>::value)
+                launch(k_bco_black_dia<double, double, double, ND>, slot_blocks(s1 - s0), SELL_TPB, s,
+                       dview(S, L0.n, (const double*)S.dval.p, (const double*)S.diag.p, false), s0, s1, r,
+                       (const double*)h.ic_uinv64.p, z);
+            else
+                launch(k_bco_black_dia<float, float, float, ND>, slot_blocks(s1 - s0), SELL_TPB, s,
+                       dview(S, L0.n, (const float*)S.dval32.p, (const float*)S.diag32.p, false), s0, s1, r,
+                       (const float*)h.ic_uinv32.p, z);
+        });
+        return;
+    }
     with_u(S.lanes, [&](auto u) {
         if constexpr (std::is_same<VT, double>::value)
             launch(k_bco_black<double, double, double, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB, s,
@@ -759,6 +968,14 @@ void apply_precond(Handle& h, int which, const double* r, double* z) {
 
 void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s) {
     const Sell& A = h.Anat;
+    if (A.ndiag) {
+        with_nd(A.ndiag, [&](auto nd) {
+            launch(k_spmv_dia<double, double, double, double, decltype(nd)::value>, slot_blocks(A.nslots), SELL_TPB, s,
+                   dview(A, h.n, (const double*)A.dval.p, (const double*)A.diag.p, true), x, y);
+        });
+        CPC_LAUNCH_CK();
+        return;
+    }
     with_u(A.lanes, [&](auto u) {
         launch(k_spmv<double, double, double, double, decltype(u)::value>, blocks_for_chunks(A.nchunks), SELL_TPB, s,
                view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, x, y);
@@ -860,11 +1077,19 @@ static void build_solve_graph(Handle& h, int which) {
         launch(k_pcg_rz<float>, vec_blocks(n), VEC_TPB, cs, n, (const double*)h.r.p, (const float*)h.z32.p, h.partial.p, h.counter.p, h.state.p);
         launch(k_pcg_p<float>, vec_blocks(n), VEC_TPB, cs, n, (const float*)h.z32.p, h.p.p, (const PcgState*)h.state.p);
     }
-    with_u(A.lanes, [&](auto u) {
-        launch(k_pcg_spmv<decltype(u)::value>, std::min(blocks_for_chunks(A.nchunks), NPART), SELL_TPB, cs,
-               view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, (const double*)h.p.p, h.q.p,
-               h.partial.p, h.counter.p, h.state.p);
-    });
+    if (A.ndiag) {
+        with_nd(A.ndiag, [&](auto nd) {
+            launch(k_pcg_spmv_dia<decltype(nd)::value>, std::min(slot_blocks(A.nslots), NPART), SELL_TPB, cs,
+                   dview(A, h.n, (const double*)A.dval.p, (const double*)A.diag.p, true), (const double*)h.p.p,
+                   h.q.p, h.partial.p, h.counter.p, h.state.p);
+        });
+    } else {
+        with_u(A.lanes, [&](auto u) {
+            launch(k_pcg_spmv<decltype(u)::value>, std::min(blocks_for_chunks(A.nchunks), NPART), SELL_TPB, cs,
+                   view(A, (const double*)A.val.p, (const double*)A.diag.p), A.nchunks, (const double*)h.p.p, h.q.p,
+                   h.partial.p, h.counter.p, h.state.p);
+        });
+    }
     launch(k_pcg_update, vec_blocks(n), VEC_TPB, cs, n, h.x.p, h.r.p, (const double*)h.p.p, (const double*)h.q.p,
            h.partial.p, h.counter.p, h.state.p, h.hist.p, (int)HIST_CAP, cond);
     CPC_CK(cudaStreamEndCapture(cs, &body));
