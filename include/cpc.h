@@ -76,9 +76,10 @@ typedef struct {
     double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
     int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (512)         */
     int32_t max_levels;     /* at most this many levels                            (20)          */
-    int64_t tail_nnz_max;   /* coarse levels run as one cluster kernel with their operators in
-                               shared memory when they fit and have at most this many nonzeros;
-                               0 = library default (capacity decides), < 0 = never               */
+    int64_t tail_nnz_max;   /* > 0: coarse levels run as one cluster kernel with their operators
+                               in shared memory when they fit and have at most this many
+                               nonzeros; 0 (default) or < 0: every level by separate launches,
+                               which measures faster on GB300                                     */
     void* stream;           /* cudaStream_t used by every call on the handle       (NULL)        */
 } cpc_options;
 

@@ -116,7 +116,6 @@ void solve_batched(Handle& h, int K, const double* b, double* x, double* lambda,
 void destroy_batched(Handle& h);
 
 // tail.cu
-constexpr int64_t TAIL_NNZ_MAX = int64_t(1) << 40;  // default: shared-memory capacity decides
 void setup_tail(Handle& h, int64_t tail_nnz_max);
 void record_tail(Handle& h, int level, const void* f0, void* x0, cudaStream_t s);
 

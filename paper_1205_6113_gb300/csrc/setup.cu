@@ -1530,7 +1530,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         h.z32.alloc(h.n); h.t32.alloc(h.n); h.y32.alloc(h.n);
     }
     setup_ic_rb(h, colour_ic, s);
-    setup_tail(h, h.opt.tail_nnz_max == 0 ? TAIL_NNZ_MAX : h.opt.tail_nnz_max);
+    setup_tail(h, h.opt.tail_nnz_max);
     // PCG and preconditioner vectors
     const size_t n = h.n;
     h.b.alloc(n); h.x.alloc(n); h.r.alloc(n); h.z.alloc(n); h.p.alloc(n); h.q.alloc(n);

@@ -117,6 +117,25 @@ def test_preconditioner_matches_oracle(case, which, op):
     assert rel(z, orc.apply(op, r)) < 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cluster_tail_matches_oracle(case, precision):
+    """The coarse end of the V-cycle as one cluster kernel (an option, off by default): same B_co
+    as the oracle, and fewer launches per iteration than the launch-per-step path."""
+    _, A, orc, s = case
+    t = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=64, precision=precision, tail_nnz_max=1 << 40)
+    assert t.solve_launches()[0] < s.solve_launches()[0]
+    r = inputs.random_vector(A.n, seed=17)
+    z = t.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    assert rel(z, orc.apply(O.BCO, r)) < (1e-11 if precision == "fp64" else 1e-5)
+    b = inputs.random_vector(A.n, seed=18)
+    x, it, st, _ = t.solve(torch.tensor(b, device=DEV), tol=1e-10, maxit=500)
+    ref = orc.pcg(b, op=O.BCO, tol=1e-10, maxit=500)
+    assert st == 0 and abs(it - ref["iters"]) <= 2
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= (1e-8 if precision == "fp64" else 1e-5) * np.linalg.norm(ref["x"])
+    t.close()
+
+
 @pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT),
                                       ("amg_ilu", O.AMG_ILU)])
 def test_pcg_matches_oracle(case, which, op):
