@@ -346,7 +346,8 @@ def batched_arm(rowptr, col, val, p, dev, stream, args, K=64):
     graph-captured batched solve, against the same 64 forward solves one at a time."""
     import torch
     from paper_1205_6113_gb300 import cpc
-    s = cpc.Solver(rowptr, col, val, precond="bco", precision="fp32", ic_order="colour")
+    s = cpc.Solver(rowptr, col, val, precond="bco", precision="fp32", ic_order="colour", autotune=True)
+    chunk = [s.level_layout(l)["C"] for l in range(s.nlevels - 1)]
     B = torch.tensor(np.ascontiguousarray(inputs.batch_rhs(p.n, K, seed=5).T), device=dev)
     X = torch.empty_like(B)
     Lam = torch.empty_like(B)
@@ -385,7 +386,8 @@ def batched_arm(rowptr, col, val, p, dev, stream, args, K=64):
                 batched_fwd_ms=round(fwd_batched_ms, 2), batched_fwd_solves_per_s=round(K / (fwd_batched_ms * 1e-3), 1),
                 sequential_fwd_ms=round(seq_ms, 2), sequential_solves_per_s=round(K / (seq_ms * 1e-3), 1),
                 iters_fwd=[int(itf.min()), int(itf.max())], iters_adj=[int(ita.min()), int(ita.max())],
-                iters_sequential=[int(min(fwd_only)), int(max(fwd_only))])
+                iters_sequential=[int(min(fwd_only)), int(max(fwd_only))],
+                chunk_height_autotuned=chunk)
 
 
 def adjoint_arm(dev, stream, tol=1e-8):

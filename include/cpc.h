@@ -76,6 +76,11 @@ typedef struct {
     double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
     int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (512)         */
     int32_t max_levels;     /* at most this many levels                            (20)          */
+    int32_t autotune;       /* 1: each coarse level's SELL chunk height C (and so its threads per
+                               row, 32 / C) is picked at setup by timing a Gauss-Seidel sweep of
+                               the candidates C/2, C, 2C around the row-length rule; 0: the rule
+                               alone.  Timing can pick differently from one setup to the next,
+                               which changes rounding (not the method).            (default 0)   */
     int64_t tail_nnz_max;   /* > 0: coarse levels run as one cluster kernel with their operators
                                in shared memory when they fit and have at most this many
                                nonzeros; 0 (default) or < 0: every level by separate launches,

@@ -36,6 +36,7 @@ class _Csr(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("ic_order", ctypes.c_int32),
                 ("theta", ctypes.c_double), ("coarse_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("autotune", ctypes.c_int32),
                 ("tail_nnz_max", ctypes.c_int64), ("stream", ctypes.c_void_p)]
 
 
@@ -159,7 +160,7 @@ class Solver:
     """
 
     def __init__(self, rowptr, col, val, precond="bco", precision="fp64", ic_order="natural", theta=0.25,
-                 coarse_max=512, max_levels=20, tail_nnz_max=0, stream=None):
+                 coarse_max=512, max_levels=20, tail_nnz_max=0, autotune=False, stream=None):
         torch = _torch()
         lib = load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -183,6 +184,7 @@ class Solver:
         opt.coarse_max = int(coarse_max)
         opt.max_levels = int(max_levels)
         opt.tail_nnz_max = int(tail_nnz_max)
+        opt.autotune = 1 if autotune else 0
         opt.stream = ctypes.c_void_p(self.stream.cuda_stream)
         h = ctypes.c_void_p()
         _check(lib.cpc_setup(ctypes.byref(csr), ctypes.byref(opt), ctypes.byref(h)))

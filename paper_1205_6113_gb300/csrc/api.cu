@@ -53,6 +53,7 @@ int cpc_default_options(cpc_options* opt) {
     opt->ic_order = 0;
     opt->theta = 0.25;
     opt->coarse_max = 512;
+    opt->autotune = 0;
     opt->max_levels = 20;
     opt->tail_nnz_max = 0;
     opt->stream = nullptr;
@@ -94,7 +95,7 @@ int cpc_setup(const cpc_csr* A, const cpc_options* opt, cpc_handle** out) {
     cpc_options o;
     if (opt) o = *opt; else cpc_default_options(&o);
     if (o.precond < 0 || o.precond > CPC_PRECOND_AMG_ILU || o.precision < 0 || o.precision > CPC_PREC_FP32_BF16 ||
-        o.ic_order < 0 || o.ic_order > 1 || !(o.theta > 0.0 && o.theta < 1.0) || o.coarse_max < 1 ||
+        o.ic_order < 0 || o.ic_order > 1 || !(o.theta > 0.0 && o.theta < 1.0) || o.coarse_max < 1 || o.autotune < 0 || o.autotune > 1 ||
         o.max_levels < 1) {
         g_setup_err = "invalid options";
         return CPC_EINVAL;

@@ -117,6 +117,9 @@ void destroy_batched(Handle& h);
 
 // tail.cu
 void setup_tail(Handle& h, int64_t tail_nnz_max);
+// Milliseconds of one forward Gauss-Seidel sweep over the colour groups of S (FP64, zero vectors),
+// replayed from a CUDA graph as in the solve: the cost the chunk-height autotuner compares.
+float time_gs_sweep(const Sell& S, int n);
 void record_tail(Handle& h, int level, const void* f0, void* x0, cudaStream_t s);
 
 // solve.cu

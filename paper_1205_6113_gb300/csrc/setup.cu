@@ -1087,15 +1087,36 @@ void setup_ic_rb(Handle& h, bool colour_ic, cudaStream_t s) {
     h.ic_rb = true;
 }
 
-void setup_level_sells(Level& L, cudaStream_t s, bool last) {
+// Chunk-height autotuning: with tune, the colour-grouped copy of A_l is also built with C/2 and 2C
+// (within 4..32) around the row-length rule, each is timed on a forward Gauss-Seidel sweep replayed
+// from a graph (time_gs_sweep), and a candidate replaces the rule's layout only when it is more
+// than 3% faster.  C sets the threads per row (32 / C) of every kernel on that copy.
+void setup_level_sells(Level& L, cudaStream_t s, bool last, bool tune) {
     // colour-grouped A_l (Gauss-Seidel and residual)
     if (!last) {
-        DBuf<int> slots;
-        int nslots = 0;
-        std::vector<int> seg;
+        auto build_grouped = [&](int C, Sell& out) {
+            DBuf<int> slots;
+            int nslots = 0;
+            std::vector<int> seg;
+            grouped_slots(L.n, L.colour.p, L.ncolours, C, s, slots, nslots, seg);
+            build_sell(L.A.ptr.p, L.A.col.p, L.A.val.p, slots, nslots, seg, C, SELL_OFFDIAG, true, nullptr, out, s);
+            CPC_CK(cudaStreamSynchronize(s));
+        };
         const int ca = choose_chunk((double)(L.A.nnz - L.n) / std::max(1, L.n));
-        grouped_slots(L.n, L.colour.p, L.ncolours, ca, s, slots, nslots, seg);
-        build_sell(L.A.ptr.p, L.A.col.p, L.A.val.p, slots, nslots, seg, ca, SELL_OFFDIAG, true, nullptr, L.S, s);
+        build_grouped(ca, L.S);
+        if (tune) {
+            float best = time_gs_sweep(L.S, L.n);
+            for (int C : {ca / 2, ca * 2}) {
+                if (C < 4 || C > 32) continue;
+                Sell cand;
+                build_grouped(C, cand);
+                const float t = time_gs_sweep(cand, L.n);
+                if (t < 0.97f * best) {
+                    best = t;
+                    L.S = std::move(cand);
+                }
+            }
+        }
         DBuf<int> ps;
         int pn = 0;
         std::vector<int> pseg;
@@ -1441,7 +1462,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         dense_chol_inverse(h.nc, M.get(), c0.get(), h.Ainv.p, f.get(), s);
         if (d2h(f.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
     }
-    for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1);
+    for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1, h.opt.autotune == 1 && l > 0);
     {   // fine A in natural order for the SpMVs
         DBuf<int> slots;
         int nslots = 0;

@@ -983,6 +983,52 @@ void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s) {
     CPC_LAUNCH_CK();
 }
 
+float time_gs_sweep(const Sell& S, int n) {
+    cudaStream_t cs;
+    CPC_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct SG { cudaStream_t s; ~SG() { cudaStreamSynchronize(s); cudaStreamDestroy(s); } } sg{cs};
+    DBuf<double> f, x;
+    f.alloc(n);
+    x.alloc(n);
+    CPC_CK(cudaMemsetAsync(f.p, 0, sizeof(double) * n, cs));
+    CPC_CK(cudaMemsetAsync(x.p, 0, sizeof(double) * n, cs));
+    CPC_CK(cudaStreamSynchronize(cs));
+    constexpr int SWEEPS = 4;
+    cudaGraph_t g;
+    CPC_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < SWEEPS; ++k)
+        for (size_t c = 0; c + 1 < S.seg.size(); ++c) {
+            const int c0 = S.seg[c], c1 = S.seg[c + 1];
+            if (c1 <= c0) continue;
+            with_u(S.lanes, [&](auto u) {
+                launch(k_gs<double, double, double, double, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB,
+                       cs, view(S, (const double*)S.val.p, (const double*)S.dinv.p), c0, c1, (const double*)f.p, x.p);
+            });
+        }
+    CPC_CK(cudaStreamEndCapture(cs, &g));
+    cudaGraphExec_t ge;
+    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CPC_CK(ie);
+    struct GE { cudaGraphExec_t g; ~GE() { cudaGraphExecDestroy(g); } } gg{ge};
+    cudaEvent_t e0, e1;
+    CPC_CK(cudaEventCreate(&e0));
+    CPC_CK(cudaEventCreate(&e1));
+    struct EV { cudaEvent_t a, b; ~EV() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
+    CPC_CK(cudaGraphLaunch(ge, cs));
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        CPC_CK(cudaEventRecord(e0, cs));
+        CPC_CK(cudaGraphLaunch(ge, cs));
+        CPC_CK(cudaEventRecord(e1, cs));
+        CPC_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CPC_CK(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms / SWEEPS);
+    }
+    return best;
+}
+
 void level_apply(Handle& h, int l, int op, const double* x, double* y) {
     const int nl = (int)h.lev.size();
     if (l < 0 || l >= nl) fail(CPC_EINVAL, "level out of range");

@@ -136,6 +136,19 @@ def test_cluster_tail_matches_oracle(case, precision):
     t.close()
 
 
+def test_autotuned_layout_matches_oracle(case):
+    """Chunk heights picked by timing (autotune) change the layout and the lanes per row, not the
+    method: B_co still equals the oracle's."""
+    _, A, orc, _ = case
+    t = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=64, autotune=True)
+    for l in range(t.nlevels - 1):
+        assert t.level_layout(l)["C"] in (4, 8, 16, 32)
+    r = inputs.random_vector(A.n, seed=19)
+    z = t.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    assert rel(z, orc.apply(O.BCO, r)) < 1e-11
+    t.close()
+
+
 @pytest.mark.parametrize("which,op", [("bco", O.BCO), ("amg", O.STILDE), ("ic0", O.B), ("bhat", O.BHAT),
                                       ("amg_ilu", O.AMG_ILU)])
 def test_pcg_matches_oracle(case, which, op):
