@@ -63,7 +63,8 @@ def lib():
         _lib.orc_nlevels.restype = i32
         _lib.orc_nlevels.argtypes = [P]
         for name in ("orc_level_sizes", "orc_level_A", "orc_level_P", "orc_level_cf_colour",
-                     "orc_ic0_values", "orc_level_apply", "orc_apply", "orc_pcg"):
+                     "orc_ic0_values", "orc_level_apply", "orc_apply", "orc_pcg", "orc_mhfem_size",
+                     "orc_mhfem"):
             getattr(_lib, name).restype = i32
         _lib.orc_level_sizes.argtypes = [P, i32, P]
         _lib.orc_level_A.argtypes = [P, i32, P, P, P]
@@ -72,6 +73,8 @@ def lib():
         _lib.orc_ic0_values.argtypes = [P, P]
         _lib.orc_level_apply.argtypes = [P, i32, i32, P, P]
         _lib.orc_apply.argtypes = [P, i32, P, P]
+        _lib.orc_mhfem_size.argtypes = [i32, i32, i32, P, f64, i32, P]
+        _lib.orc_mhfem.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
         _lib.orc_pcg.argtypes = [P, i32, P, P, f64, i32, P, P, P, P, i32, P]
     return _lib
 
@@ -126,6 +129,28 @@ def tpfa(nx, ny, nz, logk, kz_ratio, dirichlet) -> Csr:
     if st:
         raise ValueError("orc_tpfa failed: %d" % st)
     return Csr(n, rowptr, col, val)
+
+
+def mhfem(nx, ny, nz, logk, kz_ratio, dirichlet) -> Csr:
+    """The mixed-hybrid (p, lambda) system of Section 5, Eq. alge_sys, on unit bricks (oracle.cpp)."""
+    logk = _f64(logk)
+    sz = np.zeros(2, np.int32)
+    if lib().orc_mhfem_size(nx, ny, nz, _p(logk), float(kz_ratio), int(dirichlet), _p(sz)):
+        raise ValueError("bad grid")
+    n, nnz = int(sz[0]), int(sz[1])
+    ptr = np.zeros(n + 1, np.int32)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz, np.float64)
+    lib().orc_mhfem(nx, ny, nz, _p(logk), float(kz_ratio), int(dirichlet), _p(ptr), _p(col), _p(val))
+    return Csr(n, ptr, col, val)
+
+
+def mhfem_problem(prob):
+    """(A, b) of the mixed-hybrid system for a structured-grid problem: b = cell sources, 0 on faces."""
+    A = mhfem(prob.nx, prob.ny, prob.nz, prob.logk, prob.kz_ratio, prob.dirichlet)
+    b = np.zeros(A.n)
+    b[:prob.n] = prob.rhs()
+    return A, b
 
 
 def tpfa_gradient(nx, ny, nz, logk, kz_ratio, dirichlet, lam, p) -> np.ndarray:

@@ -21,6 +21,8 @@
  *                  finest-level smoother, AMG(ILU(0)) of Section 5.
  *   pcg            textbook preconditioned CG (the Krylov method the paper runs, Section 5).
  *   tpfa_gradient  -lambda^T (dA/dlog k) p, the adjoint gradient of a misfit through the assembly.
+ *   mhfem_assemble the mixed-hybrid system of Section 4 in the (pressure, multiplier) form of
+ *                  Section 5, Eq. alge_sys, for lowest-order Raviart-Thomas on unit bricks.
  *
  * Level numbering here is 0 = finest ... L-1 = coarsest (the paper numbers the other way).
  * Pins: tests/test_oracle_*.py.  Table 2 iteration counts: parity unpinned (the paper's
@@ -33,6 +35,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 namespace {
@@ -122,6 +125,98 @@ void tpfa_gradient(int nx, int ny, int nz, const double* logk, double kzr, int d
                 s += b * lam[c] * p[c];
                 g[c] = -s;
             }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Section 4 with the linear system of Section 5 (Eq. alge_sys): mixed-hybrid finite elements,
+// lowest-order Raviart-Thomas on unit bricks, fluxes eliminated, c = 0 (M = 0); unknowns are the
+// cell pressures and the face multipliers.  On a unit brick the RT0 mass matrix of a^{-1} is
+// block-diagonal per direction d with blocks (1/k_d) [[1/3, -1/6], [-1/6, 1/3]] (west/east,
+// south/north, bottom/top), so D_K^{-1} has blocks k_d [[4, 2], [2, 4]].  With div w_F = 1 per
+// face (unit outward flux) the element contributions are
+//   cell-cell  B D^{-1} B^T = sum_F 6 k_F,   cell-face  B D^{-1} C^T = -6 k_F,
+//   face-face  C D^{-1} C^T = 4 k_F on the diagonal and 2 k_F to the opposite face,
+// with k_F = k (x, y faces) or k_z = kz_ratio k (z faces).  Faces on Dirichlet sides (p = 0)
+// carry no unknown.  Unknown order: cells (i fastest), then the remaining x-faces, y-faces and
+// z-faces (i fastest within each).  Rows list columns in ascending order; a face diagonal sums its
+// cells in ascending cell order.  The right-hand side is the cell sources (f~1 = 0, f~2 = -f).
+// ---------------------------------------------------------------------------------------------
+struct MhfemIndex {
+    int nx, ny, nz, n, nfx, nfy, nfz;
+    vector<int> face_id;           // full face index -> unknown index (-1: Dirichlet)
+    int nunk = 0;
+    MhfemIndex(int nx_, int ny_, int nz_, int dmask) : nx(nx_), ny(ny_), nz(nz_) {
+        n = nx * ny * nz;
+        nfx = (nx + 1) * ny * nz;
+        nfy = nx * (ny + 1) * nz;
+        nfz = nx * ny * (nz + 1);
+        face_id.assign(nfx + nfy + nfz, -1);
+        int next = n;
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i <= nx; ++i)
+                    if (!((dmask & 1) && i == 0) && !((dmask & 2) && i == nx)) face_id[xf(i, j, k)] = next++;
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j <= ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    if (!((dmask & 4) && j == 0) && !((dmask & 8) && j == ny)) face_id[yf(i, j, k)] = next++;
+        for (int k = 0; k <= nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    if (!((dmask & 16) && k == 0) && !((dmask & 32) && k == nz)) face_id[zf(i, j, k)] = next++;
+        nunk = next;
+    }
+    int xf(int i, int j, int k) const { return (k * ny + j) * (nx + 1) + i; }
+    int yf(int i, int j, int k) const { return nfx + (k * (ny + 1) + j) * nx + i; }
+    int zf(int i, int j, int k) const { return nfx + nfy + (k * ny + j) * nx + i; }
+};
+
+Csr mhfem_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask) {
+    MhfemIndex X(nx, ny, nz, dmask);
+    const int n = X.n;
+    vector<vector<std::pair<int, double>>> rows(X.nunk);
+    for (int kk = 0; kk < nz; ++kk)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int c = i + nx * (j + ny * kk);
+                const double k = std::exp(logk[c]), kz = kzr * k;
+                const int f[6] = {X.face_id[X.xf(i, j, kk)], X.face_id[X.xf(i + 1, j, kk)],
+                                  X.face_id[X.yf(i, j, kk)], X.face_id[X.yf(i, j + 1, kk)],
+                                  X.face_id[X.zf(i, j, kk)], X.face_id[X.zf(i, j, kk + 1)]};
+                const double kf[6] = {k, k, k, k, kz, kz};
+                double cc = 0.0;
+                for (int q = 0; q < 6; ++q) cc += 6.0 * kf[q];
+                rows[c].push_back({c, cc});
+                for (int q = 0; q < 6; ++q) {
+                    if (f[q] < 0) continue;
+                    rows[c].push_back({f[q], -6.0 * kf[q]});
+                    rows[f[q]].push_back({c, -6.0 * kf[q]});
+                    rows[f[q]].push_back({f[q], 4.0 * kf[q]});
+                    const int o = f[q ^ 1];
+                    if (o >= 0) rows[f[q]].push_back({o, 2.0 * kf[q]});
+                }
+            }
+    Csr A;
+    A.n = A.m = X.nunk;
+    A.ptr.assign(X.nunk + 1, 0);
+    for (int r = 0; r < X.nunk; ++r) {
+        auto& e = rows[r];
+        // stable sort by column keeps the cell order of the contributions to one entry
+        std::stable_sort(e.begin(), e.end(), [](const std::pair<int, double>& a, const std::pair<int, double>& b) {
+            return a.first < b.first;
+        });
+        for (size_t q = 0; q < e.size();) {
+            double v = 0.0;
+            size_t t = q;
+            for (; t < e.size() && e[t].first == e[q].first; ++t) v += e[t].second;
+            A.col.push_back(e[q].first);
+            A.val.push_back(v);
+            q = t;
+        }
+        A.ptr[r + 1] = (int)A.col.size();
+    }
+    (void)n;
+    return A;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -734,6 +829,25 @@ int orc_tpfa(int nx, int ny, int nz, const double* logk, double kz_ratio, int dm
              int* rowptr, int* col, double* val) {
     if (nx < 1 || ny < 1 || nz < 1) return 1;
     Csr A = tpfa_assemble(nx, ny, nz, logk, kz_ratio, dmask);
+    std::memcpy(rowptr, A.ptr.data(), sizeof(int) * (A.n + 1));
+    std::memcpy(col, A.col.data(), sizeof(int) * A.nnz());
+    std::memcpy(val, A.val.data(), sizeof(double) * A.nnz());
+    return 0;
+}
+
+// MHFEM (p, lambda) system: sizes[0] = unknowns, sizes[1] = nonzeros.
+int orc_mhfem_size(int nx, int ny, int nz, const double* logk, double kz_ratio, int dmask, int* sizes) {
+    if (nx < 1 || ny < 1 || nz < 1) return 1;
+    Csr A = mhfem_assemble(nx, ny, nz, logk, kz_ratio, dmask);
+    sizes[0] = A.n;
+    sizes[1] = A.nnz();
+    return 0;
+}
+
+int orc_mhfem(int nx, int ny, int nz, const double* logk, double kz_ratio, int dmask, int* rowptr, int* col,
+              double* val) {
+    if (nx < 1 || ny < 1 || nz < 1) return 1;
+    Csr A = mhfem_assemble(nx, ny, nz, logk, kz_ratio, dmask);
     std::memcpy(rowptr, A.ptr.data(), sizeof(int) * (A.n + 1));
     std::memcpy(col, A.col.data(), sizeof(int) * A.nnz());
     std::memcpy(val, A.val.data(), sizeof(double) * A.nnz());

@@ -51,6 +51,46 @@ def small3d():
 
 
 # --------------------------------------------------------------------------------------------
+# Mixed-hybrid system (Section 4; Section 5, Eq. alge_sys), unit bricks
+# --------------------------------------------------------------------------------------------
+def test_mhfem_one_cell_matches_hand_derivation():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "mhfem_cell.txt")) if l.strip() and l[0] != "#"]
+    expect = np.zeros((6, 6))
+    for r, c, v in rows:
+        expect[int(r), int(c)] = float(v)
+    A = O.mhfem(1, 1, 1, np.zeros(1), 1.0, inputs.FACE_X0)
+    assert A.n == 6 and np.array_equal(A.to_dense(), expect)
+
+
+def test_mhfem_patch_test_1d():
+    """A column of unit cells, k = 1, p = 0 at x = 0, unit source in the last cell: the exact
+    pressure is p = x up to the last cell and a parabola inside it (p'(8) = 0).  The lowest-order
+    mixed method is exact here: face multipliers equal p at the x-faces, cell pressures equal the
+    cell averages of p (7 + 1/2 - 1/6 in the source cell), and the no-flow y/z faces of each cell
+    carry its pressure."""
+    nx = 8
+    p = inputs.Problem("column", nx, 1, 1, np.zeros(nx), 1.0, inputs.FACE_X0)
+    p.wells = [(nx - 1, 1.0)]
+    A, b = O.mhfem_problem(p)
+    x = np.linalg.solve(A.to_dense(), b)
+    cells, xf = x[:nx], x[nx:2 * nx]
+    assert np.allclose(cells, np.r_[np.arange(nx - 1) + 0.5, nx - 1 + 0.5 - 1.0 / 6.0], atol=1e-12)
+    assert np.allclose(xf, np.r_[np.arange(1, nx), nx - 0.5], atol=1e-12)
+    yz = x[2 * nx:].reshape(-1, nx)                       # y0, y1, z0, z1 faces, one per cell each
+    assert np.allclose(yz, cells[None, :], atol=1e-12)
+
+
+def test_mhfem_is_spd_with_positive_couplings():
+    p = inputs.small_3d(5, 4, 3, seed=31)
+    A = O.mhfem(p.nx, p.ny, p.nz, p.logk, p.kz_ratio, p.dirichlet)
+    D = A.to_dense()
+    assert np.array_equal(D, D.T)
+    assert np.linalg.eigvalsh(D).min() > 0
+    off = D - np.diag(np.diag(D))
+    assert (off > 0).any()                                # opposite faces: not an M-matrix
+
+
+# --------------------------------------------------------------------------------------------
 # TPFA assembly (Section 4, Eq. model with c = 0)
 # --------------------------------------------------------------------------------------------
 def test_tpfa_matches_hand_derived_2x2():
