@@ -35,9 +35,9 @@ MAXIT = 5000
 METRIC = "PCG ms to 1e-6 rel. residual (combined vs AMG/ILU alone, FP32 vs FP64 prec), %HBM peak"
 L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-level Gauss-Seidel launch from the
-# committed ncu capture (profiles/k_gs_dia_fine_correlated3d_128x128x64.md); None until a capture
+# committed ncu capture (profiles/k_gs_pk_fine_correlated3d_128x128x64.md); None until a capture
 # of the current kernel exists.
-TRAFFIC_K_GS_FINE = 48349184
+TRAFFIC_K_GS_FINE = 48355584
 
 
 def peaks():
@@ -301,7 +301,7 @@ def gpu_arm(args, rank, world):
     lay0 = s_bco.level_layout(0)
     if lay0["ndiag"]:       # per row: nd diagonals, 1/a_ii, slot -> row, f_i, x_i written, the other colour's x once
         kbytes = info0["n"] * (8 * lay0["ndiag"] + 36) // info0["ncolours"]
-        kname = "k_gs_dia (Gauss-Seidel colour sweep, fine level, red/black, diagonal form, FP64)"
+        kname = "k_gs_pk (Gauss-Seidel colour sweep, fine level, red/black, per-slot diagonal records, FP64)"
     else:                   # per row / entry: SELL values + columns, 1/a_ii, f_i, x_i
         kbytes = (24 * info0["n"] + 12 * info0["nnz"]) // info0["ncolours"]
         kname = "k_gs (Gauss-Seidel colour sweep, fine level, red/black, SELL, FP64)"

@@ -117,6 +117,10 @@ struct Sell {
     DiaOff doff{};
     DBuf<double> dval;
     DBuf<float> dval32;
+    // Gauss-Seidel copy of the diagonal form (colour-grouped fine level): per slot the ndiag values
+    // -a_ij / a_ii side by side, gval[s * ndiag + d], so that x_i = f_i / a_ii + sum_d g_d x_j.
+    DBuf<double> gval;
+    DBuf<float> gval32;
 };
 
 }  // namespace cpc

@@ -807,9 +807,16 @@ __global__ void k_dia_fill(int nslots, const int* perm, const int* ptr, const in
     }
 }
 
+// gval[s * nd + d] = -dval[d * nslots + s] / a_ii (times the stored reciprocal).
+__global__ void k_gval(int nslots, int nd, const double* dval, const double* dinv, double* gval) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    for (int d = 0; d < nd; ++d) gval[(size_t)s * nd + d] = -(dval[(size_t)d * nslots + s] * dinv[s]);
+}
+
 // Adds the diagonal form to S (built from the same CSR rows, diagonal split) when the off-diagonal
 // entries lie on at most 8 offsets; ndiag is rounded up to 4, 6 or 8 with zero diagonals.
-void build_dia(int n, const int* ptr, const int* col, const double* val, Sell& S, cudaStream_t s) {
+void build_dia(int n, const int* ptr, const int* col, const double* val, Sell& S, cudaStream_t s, bool gs = false) {
     Tmp<int> table(8, s), over(1, s);
     k_fill_int<<<1, 32, 0, s>>>(table.get(), 8, INT_MIN);
     CPC_CK(cudaMemsetAsync(over.get(), 0, sizeof(int), s));
@@ -832,6 +839,11 @@ void build_dia(int n, const int* ptr, const int* col, const double* val, Sell& S
     CPC_LAUNCH_CK();
     S.ndiag = nd;
     S.doff = o;
+    if (gs && S.dinv.p) {
+        S.gval.alloc((size_t)nd * S.nslots);
+        k_gval<<<nblk(S.nslots), TPB, 0, s>>>(S.nslots, nd, S.dval.p, S.dinv.p, S.gval.p);
+        CPC_LAUNCH_CK();
+    }
 }
 
 __global__ void k_to_f32(int64_t n, const double* a, float* b) {
@@ -850,6 +862,10 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
         const int64_t m = (int64_t)S.ndiag * S.nslots;
         S.dval32.alloc(m);
         k_to_f32<<<nblk(m), TPB, 0, s>>>(m, S.dval.p, S.dval32.p);
+        if (S.gval.p) {
+            S.gval32.alloc(m);
+            k_to_f32<<<nblk(m), TPB, 0, s>>>(m, S.gval.p, S.gval32.p);
+        }
     }
     S.val32.alloc(S.nelem);
     k_to_f32<<<nblk(S.nelem), TPB, 0, s>>>(S.nelem, S.val.p, S.val32.p);
@@ -1471,7 +1487,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         build_sell(h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, slots, nslots, seg, CHUNK, SELL_OFFDIAG,
                    true, nullptr, h.Anat, s);
         build_dia(h.n, h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, h.Anat, s);
-        if (nl > 1) build_dia(h.n, h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, h.lev[0].S, s);
+        if (nl > 1) build_dia(h.n, h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, h.lev[0].S, s, true);
         CPC_CK(cudaStreamSynchronize(s));
     }
     CPC_CK(cudaEventRecord(e2, s));
