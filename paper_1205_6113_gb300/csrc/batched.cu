@@ -57,6 +57,14 @@ void blaunch(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args&&...
 
 inline int rows_grid(int nrows) { return (nrows + BWARPS - 1) / BWARPS; }
 
+// Calls f(std::integral_constant<int, ND>{}) with the padded diagonal count (4, 6 or 8).
+template <class F>
+void bwith_nd(int nd, F&& f) {
+    if (nd <= 4) f(std::integral_constant<int, 4>{});
+    else if (nd <= 6) f(std::integral_constant<int, 6>{});
+    else f(std::integral_constant<int, 8>{});
+}
+
 // acc[j] += sum_w a_w x[col_w][lane + 32 j] over the entries of the row in slot s.  Padding entries
 // (col < 0) sit at the end of a row.  Four entries are loaded before their gathers.
 template <int J, class VT, class MT, class XT>
@@ -92,20 +100,21 @@ __device__ __forceinline__ void brow(const int* __restrict__ col, const MT* __re
 // Gauss-Seidel over the slots [s0, s1) of one colour, all columns.
 template <int J, class MT, class DT, class FT, class VT>
 __global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, const FT* __restrict__ f, VT* x, int Kp) {
-    pdl_launch_dependents();
-    pdl_wait();
     const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
     if (s >= s1) return;
+    pdl_launch_dependents();
     const int lane = threadIdx.x & 31;
-    const int row = A.perm[s];
-    if (row < 0) return;
+    const int row = A.perm[s];                   // matrix data: before the wait
     const int k = s / A.C, r = s % A.C;
     const int base = A.cptr[k];
+    const int width = (A.cptr[k + 1] - base) / A.C;
+    const VT dinv = Cv<VT>::f(A.diag[s]);        // the view's diagonal field holds 1 / a_ii
+    pdl_wait();
+    if (row < 0) return;
     VT acc[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = VT(0);
-    brow<J, VT>(A.col, A.val, A.C, base, (A.cptr[k + 1] - base) / A.C, r, x, Kp, lane, acc);
-    const VT dinv = Cv<VT>::f(A.diag[s]);        // the view's diagonal field holds 1 / a_ii
+    brow<J, VT>(A.col, A.val, A.C, base, width, r, x, Kp, lane, acc);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         const size_t o = (size_t)row * Kp + lane + 32 * j;
@@ -259,6 +268,174 @@ __global__ void __launch_bounds__(BTPB) kb_usolve(BV<MT, MT> U, int s0, int s1, 
         const VT v = (y[o] - acc[j]) * dinv;
         w[o] = v;
         if (zadd) zadd[o] += v;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Diagonal form (Sell::ndiag > 0, structured fine level): the gathered rows are x[i + off_d], so a
+// warp needs only its row index before it issues every gather, and the matrix values (one
+// broadcast load per diagonal) and 1 / a_ii are loaded before griddepcontrol.wait.  Products are
+// added in ascending column order, as in brow.
+// ---------------------------------------------------------------------------------------------
+template <class MT, class DT>
+struct BD {
+    int n, nslots;
+    const int* __restrict__ perm;      // nullptr: natural order
+    const MT* __restrict__ val;        // [ND][nslots]
+    const DT* __restrict__ diag;
+    DiaOff off;
+};
+
+template <class MT, class DT>
+BD<MT, DT> bdview(const Sell& S, int n, const MT* val, const DT* diag, bool natural) {
+    return BD<MT, DT>{n, S.nslots, natural ? nullptr : S.perm.p, val, diag, S.doff};
+}
+
+template <class MT, class DT>
+__device__ __forceinline__ int bd_row(const BD<MT, DT>& A, int s) {
+    return A.perm ? A.perm[s] : (s < A.n ? s : -1);
+}
+
+// acc[j] += sum_d v_d x[i + off_d][lane + 32 j] (all gathers issued before the products)
+template <int J, int ND, class VT, class XT>
+__device__ __forceinline__ void bd_dot(const VT (&v)[ND], const DiaOff& off, int row, int n, const XT* x, int Kp,
+                                       int lane, VT (&acc)[J]) {
+    VT xv[ND][J];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        int jr = row + off.o[d];
+        jr = jr < 0 ? 0 : (jr >= n ? n - 1 : jr);
+        const XT* xr = x + (size_t)jr * Kp + lane;
+#pragma unroll
+        for (int j = 0; j < J; ++j) xv[d][j] = Cv<VT>::f(xr[32 * j]);
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] += v[d] * xv[d][j];
+}
+
+template <int J, class MT, class DT, class FT, class VT, int ND>
+__global__ void __launch_bounds__(BTPB) kb_gs_dia(BD<MT, DT> A, int s0, int s1, const FT* __restrict__ f, VT* x, int Kp) {
+    const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
+    if (s >= s1) return;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31;
+    const int row = bd_row(A, s);
+    VT v[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) v[d] = Cv<VT>::f(A.val[(size_t)d * A.nslots + s]);
+    const VT dinv = Cv<VT>::f(A.diag[s]);        // 1 / a_ii
+    pdl_wait();
+    if (row < 0) return;
+    VT fr[J], acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        fr[j] = Cv<VT>::f(f[(size_t)row * Kp + lane + 32 * j]);
+        acc[j] = VT(0);
+    }
+    bd_dot<J, ND>(v, A.off, row, A.n, x, Kp, lane, acc);
+#pragma unroll
+    for (int j = 0; j < J; ++j) x[(size_t)row * Kp + lane + 32 * j] = (fr[j] - acc[j]) * dinv;
+}
+
+// out = f - A x, diagonal form (grid-stride over slots).
+template <int J, class MT, class DT, class FT, class XT, class RT, int ND>
+__global__ void __launch_bounds__(BTPB) kb_resid_dia(BD<MT, DT> A, const FT* __restrict__ f, const XT* __restrict__ x,
+                                                      RT* __restrict__ out, int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    for (int s = blockIdx.x * BWARPS + (threadIdx.x >> 5); s < A.nslots; s += gridDim.x * BWARPS) {
+        const int row = bd_row(A, s);
+        if (row < 0) continue;
+        RT v[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) v[d] = Cv<RT>::f(A.val[(size_t)d * A.nslots + s]);
+        const RT dg = Cv<RT>::f(A.diag[s]);
+        RT acc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = dg * Cv<RT>::f(x[(size_t)row * Kp + lane + 32 * j]);
+        bd_dot<J, ND>(v, A.off, row, A.n, x, Kp, lane, acc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)row * Kp + lane + 32 * j;
+            out[o] = Cv<RT>::f(f[o]) - acc[j];
+        }
+    }
+}
+
+// B_co step (2) with red-black IC(0), black rows only (see the single right-hand-side path):
+// z_b += (r_b - (A z)_b) / u_bb on the fine colour 1, diagonal form.
+template <int J, class MT, class DT, class VT, int ND>
+__global__ void __launch_bounds__(BTPB) kb_bco_black_dia(BD<MT, DT> A, int s0, int s1, const double* __restrict__ r,
+                                                          const VT* __restrict__ uinv, VT* __restrict__ z, int Kp) {
+    const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
+    if (s >= s1) return;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31;
+    const int row = bd_row(A, s);
+    VT v[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) v[d] = Cv<VT>::f(A.val[(size_t)d * A.nslots + s]);
+    const VT dg = Cv<VT>::f(A.diag[s]);
+    pdl_wait();
+    if (row < 0) return;
+    const VT ui = uinv[row];
+    VT zr[J], acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        zr[j] = z[(size_t)row * Kp + lane + 32 * j];
+        acc[j] = dg * zr[j];
+    }
+    bd_dot<J, ND>(v, A.off, row, A.n, z, Kp, lane, acc);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const size_t o = (size_t)row * Kp + lane + 32 * j;
+        z[o] = zr[j] + (Cv<VT>::f(r[o]) - acc[j]) * ui;
+    }
+}
+
+// First colour step of a sweep from a zero guess fused with the zero fill: x = f / a_ii on colour 0,
+// 0 elsewhere (colour-0 rows see only zeros).
+template <class FT, class VT>
+__global__ void kb_zero_first(int n, int Kp, const FT* __restrict__ f, const int* __restrict__ colour,
+                              const VT* __restrict__ dnat, VT* __restrict__ x) {
+    pdl_launch_dependents();
+    pdl_wait();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * Kp;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / Kp);
+        x[t] = colour[i] == 0 ? Cv<VT>::f(f[t]) * dnat[i] : VT(0);
+    }
+}
+
+// f_c = R r and the coarse level's first colour step from zero: x_c = f_c / a_ii on colour 0, 0 elsewhere.
+template <int J, class MT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_restrict_first(BV<MT, MT> M, int nslots, const VT* __restrict__ x,
+                                                           VT* __restrict__ y, VT* __restrict__ yx,
+                                                           const int* __restrict__ colour, const VT* __restrict__ dnat,
+                                                           int Kp) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    for (int s = blockIdx.x * BWARPS + (threadIdx.x >> 5); s < nslots; s += gridDim.x * BWARPS) {
+        const int row = M.perm[s];
+        if (row < 0) continue;
+        const int k = s / M.C, r = s % M.C;
+        const int base = M.cptr[k];
+        const bool c0 = colour[row] == 0;
+        const VT dr = dnat[row];
+        VT acc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = VT(0);
+        brow<J, VT>(M.col, M.val, M.C, base, (M.cptr[k + 1] - base) / M.C, r, x, Kp, lane, acc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)row * Kp + lane + 32 * j;
+            y[o] = acc[j];
+            yx[o] = c0 ? acc[j] * dr : VT(0);
+        }
     }
 }
 
@@ -429,6 +606,44 @@ __global__ void __launch_bounds__(BTPB) kb_spmv_pq(BV<double, double> A, int nsl
     });
 }
 
+template <int J, int ND>
+__global__ void __launch_bounds__(BTPB) kb_spmv_pq_dia(BD<double, double> A, int Kp, const double* __restrict__ p,
+                                                        double* __restrict__ q, double* part, unsigned* ctr, double* S) {
+    pdl_launch_dependents();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    double v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) v[j] = 0.0;
+    for (int s = blockIdx.x * BWARPS + (threadIdx.x >> 5); s < A.nslots; s += gridDim.x * BWARPS) {
+        const int row = bd_row(A, s);
+        if (row < 0) continue;
+        double w[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) w[d] = A.val[(size_t)d * A.nslots + s];
+        const double dg = A.diag[s];
+        double acc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = dg * p[(size_t)row * Kp + lane + 32 * j];
+        bd_dot<J, ND>(w, A.off, row, A.n, p, Kp, lane, acc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const size_t o = (size_t)row * Kp + lane + 32 * j;
+            q[o] = acc[j];
+            v[j] += p[o] * acc[j];
+        }
+    }
+    col_finish<J>(v, part, ctr, Kp, [&](int c, double t) {
+        const bool act = S[S_ACTIVE * Kp + c] > 0.0;
+        S[S_PQ * Kp + c] = t;
+        if (act && (!(t > 0.0) || !isfinite(t))) {
+            S[S_STATUS * Kp + c] = CPC_EBREAKDOWN;
+            S[S_ACTIVE * Kp + c] = 0.0;
+        }
+        S[S_ALPHA * Kp + c] = S[S_ACTIVE * Kp + c] > 0.0 ? S[S_RZ * Kp + c] / t : 0.0;
+    });
+}
+
 template <int J>
 __global__ void __launch_bounds__(BTPB) kb_update(int n, int Kp, double* __restrict__ x, double* __restrict__ r,
                                                    const double* __restrict__ p, const double* __restrict__ q,
@@ -509,6 +724,18 @@ void brec_gs(Level& L, int c, const FT* f, VT* x, int Kp, cudaStream_t s) {
     const int s0 = L.S.seg[c] * L.S.C, s1 = L.S.seg[c + 1] * L.S.C;
     if (s1 <= s0) return;
     const int g = rows_grid(s1 - s0);
+    if (L.S.ndiag) {
+        bwith_nd(L.S.ndiag, [&](auto nd) {
+            constexpr int ND = decltype(nd)::value;
+            if constexpr (std::is_same<VT, double>::value)
+                blaunch(kb_gs_dia<J, double, double, FT, VT, ND>, g, BTPB, s,
+                        bdview(L.S, L.n, (const double*)L.S.dval.p, (const double*)L.S.dinv.p, false), s0, s1, f, x, Kp);
+            else
+                blaunch(kb_gs_dia<J, float, float, FT, VT, ND>, g, BTPB, s,
+                        bdview(L.S, L.n, (const float*)L.S.dval32.p, (const float*)L.S.dinv32.p, false), s0, s1, f, x, Kp);
+        });
+        return;
+    }
     if constexpr (std::is_same<VT, double>::value)
         blaunch(kb_gs<J, double, double, FT, VT>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), s0, s1, f, x, Kp);
     else if (L.vt == VT_BF16)
@@ -520,6 +747,18 @@ void brec_gs(Level& L, int c, const FT* f, VT* x, int Kp, cudaStream_t s) {
 template <int J, class FT, class VT>
 void brec_resid(Level& L, const FT* f, const VT* x, VT* r, int Kp, cudaStream_t s) {
     const int g = std::min(rows_grid(L.S.nslots), 152 * 32);
+    if (L.S.ndiag) {
+        bwith_nd(L.S.ndiag, [&](auto nd) {
+            constexpr int ND = decltype(nd)::value;
+            if constexpr (std::is_same<VT, double>::value)
+                blaunch(kb_resid_dia<J, double, double, FT, VT, VT, ND>, g, BTPB, s,
+                        bdview(L.S, L.n, (const double*)L.S.dval.p, (const double*)L.S.diag.p, false), f, x, r, Kp);
+            else
+                blaunch(kb_resid_dia<J, float, float, FT, VT, VT, ND>, g, BTPB, s,
+                        bdview(L.S, L.n, (const float*)L.S.dval32.p, (const float*)L.S.diag32.p, false), f, x, r, Kp);
+        });
+        return;
+    }
     if constexpr (std::is_same<VT, double>::value)
         blaunch(kb_resid<J, double, double, FT, VT, VT>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.diag.p), L.S.nslots, f, x, r, Kp);
     else if (L.vt == VT_BF16)
@@ -534,8 +773,13 @@ BV<VT, VT> bfull(const Sell& S) {
     else return bview(S, (const float*)S.val32.p, (const float*)nullptr);
 }
 
+template <class VT> const VT* bdnat(const Level& L);
+template <> const double* bdnat<double>(const Level& L) { return L.dnat64.p; }
+template <> const float* bdnat<float>(const Level& L) { return L.dnat32.p; }
+
+// As rec_vcycle: with first_done the caller has applied the first colour step from the zero guess.
 template <int J, class FT, class VT>
-void brec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s) {
+void brec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStream_t s, bool first_done = false) {
     Batched& B = h.bat;
     const int Kp = B.Kp;
     const int nl = (int)h.lev.size();
@@ -545,12 +789,26 @@ void brec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStre
         blaunch(kb_coarse<J, VT, FT, VT>, rows_grid(L.n), BTPB, s, L.n, ai, f, x, Kp);
         return;
     }
-    if (zero_guess) blaunch(kb_zero<VT>, 1024, 256, s, (int64_t)L.n * Kp, x);
-    for (int c = 0; c < L.ncolours; ++c) brec_gs<J>(L, c, f, x, Kp, s);
+    int c0 = 0;
+    if (first_done) {
+        c0 = 1;
+    } else if (zero_guess) {
+        blaunch(kb_zero_first<FT, VT>, 2048, 256, s, L.n, Kp, f, (const int*)L.colour.p, bdnat<VT>(L), x);
+        c0 = 1;
+    }
+    for (int c = c0; c < L.ncolours; ++c) brec_gs<J>(L, c, f, x, Kp, s);
     brec_resid<J>(L, f, (const VT*)x, br<VT>(B, l), Kp, s);
-    blaunch(kb_apply<J, VT, VT>, std::min(rows_grid(L.SR.nslots), 152 * 32), BTPB, s, bfull<VT>(L.SR), L.SR.nslots,
-            (const VT*)br<VT>(B, l), bf<VT>(B, l + 1), bx<VT>(B, l + 1), Kp);
-    brec_vcycle<J, VT, VT>(h, l + 1, bf<VT>(B, l + 1), bx<VT>(B, l + 1), false, s);
+    Level& C = h.lev[l + 1];
+    if (l + 1 == nl - 1) {
+        blaunch(kb_apply<J, VT, VT>, std::min(rows_grid(L.SR.nslots), 152 * 32), BTPB, s, bfull<VT>(L.SR), L.SR.nslots,
+                (const VT*)br<VT>(B, l), bf<VT>(B, l + 1), bx<VT>(B, l + 1), Kp);
+        brec_vcycle<J, VT, VT>(h, l + 1, bf<VT>(B, l + 1), bx<VT>(B, l + 1), false, s);
+    } else {
+        blaunch(kb_restrict_first<J, VT, VT>, std::min(rows_grid(L.SR.nslots), 152 * 32), BTPB, s, bfull<VT>(L.SR),
+                L.SR.nslots, (const VT*)br<VT>(B, l), bf<VT>(B, l + 1), bx<VT>(B, l + 1), (const int*)C.colour.p,
+                bdnat<VT>(C), Kp);
+        brec_vcycle<J, VT, VT>(h, l + 1, bf<VT>(B, l + 1), bx<VT>(B, l + 1), true, s, true);
+    }
     blaunch(kb_prolong<J, VT, VT>, std::min(rows_grid(L.SP.nslots), 152 * 32), BTPB, s, bfull<VT>(L.SP), L.SP.nslots,
             (const VT*)bx<VT>(B, l + 1), x, Kp);
     for (int c = L.ncolours - 1; c >= 0; --c) brec_gs<J>(L, c, f, x, Kp, s);
@@ -586,6 +844,18 @@ void brec_precond(Handle& h, int which, const double* r, VT* z, cudaStream_t s) 
     const Sell& A = h.Anat;
     auto fine_resid = [&]() {
         const int g = std::min(rows_grid(A.nslots), 152 * 32);
+        if (A.ndiag) {
+            bwith_nd(A.ndiag, [&](auto nd) {
+                constexpr int ND = decltype(nd)::value;
+                if constexpr (std::is_same<VT, double>::value)
+                    blaunch(kb_resid_dia<J, double, double, double, VT, VT, ND>, g, BTPB, s,
+                            bdview(A, h.n, (const double*)A.dval.p, (const double*)A.diag.p, true), r, (const VT*)z, t, Kp);
+                else
+                    blaunch(kb_resid_dia<J, float, float, double, VT, VT, ND>, g, BTPB, s,
+                            bdview(A, h.n, (const float*)A.dval32.p, (const float*)A.diag32.p, true), r, (const VT*)z, t, Kp);
+            });
+            return;
+        }
         if constexpr (std::is_same<VT, double>::value)
             blaunch(kb_resid<J, double, double, double, VT, VT>, g, BTPB, s, bview(A, (const double*)A.val.p, (const double*)A.diag.p), A.nslots, r, (const VT*)z, t, Kp);
         else
@@ -594,8 +864,25 @@ void brec_precond(Handle& h, int which, const double* r, VT* z, cudaStream_t s) 
     switch (which) {
         case CPC_PRECOND_BCO:
             brec_vcycle<J, double, VT>(h, 0, r, z, true, s);
-            fine_resid();
-            brec_ic<J, VT, VT>(h, t, y, t, z, s);
+            if (h.ic_rb && h.lev[0].S.ndiag) {                   // step (2): black rows, one pass
+                const Sell& S0 = h.lev[0].S;
+                const int s0 = S0.seg[1] * S0.C, s1 = S0.seg[2] * S0.C;
+                if (s1 > s0)
+                    bwith_nd(S0.ndiag, [&](auto nd) {
+                        constexpr int ND = decltype(nd)::value;
+                        if constexpr (std::is_same<VT, double>::value)
+                            blaunch(kb_bco_black_dia<J, double, double, VT, ND>, rows_grid(s1 - s0), BTPB, s,
+                                    bdview(S0, h.n, (const double*)S0.dval.p, (const double*)S0.diag.p, false), s0, s1,
+                                    r, (const VT*)h.ic_uinv64.p, z, Kp);
+                        else
+                            blaunch(kb_bco_black_dia<J, float, float, VT, ND>, rows_grid(s1 - s0), BTPB, s,
+                                    bdview(S0, h.n, (const float*)S0.dval32.p, (const float*)S0.diag32.p, false), s0,
+                                    s1, r, (const VT*)h.ic_uinv32.p, z, Kp);
+                    });
+            } else {
+                fine_resid();
+                brec_ic<J, VT, VT>(h, t, y, t, z, s);
+            }
             brec_vcycle<J, double, VT>(h, 0, r, z, false, s);
             break;
         case CPC_PRECOND_AMG:
@@ -637,8 +924,15 @@ void brec_loop(Handle& h, cudaGraph_t g, cudaStream_t cs, cudaGraphNode_t* dep, 
     blaunch(kb_rz<J, VT>, vg, BTPB, cs, n, Kp, (const double*)B.r.p, (const VT*)z, B.partial.p, h.counter.p + 1, B.S.p);
     blaunch(kb_p<J, VT>, vg, BTPB, cs, n, Kp, (const VT*)z, B.p.p, (const double*)B.S.p);
     const Sell& A = h.Anat;
-    blaunch(kb_spmv_pq<J>, std::min(rows_grid(A.nslots), 152 * 8), BTPB, cs, bview(A, (const double*)A.val.p, (const double*)A.diag.p),
-            A.nslots, Kp, (const double*)B.p.p, B.q.p, B.partial.p, h.counter.p + 1, B.S.p);
+    if (A.ndiag)
+        bwith_nd(A.ndiag, [&](auto nd) {
+            blaunch(kb_spmv_pq_dia<J, decltype(nd)::value>, std::min(rows_grid(A.nslots), 152 * 8), BTPB, cs,
+                    bdview(A, n, (const double*)A.dval.p, (const double*)A.diag.p, true), Kp, (const double*)B.p.p,
+                    B.q.p, B.partial.p, h.counter.p + 1, B.S.p);
+        });
+    else
+        blaunch(kb_spmv_pq<J>, std::min(rows_grid(A.nslots), 152 * 8), BTPB, cs, bview(A, (const double*)A.val.p, (const double*)A.diag.p),
+                A.nslots, Kp, (const double*)B.p.p, B.q.p, B.partial.p, h.counter.p + 1, B.S.p);
     blaunch(kb_update<J>, vg, BTPB, cs, n, Kp, B.x.p, B.r.p, (const double*)B.p.p, (const double*)B.q.p, B.partial.p,
             h.counter.p + 1, B.S.p);
     blaunch(kb_any_active, 1, 32, cs, Kp, (const double*)B.S.p, cond);
