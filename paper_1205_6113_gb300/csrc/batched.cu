@@ -122,6 +122,42 @@ __global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, cons
     }
 }
 
+// Gauss-Seidel for long rows in small colour groups (coarse levels): one block of BWARPS warps per
+// row, warp w taking the entries w, w + BWARPS, ...; the warps' partial sums are added in warp
+// order through shared memory.  A step of a few thousand rows then costs a quarter of a row's
+// chain of dependent loads instead of a whole one.
+template <int J, class MT, class DT, class FT, class VT>
+__global__ void __launch_bounds__(BTPB) kb_gs_wide(BV<MT, DT> A, int s0, const FT* __restrict__ f, VT* x, int Kp) {
+    __shared__ VT part[BWARPS][32 * J];
+    const int s = s0 + blockIdx.x;
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = A.perm[s];
+    const int k = s / A.C, r = s % A.C;
+    const int base = A.cptr[k];
+    const int width = (A.cptr[k + 1] - base) / A.C;
+    const VT dinv = Cv<VT>::f(A.diag[s]);
+    pdl_wait();
+    if (row < 0) return;                         // uniform over the block
+    VT acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = VT(0);
+    // entries w, w + BWARPS, ...: a strided view of the row (base + w C, step BWARPS C)
+    const int mine = width > w ? (width - w + BWARPS - 1) / BWARPS : 0;
+    brow<J, VT>(A.col, A.val, A.C * BWARPS, base + w * A.C, mine, r, x, Kp, lane, acc);
+#pragma unroll
+    for (int j = 0; j < J; ++j) part[w][lane + 32 * j] = acc[j];
+    __syncthreads();
+    if (w != 0) return;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        VT t = part[0][lane + 32 * j];
+        for (int q = 1; q < BWARPS; ++q) t += part[q][lane + 32 * j];
+        const size_t o = (size_t)row * Kp + lane + 32 * j;
+        x[o] = (Cv<VT>::f(f[o]) - t) * dinv;
+    }
+}
+
 // out = f - A x (resid) over all slots; with DIAG the split diagonal is included.
 template <int J, class MT, class DT, class FT, class XT, class RT>
 __global__ void __launch_bounds__(BTPB) kb_resid(BV<MT, DT> A, int nslots, const FT* __restrict__ f,
@@ -734,6 +770,17 @@ void brec_gs(Level& L, int c, const FT* f, VT* x, int Kp, cudaStream_t s) {
                 blaunch(kb_gs_dia<J, float, float, FT, VT, ND>, g, BTPB, s,
                         bdview(L.S, L.n, (const float*)L.S.dval32.p, (const float*)L.S.dinv32.p, false), s0, s1, f, x, Kp);
         });
+        return;
+    }
+    // long rows in a small colour group: a block per row (kb_gs_wide), else a warp per row
+    const bool wide = L.A.nnz >= (int64_t)16 * L.n && (s1 - s0) <= 16384;
+    if (wide) {
+        if constexpr (std::is_same<VT, double>::value)
+            blaunch(kb_gs_wide<J, double, double, FT, VT>, s1 - s0, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), s0, f, x, Kp);
+        else if (L.vt == VT_BF16)
+            blaunch(kb_gs_wide<J, __nv_bfloat16, float, FT, VT>, s1 - s0, BTPB, s, bview(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), s0, f, x, Kp);
+        else
+            blaunch(kb_gs_wide<J, float, float, FT, VT>, s1 - s0, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), s0, f, x, Kp);
         return;
     }
     if constexpr (std::is_same<VT, double>::value)
