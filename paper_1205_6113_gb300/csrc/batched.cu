@@ -97,8 +97,32 @@ __device__ __forceinline__ void brow(const int* __restrict__ col, const MT* __re
     }
 }
 
+// brow with eight entries per batch (long rows): half the dependent rounds of brow.
+template <int J, class VT, class MT, class XT>
+__device__ __forceinline__ void brow8(const int* __restrict__ col, const MT* __restrict__ val, int C, int base,
+                                      int width, int r, const XT* x, int Kp, int lane, VT (&acc)[J]) {
+    int w = 0;
+    for (; w + 8 <= width; w += 8) {
+        int c[8];
+        VT a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            c[u] = col[base + (w + u) * C + r];
+            a[u] = Cv<VT>::f(val[base + (w + u) * C + r]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (c[u] < 0) continue;
+            const XT* xr = x + (size_t)c[u] * Kp + lane;
+#pragma unroll
+            for (int j = 0; j < J; ++j) acc[j] += a[u] * Cv<VT>::f(xr[32 * j]);
+        }
+    }
+    brow<J, VT>(col, val, C, base + w * C, width - w, r, x, Kp, lane, acc);
+}
+
 // Gauss-Seidel over the slots [s0, s1) of one colour, all columns.
-template <int J, class MT, class DT, class FT, class VT>
+template <int J, class MT, class DT, class FT, class VT, bool LONG = false>
 __global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, const FT* __restrict__ f, VT* x, int Kp) {
     const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
     if (s >= s1) return;
@@ -114,7 +138,8 @@ __global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, cons
     VT acc[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = VT(0);
-    brow<J, VT>(A.col, A.val, A.C, base, width, r, x, Kp, lane, acc);
+    if (LONG) brow8<J, VT>(A.col, A.val, A.C, base, width, r, x, Kp, lane, acc);
+    else brow<J, VT>(A.col, A.val, A.C, base, width, r, x, Kp, lane, acc);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         const size_t o = (size_t)row * Kp + lane + 32 * j;
@@ -783,12 +808,17 @@ void brec_gs(Level& L, int c, const FT* f, VT* x, int Kp, cudaStream_t s) {
             blaunch(kb_gs_wide<J, float, float, FT, VT>, s1 - s0, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), s0, f, x, Kp);
         return;
     }
-    if constexpr (std::is_same<VT, double>::value)
-        blaunch(kb_gs<J, double, double, FT, VT>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), s0, s1, f, x, Kp);
-    else if (L.vt == VT_BF16)
-        blaunch(kb_gs<J, __nv_bfloat16, float, FT, VT>, g, BTPB, s, bview(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), s0, s1, f, x, Kp);
-    else
-        blaunch(kb_gs<J, float, float, FT, VT>, g, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), s0, s1, f, x, Kp);
+    auto go = [&](auto longrows) {
+        constexpr bool LG = decltype(longrows)::value;
+        if constexpr (std::is_same<VT, double>::value)
+            blaunch(kb_gs<J, double, double, FT, VT, LG>, g, BTPB, s, bview(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), s0, s1, f, x, Kp);
+        else if (L.vt == VT_BF16)
+            blaunch(kb_gs<J, __nv_bfloat16, float, FT, VT, LG>, g, BTPB, s, bview(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), s0, s1, f, x, Kp);
+        else
+            blaunch(kb_gs<J, float, float, FT, VT, LG>, g, BTPB, s, bview(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), s0, s1, f, x, Kp);
+    };
+    if (L.A.nnz >= (int64_t)16 * L.n) go(std::true_type{});   // long rows: eight entries per batch
+    else go(std::false_type{});
 }
 
 template <int J, class FT, class VT>
