@@ -462,17 +462,24 @@ __device__ __forceinline__ bool jp_beats(int rj, int j, int ri, uint32_t hi) {
     return rj > ri || (rj == ri && fmix32((uint32_t)j ^ COLOUR_SEED) > hi);
 }
 
-__global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd, int* colour, int* done) {
+// blk[i]: the uncoloured neighbour of higher priority that stopped point i last time (-1: none);
+// while it stays uncoloured the point is skipped without scanning its row.
+__global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd, int* colour, int* blk, int* done) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     volatile int* vc = colour;
     if (vc[i] >= 0) return;
+    const int b = blk[i];
+    if (b >= 0 && vc[b] < 0) return;
     const int ri = rnd[i];
     const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
     const int p0 = ptr[i], p1 = ptr[i + 1];
     for (int p = p0; p < p1; ++p) {
         const int j = col[p];
-        if (j != i && jp_beats(rnd[j], j, ri, hi) && vc[j] < 0) return;
+        if (j != i && jp_beats(rnd[j], j, ri, hi) && vc[j] < 0) {
+            blk[i] = j;
+            return;
+        }
     }
     for (int base = 0;; base += 64) {
         unsigned long long used = 0ull;
@@ -492,28 +499,43 @@ __global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd
 
 // Breadth-first parity 2-colouring, propagated: every vertex adopts the smallest (root, parity^1)
 // offered by a neighbour; at the fixed point root = smallest index of the component and, for a
-// bipartite graph, parity = distance parity from it.  Jacobi-style rounds (old -> new arrays).
-__global__ void k_bip_round(int n, const int* ptr, const int* col, const int* root, const int* par,
-                            int* root2, int* par2, int* changed) {
+// bipartite graph, parity = distance parity from it (the only 2-colouring with the root at 0).
+// (root, parity) is one word, 2 root + parity, updated in place: roots only decrease and each
+// point writes only its own word, so a round may use values written in the same round (fewer
+// rounds) and still reaches that fixed point.
+__global__ void k_bip_init(int n, unsigned* w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = (unsigned)i << 1;
+}
+
+__global__ void k_bip_round(int n, const int* ptr, const int* col, unsigned* w, int* changed) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int r = root[i], q = par[i];
+    volatile unsigned* vw = w;
+    const unsigned v = vw[i];
+    unsigned best = v;
     for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
         const int j = col[p];
         if (j == i) continue;
-        const int rj = root[j];
-        if (rj < r) { r = rj; q = par[j] ^ 1; }
+        const unsigned vj = vw[j];
+        if ((vj >> 1) < (best >> 1)) best = vj ^ 1u;
     }
-    root2[i] = r;
-    par2[i] = q;
-    if (r != root[i]) atomicAdd(changed, 1);
+    if ((best >> 1) != (v >> 1)) {
+        vw[i] = best;
+        atomicAdd(changed, 1);
+    }
 }
 
-__global__ void k_bip_check(int n, const int* ptr, const int* col, const int* par, int* bad) {
+__global__ void k_bip_unpack(int n, const unsigned* w, int* colour) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) colour[i] = (int)(w[i] & 1u);
+}
+
+__global__ void k_bip_check(int n, const int* ptr, const int* col, const unsigned* w, int* bad) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int p = ptr[i]; p < ptr[i + 1]; ++p)
-        if (col[p] != i && par[col[p]] == par[i]) { atomicOr(bad, 1); return; }
+        if (col[p] != i && ((w[col[p]] ^ w[i]) & 1u) == 0u) { atomicOr(bad, 1); return; }
 }
 
 // ============================================================================================
@@ -884,59 +906,96 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 
 // ============================================================================================
 // Coarsest level: dense Cholesky A_c = L L^T and the explicit inverse (Algorithm 3.2, step 2(b)).
-// Right-looking factorisation, one launch per column j over all SMs; then one warp per column of
-// A_c^{-1} = L^{-T} L^{-1}.
+// Blocked right-looking factorisation with panels of NB = 32 columns:
+//   k_chol_diag   factor the 32 x 32 diagonal block in shared memory (one block),
+//   k_chol_trsm   L21 = A21 L11^{-T}, one thread per row below the block,
+//   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, one 32 x 32 tile per block;
+// then one warp per column of A_c^{-1} = L^{-T} L^{-1}.  L is left in the lower triangle of M.
 // ============================================================================================
-__global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const double* val, double* M, double* c0) {
+constexpr int CHOL_NB = 32;
+
+__global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const double* val, double* M) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
-        M[(size_t)i * n + col[p]] = val[p];
-        if (col[p] == 0) c0[i] = val[p];
-    }
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) M[(size_t)i * n + col[p]] = val[p];
 }
 
-// Step j.  cj = column j of the current trailing matrix (contiguous copy, rows >= j); l_jj = sqrt(a_jj),
-// l_ij = a_ij / l_jj.  One warp per row i > j updates a_ik -= l_ij l_kj for j < k <= i and writes the
-// updated a_{i,j+1} into cn, the copy of column j + 1 for the next step.  Column j of M keeps the
-// unscaled a_ij; k_chol_finish scales it.
-__global__ void k_chol_step(int n, int j, double* __restrict__ M, const double* __restrict__ cj,
-                            double* __restrict__ cn, double* __restrict__ Ld, int* fail) {
-    if (*(volatile int*)fail) return;
-    const double d = cj[j];
-    if (!(d > 0.0) || !isfinite(d)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) *fail = 1;
+__global__ void __launch_bounds__(CHOL_NB * CHOL_NB) k_chol_diag(int n, int jb, double* M, int* fail) {
+    __shared__ double D[CHOL_NB][CHOL_NB + 1];
+    __shared__ int bad;
+    const int nb = min(CHOL_NB, n - jb);
+    const int r = threadIdx.x / CHOL_NB, c = threadIdx.x % CHOL_NB;
+    if (threadIdx.x == 0) bad = *(volatile int*)fail;
+    if (r < nb && c <= r) D[r][c] = M[(size_t)(jb + r) * n + jb + c];
+    __syncthreads();
+    if (bad) return;
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = D[j][j];
+            if (!(d > 0.0) || !isfinite(d)) bad = 1;
+            else D[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        if (c == j && r > j && r < nb) D[r][j] /= D[j][j];
+        __syncthreads();
+        if (r > j && r < nb && c > j && c <= r) D[r][c] -= D[r][j] * D[c][j];
+        __syncthreads();
+    }
+    if (bad) {
+        if (threadIdx.x == 0) *fail = 1;
         return;
     }
-    const double s = sqrt(d);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        Ld[j] = s;
-        if (j + 1 < n) cn[j + 1] = M[(size_t)(j + 1) * n + j + 1] - (cj[j + 1] / s) * (cj[j + 1] / s);
+    if (r < nb && c <= r) M[(size_t)(jb + r) * n + jb + c] = D[r][c];
+}
+
+// Rows i >= jb + nb of the panel: l_i = a_i L11^{-T} by forward substitution (one thread per row).
+__global__ void k_chol_trsm(int n, int jb, double* M, const int* fail) {
+    __shared__ double L11[CHOL_NB][CHOL_NB + 1];
+    const int nb = min(CHOL_NB, n - jb);
+    for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += blockDim.x) {
+        const int r = t / CHOL_NB, c = t % CHOL_NB;
+        L11[r][c] = (r < nb && c <= r) ? M[(size_t)(jb + r) * n + jb + c] : 0.0;
     }
-    const int i = j + 2 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+    __syncthreads();
+    if (*(volatile int*)fail) return;
+    const int i = jb + nb + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double lij = cj[i] / s;
-    double* row = M + (size_t)i * n;
-    for (int k = j + 1 + lane; k <= i; k += 32) {
-        const double v = row[k] - lij * (cj[k] / s);
-        row[k] = v;
-        if (k == j + 1) cn[i] = v;
+    double* row = M + (size_t)i * n + jb;
+    for (int k = 0; k < nb; ++k) {
+        double acc = row[k];
+        for (int m = 0; m < k; ++m) acc -= row[m] * L11[k][m];
+        row[k] = acc / L11[k][k];
     }
 }
 
-// L into the lower triangle (diagonal included) and L^T into the strict upper triangle.
-__global__ void k_chol_finish(int n, double* __restrict__ M, const double* __restrict__ Ld) {
+// Trailing update of the lower triangle: a_ik -= sum_m l_im l_km over the panel columns, for
+// jb + nb <= k <= i; block (bi, bk) with bk <= bi covers a 32 x 32 tile.
+__global__ void __launch_bounds__(CHOL_NB * CHOL_NB) k_chol_syrk(int n, int jb, double* M, const int* fail) {
+    __shared__ double Li[CHOL_NB][CHOL_NB + 1], Lk[CHOL_NB][CHOL_NB + 1];
+    if (*(volatile int*)fail) return;
+    const int nb = min(CHOL_NB, n - jb);
+    const int t0 = jb + nb;
+    const int bi = blockIdx.y, bk = blockIdx.x;
+    if (bk > bi) return;
+    const int r = threadIdx.x / CHOL_NB, c = threadIdx.x % CHOL_NB;
+    const int i0 = t0 + bi * CHOL_NB, k0 = t0 + bk * CHOL_NB;
+    Li[r][c] = (i0 + r < n && c < nb) ? M[(size_t)(i0 + r) * n + jb + c] : 0.0;
+    Lk[r][c] = (k0 + r < n && c < nb) ? M[(size_t)(k0 + r) * n + jb + c] : 0.0;
+    __syncthreads();
+    const int i = i0 + r, k = k0 + c;
+    if (i >= n || k > i) return;
+    double acc = 0.0;
+    for (int m = 0; m < nb; ++m) acc += Li[r][m] * Lk[c][m];
+    M[(size_t)i * n + k] -= acc;
+}
+
+// L^T into the strict upper triangle (the lower triangle and the diagonal hold L).
+__global__ void k_chol_mirror(int n, double* __restrict__ M) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * n) return;
     const int i = (int)(t / n), k = (int)(t % n);
-    if (k < i) {
-        const double l = M[t] / Ld[k];
-        M[t] = l;
-        M[(size_t)k * n + i] = l;
-    } else if (k == i) {
-        M[t] = Ld[i];
-    }
+    if (k < i) M[(size_t)k * n + i] = M[t];
 }
 
 // Column c of A^{-1} (stored as row c; A^{-1} is symmetric): L y = e_c, then L^T x = y, in place.
@@ -964,14 +1023,18 @@ __global__ void k_chol_inverse(int n, const double* __restrict__ L, double* __re
     }
 }
 
-void dense_chol_inverse(int n, double* M, double* c0, double* Ainv, int* fail, cudaStream_t s) {
-    Tmp<double> c1(n, s), Ld(n, s);
-    double* col[2] = {c0, c1.get()};
-    for (int j = 0; j < n; ++j) {
-        const int rows = std::max(n - j - 2, 1);
-        k_chol_step<<<(rows + 7) / 8, 256, 0, s>>>(n, j, M, col[j & 1], col[(j + 1) & 1], Ld.get(), fail);
+void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t s) {
+    for (int jb = 0; jb < n; jb += CHOL_NB) {
+        const int nb = std::min(CHOL_NB, n - jb);
+        k_chol_diag<<<1, CHOL_NB * CHOL_NB, 0, s>>>(n, jb, M, fail);
+        const int below = n - jb - nb;
+        if (below > 0) {
+            k_chol_trsm<<<(below + 127) / 128, 128, 0, s>>>(n, jb, M, fail);
+            const int tiles = (below + CHOL_NB - 1) / CHOL_NB;
+            k_chol_syrk<<<dim3(tiles, tiles), CHOL_NB * CHOL_NB, 0, s>>>(n, jb, M, fail);
+        }
     }
-    k_chol_finish<<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, M, Ld.get());
+    k_chol_mirror<<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, M);
     k_chol_inverse<<<(n + 7) / 8, 256, 0, s>>>(n, M, Ainv);
     CPC_LAUNCH_CK();
 }
@@ -1174,8 +1237,9 @@ __global__ void k_tri_probe(int n, const int* ptr, const int* col, int* found) {
 
 // Smoothing colours of levels [0, nl - 1): the breadth-first parity 2-colouring if the pattern
 // graph is bipartite, else Jones-Plassmann with peel-round priority.  Every level is a small state
-// machine of round loops on its own stream; all levels advance one batch of launches at a time and
-// then read their counters, so the setup waits for the longest chain of rounds, not their sum.
+// machine of round loops on its own stream; all levels advance one batch of launches at a time
+// (16 peel rounds, 32 Jones-Plassmann rounds: rounds after completion change nothing) and then read
+// their counters, so the setup waits for the longest chain of rounds, not their sum.
 struct ColourJob {
     enum Phase { TRI, BIP, BIP_CHECK, PEEL, JP, MAX, DONE };
     int l = 0, n = 0, phase = TRI, rounds = 0;
@@ -1230,9 +1294,8 @@ void colour_levels(Handle& h, cudaStream_t s) {
         J.phase = phase;
         J.rounds = 0;
         if (phase == ColourJob::BIP) {
-            J.a0 = mk(n, q); J.a1 = mk(n, q); J.a2 = mk(n, q); J.a3 = mk(n, q);
-            k_iota<<<nblk(n), TPB, 0, q>>>(J.a0->get(), n);
-            CPC_CK(cudaMemsetAsync(J.a2->get(), 0, sizeof(int) * n, q));
+            J.a0 = mk(n, q);                                     // (root, parity) words
+            k_bip_init<<<nblk(n), TPB, 0, q>>>(n, (unsigned*)J.a0->get());
         } else if (phase == ColourJob::PEEL) {
             J.a0 = mk(n, q);                                     // degrees
             J.rnd = mk(n, q);
@@ -1241,6 +1304,8 @@ void colour_levels(Handle& h, cudaStream_t s) {
             k_fill_int<<<1, 32, 0, q>>>(J.cnt->get(), 1, n);     // points left
             k_peel_init<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(), J.dmin->get());
         } else if (phase == ColourJob::JP) {
+            J.a1 = mk(n, q);                                     // blocking neighbour per point
+            k_fill_int<<<nblk(n), TPB, 0, q>>>(J.a1->get(), n, -1);
             k_fill_int<<<nblk(n), TPB, 0, q>>>(L.colour.p, n, -1);
             CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));   // points coloured
         }
@@ -1259,20 +1324,18 @@ void colour_levels(Handle& h, cudaStream_t s) {
                     break;
                 case ColourJob::BIP:
                     CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
-                    for (int k = 0; k < 16; ++k) {
-                        k_bip_round<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.a2->get(),
-                                                            J.a1->get(), J.a3->get(), J.cnt->get());
-                        std::swap(J.a0, J.a1);
-                        std::swap(J.a2, J.a3);
-                    }
+                    for (int k = 0; k < 16; ++k)
+                        k_bip_round<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, (unsigned*)J.a0->get(),
+                                                            J.cnt->get());
                     J.rounds += 16;
                     break;
                 case ColourJob::BIP_CHECK:
                     CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
-                    k_bip_check<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a2->get(), J.cnt->get());
+                    k_bip_check<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, (const unsigned*)J.a0->get(),
+                                                        J.cnt->get());
                     break;
                 case ColourJob::PEEL:
-                    for (int k = 0; k < 8; ++k, ++J.rounds) {
+                    for (int k = 0; k < 16; ++k, ++J.rounds) {
                         k_peel_mark<<<nblk(n), TPB, 0, q>>>(n, J.a0->get(), J.rnd->get(), J.dmin->get(), J.rounds,
                                                             J.cnt->get());
                         k_peel_update<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(),
@@ -1280,10 +1343,10 @@ void colour_levels(Handle& h, cudaStream_t s) {
                     }
                     break;
                 case ColourJob::JP:
-                    for (int k = 0; k < 8; ++k)
+                    for (int k = 0; k < 32; ++k)
                         k_jp_round<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.rnd->get(), L.colour.p,
-                                                           J.cnt->get());
-                    J.rounds += 8;
+                                                           J.a1->get(), J.cnt->get());
+                    J.rounds += 32;
                     break;
                 case ColourJob::MAX:
                     CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
@@ -1308,8 +1371,7 @@ void colour_levels(Handle& h, cudaStream_t s) {
                     break;
                 case ColourJob::BIP_CHECK:
                     if (v == 0) {
-                        CPC_CK(cudaMemcpyAsync(L.colour.p, J.a2->get(), sizeof(int) * J.n, cudaMemcpyDeviceToDevice,
-                                               J.st));
+                        k_bip_unpack<<<nblk(J.n), TPB, 0, J.st>>>(J.n, (const unsigned*)J.a0->get(), L.colour.p);
                         enter(J, ColourJob::MAX);
                     } else {
                         enter(J, ColourJob::PEEL);
@@ -1317,11 +1379,11 @@ void colour_levels(Handle& h, cudaStream_t s) {
                     break;
                 case ColourJob::PEEL:
                     if (v == 0) enter(J, ColourJob::JP);
-                    else if (J.rounds > J.n + 8) fail(CPC_ESETUP, "peel rounds did not terminate");
+                    else if (J.rounds > J.n + 16) fail(CPC_ESETUP, "peel rounds did not terminate");
                     break;
                 case ColourJob::JP:
                     if (v == J.n) enter(J, ColourJob::MAX);
-                    else if (J.rounds > J.n + 8) fail(CPC_ESETUP, "colouring did not terminate");
+                    else if (J.rounds > J.n + 32) fail(CPC_ESETUP, "colouring did not terminate");
                     break;
                 case ColourJob::MAX:
                     L.ncolours = v + 1;
@@ -1469,13 +1531,11 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         if (h.nc > DENSE_MAX) fail(CPC_ESETUP, "coarsest level too large for the dense solve");
         Tmp<double> M((size_t)h.nc * h.nc, s);
         CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s));
-        Tmp<double> c0(h.nc, s);
-        CPC_CK(cudaMemsetAsync(c0.get(), 0, sizeof(double) * h.nc, s));
-        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get(), c0.get());
+        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
         h.Ainv.alloc((size_t)h.nc * h.nc);
         Tmp<int> f(1, s);
         CPC_CK(cudaMemsetAsync(f.get(), 0, sizeof(int), s));
-        dense_chol_inverse(h.nc, M.get(), c0.get(), h.Ainv.p, f.get(), s);
+        dense_chol_inverse(h.nc, M.get(), h.Ainv.p, f.get(), s);
         if (d2h(f.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
     }
     for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1, h.opt.autotune == 1 && l > 0);
