@@ -136,6 +136,26 @@ def test_cluster_tail_matches_oracle(case, precision):
     t.close()
 
 
+def test_blocked_cholesky_on_a_large_coarsest_level():
+    """A coarsest level of 504 rows: the dense inverse goes through 16 panels of the blocked
+    Cholesky (diagonal block, triangular solve, trailing update).  The coarsest solve and a whole
+    B_co application must equal the oracle's dense Cholesky solve."""
+    p = inputs.small_3d(40, 40, 16, seed=51)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=512)
+    s = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=512)
+    last = s.nlevels - 1
+    assert s.level_info(last)["n"] == orc.level_sizes(orc.nlevels - 1)["n"] > 32 * 8
+    nc = s.level_info(last)["n"]
+    x = inputs.random_vector(nc, seed=52)
+    y = s.level_apply(last, 3, torch.tensor(x, device=DEV)).cpu().numpy()
+    assert rel(y, orc.level_apply(orc.nlevels - 1, 3, x)) < 1e-11
+    r = inputs.random_vector(A.n, seed=53)
+    z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    assert rel(z, orc.apply(O.BCO, r)) < 1e-11
+    s.close()
+
+
 def test_autotuned_layout_matches_oracle(case):
     """Chunk heights picked by timing (autotune) change the layout and the lanes per row, not the
     method: B_co still equals the oracle's."""
