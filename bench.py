@@ -240,24 +240,27 @@ def gpu_arm(args, rank, world):
 
     # comparison arms (fewer steps: AMG-alone and IC(0)-alone)
     arms = {}
-    for name, pre, prec, ico, k in [
-            ("amg_fp64", "amg", "fp64", "natural", args.steps),
-            ("ic0_fp64", "ic0", "fp64", "natural", 2),
-            ("ic0_rbic_fp64", "ic0", "fp64", "colour", 2),
-            ("bco_natic_fp64", "bco", "fp64", "natural", args.steps),
-            ("bhat_fp64", "bhat", "fp64", "colour", args.steps),
-            ("amg_ilu_fp64", "amg_ilu", "fp64", "colour", args.steps),
-            ("bco_fp32", "bco", "fp32", "colour", args.steps),
-            ("bco_fp32_bf16", "bco", "fp32_bf16", "colour", args.steps),
-            ("amg_fp32", "amg", "fp32", "natural", args.steps)]:
+    # (name, preconditioner, precision, IC(0) order, Gauss-Seidel order, timed solves)
+    for name, pre, prec, ico, gso, k in [
+            ("amg_fp64", "amg", "fp64", "natural", "multicolour", args.steps),
+            ("ic0_fp64", "ic0", "fp64", "natural", "multicolour", 2),
+            ("ic0_rbic_fp64", "ic0", "fp64", "colour", "multicolour", 2),
+            ("bco_natic_fp64", "bco", "fp64", "natural", "multicolour", args.steps),
+            ("bco_natgs_fp64", "bco", "fp64", "natural", "natural", 2),
+            ("bhat_fp64", "bhat", "fp64", "colour", "multicolour", args.steps),
+            ("amg_ilu_fp64", "amg_ilu", "fp64", "colour", "multicolour", args.steps),
+            ("bco_fp32", "bco", "fp32", "colour", "multicolour", args.steps),
+            ("bco_fp32_bf16", "bco", "fp32_bf16", "colour", "multicolour", args.steps),
+            ("amg_fp32", "amg", "fp32", "natural", "multicolour", args.steps)]:
         if world > 1:
             continue
         t = time.perf_counter()
-        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order=ico)
+        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order=ico, gs_order=gso)
         setup = dict(zip(("ic0_ms", "amg_ms"), s.setup_time_ms()))
         setup["wall_ms"] = (time.perf_counter() - t) * 1e3
         try:
-            m, it, _ = time_solves(s, k, 1 if name.startswith("ic0") else args.warmup)
+            slow = name in ("ic0_fp64", "ic0_rbic_fp64", "bco_natgs_fp64")      # one warm-up solve
+            m, it, _ = time_solves(s, k, 1 if slow else args.warmup)
         except SolveFailed as e:                 # AMG(ILU(0)) need not be SPD (Section 5): record it
             arms[name] = dict(ms=None, iters=e.iters, status=e.status, setup=setup)
             s.close()

@@ -58,6 +58,15 @@ enum {
     CPC_PREC_FP32_BF16 = 2  /* as FP32, with coarse-level operators stored in BF16               */
 };
 
+/* Gauss-Seidel ordering of the AMG smoother S_l (Section 3.3). */
+enum {
+    CPC_GS_MULTICOLOUR = 0, /* rows in colour-major order: a 2-colouring by breadth-first parity on a  */
+                            /* bipartite level, else a greedy colouring; one parallel step per colour */
+    CPC_GS_NATURAL = 1      /* the natural row order of each level ("standard GS"): one step per      */
+                            /* wavefront of the lower-triangular dependency graph, giving exactly the */
+                            /* sequential sweep i = 0..n-1 (and n-1..0 for S_l^T).  Far more steps.   */
+};
+
 /* CSR matrix, caller-owned; cpc_setup copies what it needs. */
 typedef struct {
     int32_t n;              /* rows = columns                                                    */
@@ -73,6 +82,8 @@ typedef struct {
     int32_t precision;      /* CPC_PREC_*                                          (default FP64)*/
     int32_t ic_order;       /* 0: natural order (level-scheduled); 1: multicolour order of the
                                finest level's Gauss-Seidel colouring                (default 0)   */
+    int32_t gs_order;       /* CPC_GS_*; CPC_GS_NATURAL needs ic_order = 0 and tail_nnz_max <= 0
+                                                                                    (default 0)   */
     double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
     int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (512)         */
     int32_t max_levels;     /* at most this many levels                            (20)          */
@@ -226,7 +237,8 @@ int cpc_level_matrix(const cpc_handle* h, int32_t level, int32_t* rowptr, int32_
 int cpc_level_interp(const cpc_handle* h, int32_t level, int32_t* rowptr, int32_t* colidx,
                      double* vals);
 
-/* Copy the C/F splitting (1 = C, 0 = F) and the smoothing colour of every row of level l. */
+/* Copy the C/F splitting (1 = C, 0 = F) and the smoothing colour of every row of level l (with
+ * CPC_GS_NATURAL: the row's wavefront of the lower-triangular dependency graph of A_l). */
 int cpc_level_splitting(const cpc_handle* h, int32_t level, int32_t* cf, int32_t* colour);
 
 /* Copy the IC(0) factor values (L strictly below the diagonal, U on and above) laid out on the

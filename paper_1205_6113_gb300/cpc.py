@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libcpc.so")
 
 PRECOND = {"bco": 0, "amg": 1, "ic0": 2, "ilu": 2, "bhat": 3, "none": 4, "amg_ilu": 5}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_bf16": 2}
+GS_ORDER = {"multicolour": 0, "natural": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "IC(0) breakdown", 3: "not converged", 4: "CG breakdown",
           5: "CUDA error", 6: "device wait timeout", 7: "AMG setup failure"}
 FACE = {"x0": 1, "x1": 2, "y0": 4, "y1": 8, "z0": 16, "z1": 32}
@@ -35,7 +36,7 @@ class _Csr(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("ic_order", ctypes.c_int32),
-                ("theta", ctypes.c_double), ("coarse_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("gs_order", ctypes.c_int32), ("theta", ctypes.c_double), ("coarse_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("autotune", ctypes.c_int32),
                 ("tail_nnz_max", ctypes.c_int64), ("stream", ctypes.c_void_p)]
 
@@ -160,7 +161,8 @@ class Solver:
     """
 
     def __init__(self, rowptr, col, val, precond="bco", precision="fp64", ic_order="natural", theta=0.25,
-                 coarse_max=512, max_levels=20, tail_nnz_max=0, autotune=False, stream=None):
+                 coarse_max=512, max_levels=20, tail_nnz_max=0, autotune=False, gs_order="multicolour",
+                 stream=None):
         torch = _torch()
         lib = load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -180,6 +182,7 @@ class Solver:
         opt.precond = PRECOND[precond]
         opt.precision = PRECISION[precision]
         opt.ic_order = {"natural": 0, "colour": 1}[ic_order]
+        opt.gs_order = GS_ORDER[gs_order]
         opt.theta = float(theta)
         opt.coarse_max = int(coarse_max)
         opt.max_levels = int(max_levels)
@@ -194,6 +197,7 @@ class Solver:
         self.precond = precond
         self.precision = precision
         self.ic_order = ic_order
+        self.gs_order = gs_order
 
     def close(self):
         if getattr(self, "_h", None):

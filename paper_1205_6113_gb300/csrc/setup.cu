@@ -9,7 +9,8 @@
 //   colour  breadth-first parity 2-colouring when the level graph is bipartite (red-black on a
 //           structured grid), else Jones-Plassmann with priority (peel round, fmix32(i ^
 //           0x5bd1e995)) and the smallest free colour; peel rounds are a smallest-last style
-//           ordering that needs fewer colours than a random one.
+//           ordering that needs fewer colours than a random one; with natural-order
+//           Gauss-Seidel, the wavefronts of the lower-triangular graph of A_l instead.
 // Sums that define matrix entries are accumulated in a fixed order (the order the products are
 // generated in), so results do not depend on thread scheduling.
 #include <cub/cub.cuh>
@@ -1235,6 +1236,20 @@ __global__ void k_tri_probe(int n, const int* ptr, const int* col, int* found) {
     }
 }
 
+// Natural-order Gauss-Seidel ("standard GS", Section 3.3): the group of row i is its wavefront in the
+// lower-triangular dependency graph of A_l, w(i) = 1 + max w(j) over j < i with a_ij != 0 (0 when
+// there is none).  Rows of one wavefront are not coupled, and the pattern is symmetric, so every
+// coupled j > i lies in a later wavefront.  Ascending wavefronts therefore reproduce the sequential
+// forward sweep i = 0, ..., n-1 exactly, and descending wavefronts the backward sweep.
+void wavefront_levels(Handle& h, cudaStream_t s) {
+    const int nl = (int)h.lev.size();
+    for (int l = 0; l + 1 < nl; ++l) {
+        Level& L = h.lev[l];
+        L.colour.alloc(L.n);
+        L.ncolours = dag_levels(L.A, false, L.colour.p, s);
+    }
+}
+
 // Smoothing colours of levels [0, nl - 1): the breadth-first parity 2-colouring if the pattern
 // graph is bipartite, else Jones-Plassmann with peel-round priority.  Every level is a small state
 // machine of round loops on its own stream; all levels advance one batch of launches at a time
@@ -1523,7 +1538,8 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         const bool stop = h.lev[l].n <= h.opt.coarse_max || (int)h.lev.size() >= h.opt.max_levels;
         if (stop || !coarsen(h, l, s)) break;
     }
-    colour_levels(h, s);
+    if (h.opt.gs_order == CPC_GS_NATURAL) wavefront_levels(h, s);
+    else colour_levels(h, s);
     const int nl = (int)h.lev.size();
     {
         Level& Lc = h.lev[nl - 1];

@@ -51,6 +51,7 @@ def test_pure_host_entry_points(lib):
     opt = cpc._Options()
     assert L.cpc_default_options(ctypes.byref(opt)) == 0
     assert opt.precond == 0 and opt.theta == 0.25 and opt.coarse_max == 512 and opt.max_levels == 20 and opt.autotune == 0
+    assert opt.gs_order == 0 and opt.ic_order == 0 and opt.tail_nnz_max == 0
     assert L.cpc_default_options(None) == 1
     assert L.cpc_tpfa_nnz(128, 128, 64) == 7274496
     assert L.cpc_tpfa_nnz(256, 256, 128) == 58458112
@@ -59,6 +60,20 @@ def test_pure_host_entry_points(lib):
     assert L.cpc_setup(None, None, ctypes.byref(h)) == 1 and not h.value
     assert L.cpc_solve(None, None, None, 1e-6, 10, None, None, 0) == 1
     L.cpc_destroy(None)
+    # option validation happens before any device work: a valid 1 x 1 host CSR with bad options
+    rp, ci, va = (ctypes.c_int32 * 2)(0, 1), (ctypes.c_int32 * 1)(0), (ctypes.c_double * 1)(1.0)
+    csr = cpc._Csr(1, 1, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(ci, ctypes.c_void_p),
+                   ctypes.cast(va, ctypes.c_void_p), 0)
+    for field, value in [("gs_order", 2), ("gs_order", -1), ("precond", 6), ("autotune", 2)]:
+        bad = cpc._Options()
+        L.cpc_default_options(ctypes.byref(bad))
+        setattr(bad, field, value)
+        assert L.cpc_setup(ctypes.byref(csr), ctypes.byref(bad), ctypes.byref(h)) == 1 and not h.value
+    for ic_order, tail in [(1, 0), (0, 1 << 20)]:      # natural-order GS: natural IC(0), no cluster kernel
+        bad = cpc._Options()
+        L.cpc_default_options(ctypes.byref(bad))
+        bad.gs_order, bad.ic_order, bad.tail_nnz_max = 1, ic_order, tail
+        assert L.cpc_setup(ctypes.byref(csr), ctypes.byref(bad), ctypes.byref(h)) == 1 and not h.value
 
 
 def test_cuda_path_has_no_cpu_fallback():

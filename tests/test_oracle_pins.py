@@ -410,6 +410,44 @@ def test_vcycle_symmetric_and_adjoint(small3d):
     assert rho < 1.0
 
 
+def test_natural_order_gauss_seidel_is_triangular_solve():
+    """Natural-order ("standard") GS of Section 3.3: the forward sweep is S_l = (D + L)^{-1} and the
+    backward sweep S_l^T = (D + U)^{-1} with the natural row order, i.e. the lower and upper
+    triangles of A_l including the diagonal; the V-cycle built on them obeys the recursion of
+    Algorithm 3.2 and B_co built on it is symmetric."""
+    p = inputs.small_3d(9, 8, 6, seed=11)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=20, gs_natural=True)
+    L = orc.nlevels
+    assert L >= 3
+    Bnext = np.linalg.inv(orc.level_A(L - 1).to_dense())
+    for l in range(L - 2, -1, -1):
+        D = orc.level_A(l).to_dense()
+        n = D.shape[0]
+        I = np.eye(n)
+        Sf = dense_op(lambda v: orc.level_apply(l, 1, v), n)
+        Sb = dense_op(lambda v: orc.level_apply(l, 2, v), n)
+        assert rel(Sf, np.linalg.inv(np.tril(D))) < 1e-12
+        assert rel(Sb, np.linalg.inv(np.triu(D))) < 1e-12
+        P = orc.level_P(l).to_dense()
+        E = (I - Sb @ D) @ (I - P @ Bnext @ P.T @ D) @ (I - Sf @ D)
+        Bl = (I - E) @ np.linalg.inv(D)
+        assert rel(dense_op(lambda v: orc.level_apply(l, 4, v), n), Bl) < 1e-11
+        Bnext = Bl
+    D = A.to_dense()
+    Bco = dense_op(lambda v: orc.apply(O.BCO, v), A.n)
+    assert rel(Bco, Bco.T) < 1e-11
+    assert np.min(np.linalg.eigvalsh(0.5 * (Bco + Bco.T))) > 0.0
+    # the multicolour cycle is a different operator (the orderings differ)
+    mc = O.Oracle(A, coarse_max=20)
+    assert rel(dense_op(lambda v: mc.level_apply(0, 1, v), A.n), Sf) > 1e-3
+    b = np.zeros(A.n)
+    b[A.n // 2] = 1.0
+    res = orc.pcg(b, op=O.BCO, tol=1e-12, maxit=200)
+    x = np.linalg.solve(D, b)
+    assert np.linalg.norm(res["x"] - x) <= 1e-8 * np.linalg.norm(x)
+
+
 def test_single_level_hierarchy_is_exact():
     p = inputs.small_3d(5, 4, 3, seed=2)
     A = O.tpfa_problem(p)
