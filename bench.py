@@ -373,6 +373,14 @@ def batched_arm(rowptr, col, val, p, dev, stream, args, K=64):
     e1.record(stream)
     torch.cuda.synchronize()
     fwd_batched_ms = e0.elapsed_time(e1)
+    # block PCG (O'Leary) on the same 64 columns: coupled through K x K FP64 Gram matrices
+    s.solve_block(B, tol=TOL, maxit=MAXIT, X=X)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, blk_it, blk_res, blk_st = s.solve_block(B, tol=TOL, maxit=MAXIT, X=X)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    block_ms = e0.elapsed_time(e1)
     cols = [B[:, k].contiguous() for k in range(K)]
     s.solve(cols[0], tol=TOL, maxit=MAXIT, hist=False)
     torch.cuda.synchronize()
@@ -390,6 +398,8 @@ def batched_arm(rowptr, col, val, p, dev, stream, args, K=64):
                 sequential_fwd_ms=round(seq_ms, 2), sequential_solves_per_s=round(K / (seq_ms * 1e-3), 1),
                 iters_fwd=[int(itf.min()), int(itf.max())], iters_adj=[int(ita.min()), int(ita.max())],
                 iters_sequential=[int(min(fwd_only)), int(max(fwd_only))],
+                block_cg_fwd_ms=round(block_ms, 2), block_cg_solves_per_s=round(K / (block_ms * 1e-3), 1),
+                block_cg_iters=int(blk_it), block_cg_status=int(blk_st), block_cg_max_res=float(np.max(blk_res)),
                 chunk_height_autotuned=chunk)
 
 

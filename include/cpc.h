@@ -189,6 +189,23 @@ int cpc_solve_batched(cpc_handle* h, int32_t nrhs, const double* B, double* X, d
                       int32_t maxit, int32_t* iters, int32_t* status);
 
 /*
+ * Block PCG (O'Leary 1980) on K = nrhs right-hand sides (1 <= nrhs <= 64) coupled in one block
+ * Krylov space, with the handle's preconditioner applied to all K columns at once:
+ *   Q = A P, alpha = (P^T Q)^{-1} gamma, X += P alpha, R -= Q alpha, Z = M R,
+ *   beta = gamma^{-1} (Z^T R), gamma = Z^T R, P = Z + P beta  (gamma_0 = Z_0^T R_0, P_0 = Z_0),
+ * with the K x K systems solved by Cholesky in FP64.  Stops when every column has
+ * ||r_k||_2 / ||b_k||_2 < tol (recursive residual).  B, X: device, [n][nrhs] row-major as in
+ * cpc_solve_batched.  *iters = block iterations taken; res[nrhs] (host, may be NULL) the final
+ * relative residual of each column.  Not a passage of the paper: the coupled-column variant of the
+ * many-right-hand-side solve.  Returns CPC_OK, CPC_ENOCONV, CPC_EBREAKDOWN (a K x K matrix not
+ * positive definite: a rank-deficient block; X holds the last good iterate), CPC_EINVAL (nrhs out
+ * of range, a zero column, or the AMG(ILU(0)) preconditioner) or CPC_ECUDA.  Synchronises the
+ * stream once per iteration.
+ */
+int cpc_solve_block(cpc_handle* h, int32_t nrhs, const double* B, double* X, double tol, int32_t maxit,
+                    int32_t* iters, double* res);
+
+/*
  * As cpc_solve_batched, then in the same graph the adjoint solves A Lambda = G with
  * G[i][k] = X[i][k] where B[i][k] != 0 and 0 elsewhere (the gradient of
  * J_k = 1/2 sum over the source cells of column k of X[i][k]^2).  X receives the forward

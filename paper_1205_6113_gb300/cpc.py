@@ -58,6 +58,7 @@ SIGNATURES = [
     ("cpc_solve_host", _I32, [_P, _P, _P, _F64, _I32, _P, _P, _I32]),
     ("cpc_solve_batched", _I32, [_P, _I32, _P, _P, _F64, _I32, _P, _P]),
     ("cpc_solve_batched_adjoint", _I32, [_P, _I32, _P, _P, _P, _F64, _I32, _P, _P]),
+    ("cpc_solve_block", _I32, [_P, _I32, _P, _P, _F64, _I32, _P, _P]),
     ("cpc_apply_precond", _I32, [_P, _I32, _P, _P]),
     ("cpc_apply_Bcom", _I32, [_P, _P, _P]),
     ("cpc_spmv", _I32, [_P, _P, _P]),
@@ -249,6 +250,21 @@ class Solver:
                                         int(maxit), ctypes.c_void_p(it.ctypes.data), ctypes.c_void_p(st.ctypes.data)),
                self._h)
         return X, it, st
+
+    def solve_block(self, B, tol=1e-6, maxit=1000, X=None, check=True):
+        """Block PCG on the columns of B ([n, K] CUDA float64, K <= 64); returns (X, iters, res[K], status).
+        With check, a status other than ok / not converged raises."""
+        torch = _torch()
+        if X is None:
+            X = torch.empty_like(B)
+        K = int(B.shape[1])
+        it = ctypes.c_int32(0)
+        res = np.zeros(K, np.float64)
+        rc = load().cpc_solve_block(self._h, K, _dptr(B, torch.float64), _dptr(X, torch.float64), float(tol),
+                                    int(maxit), ctypes.byref(it), ctypes.c_void_p(res.ctypes.data))
+        if check and rc not in (0, 3):
+            _check(rc, self._h)
+        return X, it.value, res, rc
 
     def solve_batched_adjoint(self, B, tol=1e-6, maxit=1000, X=None, Lam=None):
         """Forward solves of B's columns, then adjoint solves with sources X at B's nonzeros (one graph)."""

@@ -161,6 +161,17 @@ int cpc_solve_batched(cpc_handle* h, int32_t nrhs, const double* B, double* X, d
     return guarded(h, [&] { cpc::solve_batched(h->h, nrhs, B, X, nullptr, tol, maxit, iters, status, nullptr, nullptr); });
 }
 
+int cpc_solve_block(cpc_handle* h, int32_t nrhs, const double* B, double* X, double tol, int32_t maxit,
+                    int32_t* iters, double* res) {
+    if (!h || nrhs < 1 || nrhs > 64 || !B || !X || !iters || maxit < 0 || !(tol >= 0.0)) return CPC_EINVAL;
+    int status = CPC_OK;
+    const int rc = guarded(h, [&] { status = cpc::solve_block(h->h, nrhs, B, X, tol, maxit, iters, res); });
+    if (rc != CPC_OK) return rc;
+    if (status == CPC_ENOCONV) h->h.err = "block CG not converged within maxit";
+    if (status == CPC_EBREAKDOWN) h->h.err = "block CG breakdown (a K x K matrix is not positive definite)";
+    return status;
+}
+
 int cpc_solve_batched_adjoint(cpc_handle* h, int32_t nrhs, const double* B, double* X, double* Lambda, double tol,
                               int32_t maxit, int32_t* iters_fwd, int32_t* iters_adj) {
     if (!h || nrhs < 1 || nrhs > 128 || !B || !X || !Lambda || !iters_fwd || !iters_adj || maxit < 0 || !(tol >= 0.0))

@@ -776,6 +776,301 @@ __global__ void kb_adjoint_rhs(int64_t nk, double* __restrict__ b, const double*
 // ---------------------------------------------------------------------------------------------
 // Recording (column-wise V-cycle, IC(0), B_co)
 // ---------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------------
+// Block PCG (O'Leary 1980): the K columns share one block Krylov space through K x K matrices.
+// Not a method of the paper; the coupled counterpart of the batched solve above.  All K x K
+// arithmetic is FP64 and every sum finishes in a fixed order.
+// ------------------------------------------------------------------------------------------------
+constexpr int KK_TPB = 256;
+constexpr int KK_ROWS = 32;               // rows staged per step of kk_gram
+constexpr int KK_GRID = 152 * 2;          // blocks of kk_gram / kk_update / kk_colnorm (fixed)
+enum { KM_PQ = 0, KM_GAMMA, KM_GAMMA_NEW, KM_ALPHA, KM_BETA, KM_COUNT };
+enum { KV_BNORM = 0, KV_RES, KV_COUNT };
+enum { KF_BAD = 0, KF_DONE, KF_COUNT };
+
+// part[block] = U^T V over the block's rows, on the 4 x 4 tiles (ti, tj) with ti <= tj of the
+// Kp x Kp result (Kp = 32 or 64); U is Z (preconditioner precision) or P, V is R or Q (FP64).
+template <class UT>
+__global__ void __launch_bounds__(KK_TPB) kk_gram(int n, int Kp, const UT* __restrict__ U,
+                                                  const double* __restrict__ V, double* __restrict__ part) {
+    extern __shared__ double ksm[];
+    double* us = ksm;                      // [KK_ROWS][Kp]
+    double* vs = ksm + KK_ROWS * Kp;       // [KK_ROWS][Kp]
+    const int T = Kp / 4, t = threadIdx.x;
+    const int ti = t / T, tj = t - (t / T) * T;
+    const bool act = t < T * T && ti <= tj;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int r0 = min(n, blockIdx.x * per), r1 = min(n, r0 + per);
+    for (int base = r0; base < r1; base += KK_ROWS) {
+        const int rows = min(KK_ROWS, r1 - base);
+        __syncthreads();
+        for (int e = t; e < KK_ROWS * Kp; e += KK_TPB) {
+            const int rr = e / Kp;
+            const size_t g = (size_t)base * Kp + e;
+            us[e] = rr < rows ? (double)U[g] : 0.0;
+            vs[e] = rr < rows ? V[g] : 0.0;
+        }
+        __syncthreads();
+        if (act) {
+            for (int rr = 0; rr < rows; ++rr) {
+                double a[4], c[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = us[rr * Kp + ti * 4 + q];
+                    c[q] = vs[rr * Kp + tj * 4 + q];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) acc[q][w] = __fma_rn(a[q], c[w], acc[q][w]);
+            }
+        }
+    }
+    if (act)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) part[((size_t)blockIdx.x * Kp + ti * 4 + q) * Kp + tj * 4 + w] = acc[q][w];
+}
+
+// out = sum over blocks of part, in block order; entry (i, j) and (j, i) both take the computed
+// upper entry (min, max), so the result is exactly symmetric.
+__global__ void kk_gram_sum(int G, int Kp, const double* __restrict__ part, double* __restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Kp * Kp; e += gridDim.x * blockDim.x) {
+        const int i = e / Kp, j = e - (e / Kp) * Kp;
+        const int a = min(i, j), b = max(i, j);
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part[((size_t)g * Kp + a) * Kp + b];
+        out[e] = s;
+    }
+}
+
+// Y = S^{-1} W on the leading K x K blocks by Cholesky S = L L^T (one block; S symmetric).  out is
+// Kp x Kp with zeros outside K x K.  A pivot that is not finite or at most 1e-12 times its diagonal
+// entry s_kk (a block column within rounding of the span of the others) sets flag[KF_BAD].
+// With copy_to, W is copied there afterwards (gamma_old <- gamma_new).
+__global__ void __launch_bounds__(KK_TPB) kk_solve(int K, int Kp, const double* S, const double* W,
+                                                   double* __restrict__ out, double* copy_to, int* flag) {
+    extern __shared__ double ksm[];
+    double* L = ksm;                       // [K][K]
+    double* Y = ksm + K * K;               // [K][K]
+    __shared__ int bad;
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (t == 0) bad = 0;
+    for (int e = t; e < K * K; e += nt) {
+        const int i = e / K, j = e - (e / K) * K;
+        L[e] = S[(size_t)i * Kp + j];
+        Y[e] = W[(size_t)i * Kp + j];
+    }
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+        if (t == 0) {
+            const double d = L[k * K + k];
+            if (!(d > 1e-12 * S[(size_t)k * Kp + k]) || !isfinite(d)) bad = 1;
+            L[k * K + k] = sqrt(d > 0.0 && isfinite(d) ? d : 1.0);
+        }
+        __syncthreads();
+        const double dk = L[k * K + k];
+        for (int i = k + 1 + t; i < K; i += nt) L[i * K + k] /= dk;
+        __syncthreads();
+        const int m = K - k - 1;
+        for (int e = t; e < m * m; e += nt) {
+            const int i = k + 1 + e / m, j = k + 1 + (e - (e / m) * m);
+            if (j <= i) L[i * K + j] -= L[i * K + k] * L[j * K + k];
+        }
+        __syncthreads();
+    }
+    for (int c = t; c < K; c += nt) {      // one right-hand-side column per thread
+        for (int i = 0; i < K; ++i) {      // L z = w
+            double s = Y[i * K + c];
+            for (int q = 0; q < i; ++q) s -= L[i * K + q] * Y[q * K + c];
+            Y[i * K + c] = s / L[i * K + i];
+        }
+        for (int i = K - 1; i >= 0; --i) { // L^T y = z
+            double s = Y[i * K + c];
+            for (int q = i + 1; q < K; ++q) s -= L[q * K + i] * Y[q * K + c];
+            Y[i * K + c] = s / L[i * K + i];
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < Kp * Kp; e += nt) {
+        const int i = e / Kp, j = e - (e / Kp) * Kp;
+        out[e] = (i < K && j < K) ? Y[i * K + j] : 0.0;
+        if (copy_to) copy_to[e] = W[e];
+    }
+    if (t == 0 && bad) flag[KF_BAD] = 1;
+}
+
+// Entry k of a row held across the warp (lane k mod 32 of register k / 32).
+template <int J>
+__device__ __forceinline__ double kk_lane(const double (&v)[J], int k) {
+    if constexpr (J == 1) return __shfl_sync(0xffffffffu, v[0], k & 31);
+    else return __shfl_sync(0xffffffffu, k < 32 ? v[0] : v[1], k & 31);
+}
+
+// X += P alpha and R -= Q alpha (warp per row, lanes over columns, alpha in shared memory), and
+// per block the column sums of r_ij^2 in warp order into part[block][Kp].
+template <int J>
+__global__ void __launch_bounds__(BTPB) kk_update(int n, int Kp, int K, double* __restrict__ X, double* __restrict__ R,
+                                                  const double* __restrict__ P, const double* __restrict__ Q,
+                                                  const double* __restrict__ alpha, double* __restrict__ part,
+                                                  const int* __restrict__ flag) {
+    if (flag[KF_BAD]) return;              // a K x K solve failed: keep the last good iterate
+    extern __shared__ double ksm[];
+    double* al = ksm;                      // [Kp][Kp]
+    double* ws = ksm + Kp * Kp;            // [BWARPS][Kp]
+    for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) al[e] = alpha[e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double rr[J];
+#pragma unroll
+    for (int m = 0; m < J; ++m) rr[m] = 0.0;
+    for (int i = blockIdx.x * BWARPS + w; i < n; i += gridDim.x * BWARPS) {
+        const size_t o = (size_t)i * Kp + lane;
+        double p[J], q[J], dx[J], dr[J];
+#pragma unroll
+        for (int m = 0; m < J; ++m) {
+            p[m] = P[o + 32 * m];
+            q[m] = Q[o + 32 * m];
+            dx[m] = 0.0;
+            dr[m] = 0.0;
+        }
+        for (int k = 0; k < K; ++k) {
+            const double pk = kk_lane<J>(p, k), qk = kk_lane<J>(q, k);
+#pragma unroll
+            for (int m = 0; m < J; ++m) {
+                const double a = al[k * Kp + lane + 32 * m];
+                dx[m] = __fma_rn(pk, a, dx[m]);
+                dr[m] = __fma_rn(qk, a, dr[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < J; ++m) {
+            X[o + 32 * m] += dx[m];
+            const double r = R[o + 32 * m] - dr[m];
+            R[o + 32 * m] = r;
+            rr[m] = __fma_rn(r, r, rr[m]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < J; ++m) ws[w * Kp + lane + 32 * m] = rr[m];
+    __syncthreads();
+    for (int c = threadIdx.x; c < Kp; c += blockDim.x) {
+        double s = 0.0;
+        for (int v = 0; v < BWARPS; ++v) s += ws[v * Kp + c];
+        part[(size_t)blockIdx.x * Kp + c] = s;
+    }
+}
+
+// P = Z + P beta, in place (a warp reads its whole row of P before writing it).
+template <int J, class ZT>
+__global__ void __launch_bounds__(BTPB) kk_pupdate(int n, int Kp, int K, const ZT* __restrict__ Z, double* __restrict__ P,
+                                                   const double* __restrict__ beta, const int* __restrict__ flag) {
+    if (flag[KF_BAD]) return;
+    extern __shared__ double ksm[];
+    for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) ksm[e] = beta[e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = blockIdx.x * BWARPS + w; i < n; i += gridDim.x * BWARPS) {
+        const size_t o = (size_t)i * Kp + lane;
+        double p[J], acc[J];
+#pragma unroll
+        for (int m = 0; m < J; ++m) {
+            p[m] = P[o + 32 * m];
+            acc[m] = 0.0;
+        }
+        for (int k = 0; k < K; ++k) {
+            const double pk = kk_lane<J>(p, k);
+#pragma unroll
+            for (int m = 0; m < J; ++m) acc[m] = __fma_rn(pk, ksm[k * Kp + lane + 32 * m], acc[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < J; ++m) P[o + 32 * m] = (double)Z[o + 32 * m] + acc[m];
+    }
+}
+
+template <class ZT>
+__global__ void kk_copy(int64_t nk, const ZT* __restrict__ z, double* __restrict__ p) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = (double)z[e];
+}
+
+// Q = A P with A in CSR (warp per row, lanes over columns).
+template <int J>
+__global__ void __launch_bounds__(BTPB) kk_spmm(int n, int Kp, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                const double* __restrict__ val, const double* __restrict__ P,
+                                                double* __restrict__ Q) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = blockIdx.x * BWARPS + w; i < n; i += gridDim.x * BWARPS) {
+        double acc[J];
+#pragma unroll
+        for (int m = 0; m < J; ++m) acc[m] = 0.0;
+        for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+            const double a = val[e];
+            const size_t o = (size_t)col[e] * Kp + lane;
+#pragma unroll
+            for (int m = 0; m < J; ++m) acc[m] = __fma_rn(a, P[o + 32 * m], acc[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < J; ++m) Q[(size_t)i * Kp + lane + 32 * m] = acc[m];
+    }
+}
+
+// Per block, the column sums of v_ij^2 in warp order into part[block][Kp].
+template <int J>
+__global__ void __launch_bounds__(BTPB) kk_colnorm(int n, int Kp, const double* __restrict__ V, double* __restrict__ part) {
+    __shared__ double ws[BWARPS * 128];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double s[J];
+#pragma unroll
+    for (int m = 0; m < J; ++m) s[m] = 0.0;
+    for (int i = blockIdx.x * BWARPS + w; i < n; i += gridDim.x * BWARPS)
+#pragma unroll
+        for (int m = 0; m < J; ++m) {
+            const double v = V[(size_t)i * Kp + lane + 32 * m];
+            s[m] = __fma_rn(v, v, s[m]);
+        }
+#pragma unroll
+    for (int m = 0; m < J; ++m) ws[w * Kp + lane + 32 * m] = s[m];
+    __syncthreads();
+    for (int c = threadIdx.x; c < Kp; c += blockDim.x) {
+        double t = 0.0;
+        for (int v = 0; v < BWARPS; ++v) t += ws[v * Kp + c];
+        part[(size_t)blockIdx.x * Kp + c] = t;
+    }
+}
+
+// One block.  Column norms from the partials (block order).  init: bnorm_k = ||b_k||, a zero column
+// sets KF_BAD.  Otherwise res_k = ||r_k|| / ||b_k||; KF_DONE = 1 when every column is below tol,
+// and a residual that is not finite sets KF_BAD.
+__global__ void kk_check(int G, int Kp, int K, const double* __restrict__ part, double* __restrict__ vec, double tol,
+                         int init, int* flag) {
+    __shared__ int all;
+    if (threadIdx.x == 0) all = 1;
+    __syncthreads();
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part[(size_t)g * Kp + c];
+        const double nrm = sqrt(s);
+        if (init) {
+            vec[KV_BNORM * Kp + c] = nrm;
+            if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(&flag[KF_BAD], 1);
+        } else {
+            const double r = nrm / vec[KV_BNORM * Kp + c];
+            vec[KV_RES * Kp + c] = r;
+            if (!isfinite(r)) atomicOr(&flag[KF_BAD], 1);
+            if (!(r < tol)) atomicAnd(&all, 0);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !init) flag[KF_DONE] = all;
+}
+
 template <class VT> VT* bx(Batched& B, int l) { return (VT*)B.lx[l].p; }
 template <class VT> VT* bf(Batched& B, int l) { return (VT*)B.lf[l].p; }
 template <class VT> VT* br(Batched& B, int l) { return (VT*)B.lr[l].p; }
@@ -1080,6 +1375,85 @@ void build_batched_graph(Handle& h, bool with_adjoint) {
     B.gexec = ge;
 }
 
+
+// Block PCG loop on the packed block vectors of h.bat (K <= Kp <= 64).  Each iteration:
+//   Q = A P;  alpha = (P^T Q)^{-1} gamma;  X += P alpha, R -= Q alpha;  stop when every column
+//   has ||r_k|| / ||b_k|| < tol;  Z = M R;  beta = gamma^{-1} (Z^T R);  gamma = Z^T R;  P = Z + P beta.
+// The host reads two flags per iteration (one stream synchronisation).
+template <int J, class VT>
+int solve_block_t(Handle& h, int K, double tol, int maxit, int* iters, double* res) {
+    Batched& B = h.bat;
+    const int Kp = B.Kp, n = h.n;
+    cudaStream_t s = h.s;
+    const int64_t nk = (int64_t)n * Kp;
+    auto km = [&](int i) { return B.kmat.p + (size_t)i * Kp * Kp; };
+    const size_t gram_smem = 2 * (size_t)KK_ROWS * Kp * sizeof(double);
+    const size_t solve_smem = 2 * (size_t)K * K * sizeof(double);
+    const size_t upd_smem = ((size_t)Kp * Kp + BWARPS * Kp) * sizeof(double);
+    const size_t pup_smem = (size_t)Kp * Kp * sizeof(double);
+    CPC_CK(cudaFuncSetAttribute(kk_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * (int)sizeof(double)));
+    const Csr& A = h.lev[0].A;
+    const int rg = std::min(rows_grid(n), 152 * 8);
+    VT* z = (VT*)B.z.p;
+    auto gram = [&](const auto* U, const double* V, double* out) {
+        kk_gram<<<KK_GRID, KK_TPB, gram_smem, s>>>(n, Kp, U, V, B.kpart.p);
+        kk_gram_sum<<<16, 256, 0, s>>>(KK_GRID, Kp, B.kpart.p, out);
+    };
+    int flags[KF_COUNT] = {0, 0};
+    auto read_flags = [&]() {
+        CPC_LAUNCH_CK();
+        CPC_CK(cudaMemcpyAsync(flags, B.kflag.p, sizeof(flags), cudaMemcpyDeviceToHost, s));
+        CPC_CK(cudaStreamSynchronize(s));
+    };
+    CPC_CK(cudaMemsetAsync(B.kflag.p, 0, sizeof(int) * KF_COUNT, s));
+    CPC_CK(cudaMemsetAsync(B.kmat.p, 0, sizeof(double) * KM_COUNT * Kp * Kp, s));
+    kb_pack<<<2048, 256, 0, s>>>(n, K, Kp, (const double*)B.user_b, B.b.p);
+    CPC_CK(cudaMemcpyAsync(B.r.p, B.b.p, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+    CPC_CK(cudaMemsetAsync(B.x.p, 0, sizeof(double) * nk, s));
+    kk_colnorm<J><<<KK_GRID, BTPB, 0, s>>>(n, Kp, B.r.p, B.kpart.p);
+    kk_check<<<1, 64, 0, s>>>(KK_GRID, Kp, K, B.kpart.p, B.kvec.p, tol, 1, B.kflag.p);
+    read_flags();
+    if (flags[KF_BAD]) fail(CPC_EINVAL, "a right-hand-side column is zero or not finite");
+    brec_precond<J, VT>(h, h.opt.precond, B.r.p, z, s);              // Z = M R
+    kk_copy<VT><<<2048, 256, 0, s>>>(nk, (const VT*)z, B.p.p);         // P = Z
+    gram((const VT*)z, B.r.p, km(KM_GAMMA));                           // gamma = Z^T R
+    int status = CPC_ENOCONV, it = 0;
+    for (int k = 1; k <= maxit; ++k) {
+        kk_spmm<J><<<rg, BTPB, 0, s>>>(n, Kp, A.ptr.p, A.col.p, A.val.p, (const double*)B.p.p, B.q.p);
+        gram((const double*)B.p.p, B.q.p, km(KM_PQ));
+        kk_solve<<<1, KK_TPB, solve_smem, s>>>(K, Kp, km(KM_PQ), km(KM_GAMMA), km(KM_ALPHA), nullptr, B.kflag.p);
+        kk_update<J><<<KK_GRID, BTPB, upd_smem, s>>>(n, Kp, K, B.x.p, B.r.p, B.p.p, B.q.p, km(KM_ALPHA), B.kpart.p,
+                                                    B.kflag.p);
+        kk_check<<<1, 64, 0, s>>>(KK_GRID, Kp, K, B.kpart.p, B.kvec.p, tol, 0, B.kflag.p);
+        read_flags();
+        if (flags[KF_BAD]) {                                           // X holds iteration k - 1
+            status = CPC_EBREAKDOWN;
+            it = k - 1;
+            break;
+        }
+        it = k;
+        if (flags[KF_DONE]) {
+            status = CPC_OK;
+            break;
+        }
+        if (k == maxit) break;
+        brec_precond<J, VT>(h, h.opt.precond, B.r.p, z, s);          // Z = M R
+        gram((const VT*)z, B.r.p, km(KM_GAMMA_NEW));                   // Z^T R
+        kk_solve<<<1, KK_TPB, solve_smem, s>>>(K, Kp, km(KM_GAMMA), km(KM_GAMMA_NEW), km(KM_BETA), km(KM_GAMMA),
+                                               B.kflag.p);
+        kk_pupdate<J, VT><<<KK_GRID, BTPB, pup_smem, s>>>(n, Kp, K, (const VT*)z, B.p.p, km(KM_BETA), B.kflag.p);
+    }
+    kb_unpack<<<2048, 256, 0, s>>>(n, K, Kp, (const double*)B.x.p, B.user_x);
+    CPC_LAUNCH_CK();
+    std::vector<double> hv((size_t)KV_COUNT * Kp);
+    CPC_CK(cudaMemcpyAsync(hv.data(), B.kvec.p, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, s));
+    CPC_CK(cudaStreamSynchronize(s));
+    *iters = it;
+    if (res)
+        for (int c = 0; c < K; ++c) res[c] = hv[(size_t)KV_RES * Kp + c];
+    return status;
+}
+
 }  // namespace
 
 void destroy_batched(Handle& h) {
@@ -1113,6 +1487,12 @@ static void ensure_batched(Handle& h, int K, bool adjoint, double* user_b, doubl
         B.S.alloc((size_t)NB_STATE * Kp);
         B.partial.alloc((size_t)152 * 32 * Kp);
         B.kfwd.alloc(2 * (size_t)Kp);
+        if (Kp <= 64) {
+            B.kmat.alloc((size_t)KM_COUNT * Kp * Kp);
+            B.kpart.alloc((size_t)KK_GRID * Kp * Kp);
+            B.kvec.alloc((size_t)KV_COUNT * Kp);
+            B.kflag.alloc(KF_COUNT);
+        }
     }
     if (B.gexec && (B.K != K || B.adjoint != adjoint || B.user_b != user_b || B.user_x != user_x ||
                     B.user_lambda != user_lambda)) destroy_batched(h);
@@ -1169,6 +1549,17 @@ void solve_batched(Handle& h, int K, const double* b, double* x, double* lambda,
             if (status) status[c] = si;
         }
     }
+}
+
+int solve_block(Handle& h, int K, const double* b, double* x, double tol, int maxit, int* iters, double* res) {
+    if (K < 1 || K > 64) fail(CPC_EINVAL, "block CG takes 1 to 64 right-hand sides");
+    if (h.opt.precond == CPC_PRECOND_AMG_ILU) fail(CPC_EINVAL, "block CG supports B_co, AMG, IC(0) and B^");
+    ensure_batched(h, K, false, (double*)b, x, nullptr);
+    const bool fp64 = h.opt.precision == CPC_PREC_FP64;
+    if (h.bat.Kp == 32) return fp64 ? solve_block_t<1, double>(h, K, tol, maxit, iters, res)
+                                    : solve_block_t<1, float>(h, K, tol, maxit, iters, res);
+    return fp64 ? solve_block_t<2, double>(h, K, tol, maxit, iters, res)
+                : solve_block_t<2, float>(h, K, tol, maxit, iters, res);
 }
 
 }  // namespace cpc

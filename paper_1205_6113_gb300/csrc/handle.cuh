@@ -37,6 +37,9 @@ struct Batched {
     DBuf<char> z, t, y;
     std::vector<DBuf<char>> lx, lf, lr;
     DBuf<double> S, partial, kfwd;
+    // block CG: K x K matrices [KM_COUNT][Kp][Kp], Gram partials, column vectors [KV_COUNT][Kp], flags
+    DBuf<double> kmat, kpart, kvec;
+    DBuf<int> kflag;
     double* user_b = nullptr;
     double* user_x = nullptr;
     double* user_lambda = nullptr;
@@ -113,6 +116,8 @@ void setup_handle(Handle& h, const cpc_csr& A);
 // batched.cu
 void solve_batched(Handle& h, int K, const double* b, double* x, double* lambda, double tol, int maxit,
                    int* iters, int* status, int* iters_adj, int* status_adj);
+// Block PCG (O'Leary 1980) on K <= 64 columns; returns CPC_OK, CPC_ENOCONV or CPC_EBREAKDOWN.
+int solve_block(Handle& h, int K, const double* b, double* x, double tol, int maxit, int* iters, double* res);
 void destroy_batched(Handle& h);
 
 // tail.cu

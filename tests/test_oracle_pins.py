@@ -448,6 +448,54 @@ def test_natural_order_gauss_seidel_is_triangular_solve():
     assert np.linalg.norm(res["x"] - x) <= 1e-8 * np.linalg.norm(x)
 
 
+def test_block_pcg_reduces_to_pcg_for_one_column(small3d):
+    """Block CG with K = 1 is textbook PCG: same iterates, same residual history."""
+    p, A, orc, D = small3d
+    b = inputs.random_vector(A.n, seed=17)
+    ref = orc.pcg(b, op=O.BCO, tol=1e-10, maxit=200)
+    blk = O.block_pcg(orc, b[:, None], op=O.BCO, tol=1e-10, maxit=200)
+    assert blk["status"] == 0 and blk["iters"] == ref["iters"]
+    assert np.linalg.norm(blk["X"][:, 0] - ref["x"]) <= 1e-12 * np.linalg.norm(ref["x"])
+    assert np.allclose(blk["res_hist"][:, 0], ref["res_hist"], rtol=1e-7, atol=0.0)
+
+
+def test_block_cg_finite_termination_and_solution():
+    """Unpreconditioned block CG on n = 60 with K = 6 columns spans the whole space after n / K = 10
+    block iterations (exact arithmetic; two more allowed for rounding), and the solution is the
+    dense solve.  With B_co, every column is solved to the dense solution at tol 1e-12."""
+    p = inputs.small_3d(5, 4, 3, seed=3)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=20)
+    D = A.to_dense()
+    Bm = np.stack([inputs.random_vector(A.n, seed=40 + j) for j in range(6)], axis=1)
+    plain = O.block_pcg(orc, Bm, op=O.I, tol=1e-10, maxit=60)
+    assert plain["status"] == 0 and plain["iters"] <= A.n // 6 + 2
+    Xd = np.linalg.solve(D, Bm)
+    assert np.linalg.norm(plain["X"] - Xd) <= 1e-8 * np.linalg.norm(Xd)
+    pre = O.block_pcg(orc, Bm, op=O.BCO, tol=1e-12, maxit=60)
+    assert pre["status"] == 0
+    assert np.linalg.norm(pre["X"] - Xd) <= 1e-9 * np.linalg.norm(Xd)
+
+
+def test_block_cg_needs_no_more_iterations_than_its_columns(small3d):
+    """The block Krylov space contains each column's own Krylov space, so block CG minimises each
+    column's error over a larger space: it stops no later than the slowest single solve."""
+    p, A, orc, D = small3d
+    Bm = np.ascontiguousarray(inputs.batch_rhs(A.n, 8, cells_per_rhs=4, seed=6).T)
+    blk = O.block_pcg(orc, Bm, op=O.BCO, tol=1e-8, maxit=200)
+    single = [orc.pcg(Bm[:, j], op=O.BCO, tol=1e-8, maxit=200)["iters"] for j in range(8)]
+    assert blk["status"] == 0 and blk["iters"] <= max(single)
+    for j in range(8):
+        assert np.linalg.norm(Bm[:, j] - A.matvec(blk["X"][:, j])) <= 1.0001e-8 * np.linalg.norm(Bm[:, j])
+
+
+def test_block_cg_rank_deficient_block_is_a_breakdown(small3d):
+    p, A, orc, D = small3d
+    b = inputs.random_vector(A.n, seed=5)
+    blk = O.block_pcg(orc, np.stack([b, b], axis=1), op=O.BCO, tol=1e-8, maxit=50)
+    assert blk["status"] == 4
+
+
 def test_single_level_hierarchy_is_exact():
     p = inputs.small_3d(5, 4, 3, seed=2)
     A = O.tpfa_problem(p)
