@@ -527,7 +527,9 @@ def whole_job_ms_per_solve(ms_per_step: float, world: int) -> float:
 
 def profile_mode(name):
     """One preconditioner application plus one fine-level sweep between cudaProfilerStart/Stop
-    (for `ncu --profile-from-start off`), after two untimed warm-up applications."""
+    (for `ncu --profile-from-start off`), after two untimed warm-up applications.  With
+    name = "blockcg_fp32": one block PCG solve of the 64 right-hand sides of the batched workload
+    (FP32 preconditioner) after one untimed warm-up solve."""
     import torch
     from paper_1205_6113_gb300 import cpc
     pre, prec = name.split("_")
@@ -535,6 +537,18 @@ def profile_mode(name):
     p = inputs.workload(WORKLOAD)
     logk = torch.tensor(p.logk, device=dev)
     rowptr, col, val = cpc.tpfa_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+    if pre == "blockcg":
+        s = cpc.Solver(rowptr, col, val, precond="bco", precision=prec, ic_order="colour")
+        B = torch.tensor(np.ascontiguousarray(inputs.batch_rhs(p.n, 64, seed=5).T), device=dev)
+        X = torch.empty_like(B)
+        s.solve_block(B, tol=TOL, maxit=MAXIT, X=X)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        _, it, _, st = s.solve_block(B, tol=TOL, maxit=MAXIT, X=X)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profiled": name, "block_iterations": int(it), "status": int(st)}))
+        return
     s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order="colour")
     r = torch.tensor(p.rhs(), device=dev)
     z = torch.empty_like(r)

@@ -790,6 +790,9 @@ enum { KF_BAD = 0, KF_DONE, KF_COUNT };
 
 // part[block] = U^T V over the block's rows, on the 4 x 4 tiles (ti, tj) with ti <= tj of the
 // Kp x Kp result (Kp = 32 or 64); U is Z (preconditioner precision) or P, V is R or Q (FP64).
+// Thread t owns the t-th upper tile in row-major order, so the T (T + 1) / 2 active threads fill
+// whole warps: an FP64 warp instruction costs the same with idle lanes, and FP64 issue is the
+// bound of this kernel on this part.
 template <class UT>
 __global__ void __launch_bounds__(KK_TPB) kk_gram(int n, int Kp, const UT* __restrict__ U,
                                                   const double* __restrict__ V, double* __restrict__ part) {
@@ -797,8 +800,13 @@ __global__ void __launch_bounds__(KK_TPB) kk_gram(int n, int Kp, const UT* __res
     double* us = ksm;                      // [KK_ROWS][Kp]
     double* vs = ksm + KK_ROWS * Kp;       // [KK_ROWS][Kp]
     const int T = Kp / 4, t = threadIdx.x;
-    const int ti = t / T, tj = t - (t / T) * T;
-    const bool act = t < T * T && ti <= tj;
+    int ti = 0, rem = t;
+    while (ti < T && rem >= T - ti) {
+        rem -= T - ti;
+        ++ti;
+    }
+    const int tj = ti + rem;
+    const bool act = ti < T;
     double acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
