@@ -246,6 +246,18 @@ int cpc_level_info(const cpc_handle* h, int32_t level, int64_t* info);
  * info[3..5].  Returns CPC_EINVAL for a bad level; the coarsest level reports zeros. */
 int cpc_level_layout(const cpc_handle* h, int32_t level, int64_t* info);
 
+/*
+ * Structural check of every device layout of the handle, a stand-in for a memory and race
+ * sanitizer (every index a solve kernel gathers through comes from these layouts).  counts[5]
+ * (host) receives: [0] indices out of range (slot rows, chunk pointers, columns, diagonal offsets,
+ * group boundaries); [1] rows missing from or repeated in a layout; [2] pairs of coupled rows
+ * (a_ij != 0) in one Gauss-Seidel colour group, which one launch would update in parallel
+ * (Section 3.3); [3] IC(0) factor entries whose row's triangular-solve level is not after its
+ * column's (Algorithm 3.1); [4] the number of layouts checked.  All but [4] are 0 for a sound
+ * handle.  Synchronises the stream; allocates temporary device memory.
+ */
+int cpc_check_layouts(const cpc_handle* h, int64_t* counts);
+
 /* Copy A_l (CSR, natural order) to host arrays sized from cpc_level_info. */
 int cpc_level_matrix(const cpc_handle* h, int32_t level, int32_t* rowptr, int32_t* colidx,
                      double* vals);

@@ -59,6 +59,7 @@ SIGNATURES = [
     ("cpc_solve_batched", _I32, [_P, _I32, _P, _P, _F64, _I32, _P, _P]),
     ("cpc_solve_batched_adjoint", _I32, [_P, _I32, _P, _P, _P, _F64, _I32, _P, _P]),
     ("cpc_solve_block", _I32, [_P, _I32, _P, _P, _F64, _I32, _P, _P]),
+    ("cpc_check_layouts", _I32, [_P, _P]),
     ("cpc_apply_precond", _I32, [_P, _I32, _P, _P]),
     ("cpc_apply_Bcom", _I32, [_P, _P, _P]),
     ("cpc_spmv", _I32, [_P, _P, _P]),
@@ -350,6 +351,13 @@ class Solver:
         _check(load().cpc_level_interp(self._h, l, ctypes.c_void_p(ptr.ctypes.data), ctypes.c_void_p(col.ctypes.data),
                                        ctypes.c_void_p(val.ctypes.data)), self._h)
         return ptr, col[:i["nnzP"]], val[:i["nnzP"]]
+
+    def check_layouts(self):
+        """Structural check of the handle's device layouts (cpc_check_layouts): dict of counts."""
+        c = np.zeros(5, np.int64)
+        _check(load().cpc_check_layouts(self._h, ctypes.c_void_p(c.ctypes.data)), self._h)
+        return dict(out_of_range=int(c[0]), coverage=int(c[1]), gs_races=int(c[2]), triangular_races=int(c[3]),
+                    layouts=int(c[4]))
 
     def level_splitting(self, l):
         n = self.level_info(l)["n"]

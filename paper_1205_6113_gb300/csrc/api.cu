@@ -161,6 +161,12 @@ int cpc_solve_batched(cpc_handle* h, int32_t nrhs, const double* B, double* X, d
     return guarded(h, [&] { cpc::solve_batched(h->h, nrhs, B, X, nullptr, tol, maxit, iters, status, nullptr, nullptr); });
 }
 
+int cpc_check_layouts(const cpc_handle* h, int64_t* counts) {
+    if (!h || !counts) return CPC_EINVAL;
+    cpc_handle* hh = const_cast<cpc_handle*>(h);
+    return guarded(hh, [&] { cpc::check_layouts(hh->h, counts); });
+}
+
 int cpc_solve_block(cpc_handle* h, int32_t nrhs, const double* B, double* X, double tol, int32_t maxit,
                     int32_t* iters, double* res) {
     if (!h || nrhs < 1 || nrhs > 64 || !B || !X || !iters || maxit < 0 || !(tol >= 0.0)) return CPC_EINVAL;

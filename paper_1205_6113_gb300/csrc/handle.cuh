@@ -116,6 +116,10 @@ void setup_handle(Handle& h, const cpc_csr& A);
 // batched.cu
 void solve_batched(Handle& h, int K, const double* b, double* x, double* lambda, double tol, int maxit,
                    int* iters, int* status, int* iters_adj, int* status_adj);
+// Structural checks of every device layout (check.cu); counts[5]: out of range, coverage,
+// Gauss-Seidel races, triangular-solve races, layouts checked.
+void check_layouts(Handle& h, int64_t* counts);
+
 // Block PCG (O'Leary 1980) on K <= 64 columns; returns CPC_OK, CPC_ENOCONV or CPC_EBREAKDOWN.
 int solve_block(Handle& h, int K, const double* b, double* x, double tol, int maxit, int* iters, double* res);
 void destroy_batched(Handle& h);
