@@ -279,6 +279,10 @@ def gpu_arm(args, rank, world):
     if world == 1 and not args.no_batched:
         out["batched"] = batched_arm(rowptr, col, val, p, dev, stream, args)
 
+    # the mixed-hybrid system of the same grid (second matrix family), assembled on the device
+    if world == 1 and not args.no_mhfem:
+        out["mhfem"] = mhfem_arm(p, dev, stream, args)
+
     # differentiable solve on the 256 x 256 x 128 channel problem: gradient of the well misfit
     if world == 1 and not args.no_adjoint:
         out["adjoint"] = adjoint_arm(dev, stream)
@@ -401,6 +405,47 @@ def batched_arm(rowptr, col, val, p, dev, stream, args, K=64):
                 block_cg_fwd_ms=round(block_ms, 2), block_cg_solves_per_s=round(K / (block_ms * 1e-3), 1),
                 block_cg_iters=int(blk_it), block_cg_status=int(blk_st), block_cg_max_res=float(np.max(blk_res)),
                 chunk_height_autotuned=chunk)
+
+
+def mhfem_arm(p, dev, stream, args):
+    """The mixed-hybrid (p, lambda) system of the same grid (Section 4, Eq. alge_sys), assembled on
+    the device: cell sources, 0 on faces; B_co and AMG alone in FP64, B_co with the FP32
+    preconditioner.  IC(0) alone is left out (over a thousand iterations at this size)."""
+    import torch
+    from paper_1205_6113_gb300 import cpc
+    logk = torch.tensor(p.logk, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cpc.mhfem_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rowptr, col, val = cpc.mhfem_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    asm_ms = e0.elapsed_time(e1)
+    nu = int(rowptr.shape[0]) - 1
+    b = torch.zeros(nu, dtype=torch.float64, device=dev)
+    b[:p.n] = torch.tensor(p.rhs(), device=dev)
+    out = dict(workload=WORKLOAD + "_mhfem", unknowns=nu, nnz=int(col.shape[0]), assembly_ms=round(asm_ms, 3))
+    steps = max(1, min(args.steps, 3))
+    for name, pre, prec in [("bco_fp64", "bco", "fp64"), ("amg_fp64", "amg", "fp64"), ("bco_fp32", "bco", "fp32")]:
+        t = time.perf_counter()
+        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order="colour")
+        setup_ms = (time.perf_counter() - t) * 1e3
+        x, it, st, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
+        ms = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            x, it, st, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        xr = x.cpu().numpy()
+        res = float(np.linalg.norm(b.cpu().numpy() - csr_matvec(rowptr, col, val, xr)) / np.linalg.norm(b.cpu().numpy()))
+        out[name] = dict(ms=round(float(np.mean(ms)), 3), iters=int(it), status=int(st), setup_wall_ms=round(setup_ms, 1),
+                         levels=s.nlevels, true_res=res)
+        s.close()
+    return out
 
 
 def adjoint_arm(dev, stream, tol=1e-8):
@@ -577,6 +622,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-mhfem", action="store_true")
     ap.add_argument("--profile", default=None, help="e.g. bco_fp64: one application for ncu, then exit")
     args = ap.parse_args()
     if args.profile:
@@ -619,6 +665,7 @@ def main():
         "true_res": out["true_res"],
         "adjoint": out.get("adjoint"),
         "batched": out.get("batched"),
+        "mhfem": out.get("mhfem"),
         "clocks": out["clocks"],
         "gpu_launches": launches,
         "launches_per_iteration": per_it,

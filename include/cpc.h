@@ -119,6 +119,23 @@ int cpc_tpfa_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, do
                       void* stream);
 
 /*
+ * Mixed-hybrid system of Section 4 (Eq. alge_sys) for the lowest-order Raviart-Thomas element on
+ * the same grid of unit cells, in (pressure, multiplier) form: unknowns are the n cell pressures,
+ * then the multipliers of the x-, y- and z-faces, each family in (k, j, i) order, leaving out the
+ * faces flagged in dirichlet_mask (bits as above; p = 0 there).  Entries (columns ascending):
+ * cell row (c, sum over its six faces of 6 k_f), (f, -6 k_f) per free face; face row (L, -6 k_L),
+ * (R, -6 k_R) for its cells, (o, 2 k_c) for the opposite face o of each cell c, (f, 4 k_L + 4 k_R);
+ * k_f = k on x and y faces, k_z = kz_ratio k on z faces.  The matrix is SPD with positive
+ * off-diagonal face-face entries (not an M-matrix).
+ * cpc_mhfem_size returns nnz and writes the number of unknowns (host only; -1 when a size
+ * exceeds int32).  cpc_mhfem_assemble writes rowptr[n_unknowns + 1], colidx[nnz], vals[nnz]
+ * (device, caller-allocated) from logk[n] (device); asynchronous on `stream`.
+ */
+int64_t cpc_mhfem_size(int32_t nx, int32_t ny, int32_t nz, int32_t dirichlet_mask, int64_t* n_unknowns);
+int cpc_mhfem_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, double kz_ratio,
+                       int32_t dirichlet_mask, int32_t* rowptr, int32_t* colidx, double* vals, void* stream);
+
+/*
  * Adjoint gradient through the assembly above: g_c = -lambda^T (dA/dtheta_c) p with theta = logk.
  * For A(theta) p = q and a misfit J(p), with A lambda = dJ/dp (A is symmetric, so the solver of
  * A serves), g = dJ/dtheta.  A face contributes dT/dtheta_c (lambda_c - lambda_j)(p_c - p_j) with

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcpc.so")
-SOURCES = ["setup.cu", "solve.cu", "tail.cu", "adjoint.cu", "batched.cu", "api.cu", "noalloc.cu", "check.cu"]
+SOURCES = ["setup.cu", "solve.cu", "tail.cu", "adjoint.cu", "batched.cu", "api.cu", "noalloc.cu", "check.cu", "mhfem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -60,6 +60,8 @@ SIGNATURES = [
     ("cpc_solve_batched_adjoint", _I32, [_P, _I32, _P, _P, _P, _F64, _I32, _P, _P]),
     ("cpc_solve_block", _I32, [_P, _I32, _P, _P, _F64, _I32, _P, _P]),
     ("cpc_check_layouts", _I32, [_P, _P]),
+    ("cpc_mhfem_size", _I64, [_I32, _I32, _I32, _I32, _P]),
+    ("cpc_mhfem_assemble", _I32, [_I32, _I32, _I32, _P, _F64, _I32, _P, _P, _P, _P]),
     ("cpc_apply_precond", _I32, [_P, _I32, _P, _P]),
     ("cpc_apply_Bcom", _I32, [_P, _P, _P]),
     ("cpc_spmv", _I32, [_P, _P, _P]),
@@ -131,6 +133,29 @@ def tpfa_assemble(nx, ny, nz, logk, kz_ratio, dirichlet_mask, stream=None):
     _check(load().cpc_tpfa_assemble(nx, ny, nz, _dptr(logk, torch.float64), float(kz_ratio), int(dirichlet_mask),
                                     _dptr(rowptr, torch.int32), _dptr(col, torch.int32),
                                     _dptr(val, torch.float64), _stream_ptr(stream)))
+    return rowptr, col, val
+
+
+def mhfem_size(nx, ny, nz, dirichlet_mask):
+    """(unknowns, nnz) of the mixed-hybrid system (cpc_mhfem_size)."""
+    nu = ctypes.c_int64(0)
+    nnz = int(load().cpc_mhfem_size(nx, ny, nz, int(dirichlet_mask), ctypes.byref(nu)))
+    if nnz < 0:
+        raise CpcError(1, "grid too large for int32 indices")
+    return int(nu.value), nnz
+
+
+def mhfem_assemble(nx, ny, nz, logk, kz_ratio, dirichlet_mask, stream=None):
+    """Mixed-hybrid (p, lambda) matrix on the device from a device log-permeability (cpc_mhfem_assemble)."""
+    torch = _torch()
+    nu, nnz = mhfem_size(nx, ny, nz, dirichlet_mask)
+    dev = logk.device
+    rowptr = torch.empty(nu + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float64, device=dev)
+    _check(load().cpc_mhfem_assemble(nx, ny, nz, _dptr(logk, torch.float64), float(kz_ratio), int(dirichlet_mask),
+                                     _dptr(rowptr, torch.int32), _dptr(col, torch.int32),
+                                     _dptr(val, torch.float64), _stream_ptr(stream)))
     return rowptr, col, val
 
 

@@ -77,6 +77,24 @@ int cpc_tpfa_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, do
     });
 }
 
+int64_t cpc_mhfem_size(int32_t nx, int32_t ny, int32_t nz, int32_t dirichlet_mask, int64_t* n_unknowns) {
+    if (nx < 1 || ny < 1 || nz < 1 || !n_unknowns || (int64_t)nx * ny * nz > INT32_MAX) return -1;
+    const int64_t nnz = cpc::mhfem_size(nx, ny, nz, dirichlet_mask, n_unknowns);
+    if (*n_unknowns > INT32_MAX || nnz > INT32_MAX) return -1;
+    return nnz;
+}
+
+int cpc_mhfem_assemble(int32_t nx, int32_t ny, int32_t nz, const double* logk, double kz_ratio,
+                       int32_t dirichlet_mask, int32_t* rowptr, int32_t* colidx, double* vals, void* stream) {
+    int64_t nu = 0;
+    if (!logk || !rowptr || !colidx || !vals || !(kz_ratio > 0.0) ||
+        cpc_mhfem_size(nx, ny, nz, dirichlet_mask, &nu) < 0)
+        return CPC_EINVAL;
+    return guarded(nullptr, [&] {
+        cpc::mhfem_assemble(nx, ny, nz, logk, kz_ratio, dirichlet_mask, rowptr, colidx, vals, (cudaStream_t)stream);
+    });
+}
+
 int cpc_tpfa_gradient(int32_t nx, int32_t ny, int32_t nz, const double* logk, double kz_ratio,
                       int32_t dirichlet_mask, const double* lambda, const double* p, double* g, void* stream) {
     if (nx < 1 || ny < 1 || nz < 1 || !logk || !lambda || !p || !g || !(kz_ratio > 0.0)) return CPC_EINVAL;

@@ -111,6 +111,10 @@ void tpfa_gradient(int nx, int ny, int nz, const double* logk, double kzr, int d
 // setup.cu
 void tpfa_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask, int* rowptr,
                    int* col, double* val, cudaStream_t s);
+// Mixed-hybrid (p, lambda) system of Section 4 on unit bricks (mhfem.cu): sizes, then assembly.
+int64_t mhfem_size(int nx, int ny, int nz, int dmask, int64_t* nunk);
+void mhfem_assemble(int nx, int ny, int nz, const double* logk, double kzr, int dmask, int* rowptr, int* col,
+                    double* val, cudaStream_t s);
 void setup_handle(Handle& h, const cpc_csr& A);
 
 // batched.cu

@@ -1,5 +1,7 @@
 """The C ABI: the library builds for sm_103a, loads, and exports every entry point of include/cpc.h."""
 import ctypes
+
+import numpy as np
 import os
 import re
 
@@ -60,6 +62,12 @@ def test_pure_host_entry_points(lib):
     assert L.cpc_setup(None, None, ctypes.byref(h)) == 1 and not h.value
     assert L.cpc_solve(None, None, None, 1e-6, 10, None, None, 0) == 1
     L.cpc_destroy(None)
+    # mixed-hybrid sizes are host arithmetic: they must match the oracle's assembled system
+    import oracle as O
+    for shape, mask in [((3, 2, 2), 1), ((4, 3, 2), 0), ((2, 2, 2), 63), ((1, 1, 1), 3), ((5, 1, 3), 1 | 8 | 32)]:
+        nx, ny, nz = shape
+        A = O.mhfem(nx, ny, nz, np.zeros(nx * ny * nz), 0.1, mask)
+        assert cpc.mhfem_size(nx, ny, nz, mask) == (A.n, A.nnz)
     # option validation happens before any device work: a valid 1 x 1 host CSR with bad options
     rp, ci, va = (ctypes.c_int32 * 2)(0, 1), (ctypes.c_int32 * 1)(0), (ctypes.c_double * 1)(1.0)
     csr = cpc._Csr(1, 1, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(ci, ctypes.c_void_p),
