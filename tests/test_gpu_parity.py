@@ -226,6 +226,31 @@ def test_single_level_and_ragged_sizes():
         assert np.linalg.norm(x.cpu().numpy() - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
 
 
+@pytest.mark.parametrize("shape", [(16, 12, 8), (64, 1, 1), (32, 24, 1)])
+def test_even_width_grids(shape):
+    """Fine grids of even width (3-D, a 1-D line, a 2-D plane) in the diagonal form with the
+    red-black colour-ordered IC(0): applications, the fine sweep and PCG against the oracle."""
+    p = inputs.small_3d(*shape, seed=31)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=16, ic_colour_order=True)
+    s = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=16, ic_order="colour")
+    assert s.level_layout(0)["ndiag"] > 0
+    r = inputs.random_vector(A.n, seed=32)
+    rt = torch.tensor(r, device=DEV)
+    for which, op in [("bco", O.BCO), ("amg", O.STILDE), ("bhat", O.BHAT)]:
+        assert rel(s.apply(rt, which=which).cpu().numpy(), orc.apply(op, r)) < 1e-11
+    y = s.level_apply(0, 1, rt).cpu().numpy()
+    assert rel(y, orc.level_apply(0, 1, r)) < 1e-12
+    b = inputs.random_vector(A.n, seed=33)
+    ref = orc.pcg(b, op=O.BCO, tol=1e-10, maxit=300)
+    x, iters, status, _ = s.solve(torch.tensor(b, device=DEV), tol=1e-10, maxit=300)
+    assert status == 0 and abs(iters - ref["iters"]) <= 1
+    assert np.linalg.norm(x.cpu().numpy() - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    c = s.check_layouts()
+    assert c["out_of_range"] == 0 and c["gs_races"] == 0 and c["triangular_races"] == 0
+    s.close()
+
+
 def test_zero_rhs_and_maxit():
     p = inputs.small_3d(9, 8, 6, seed=1)
     A = O.tpfa_problem(p)
