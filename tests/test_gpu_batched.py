@@ -2,7 +2,7 @@
 
 Each column must reproduce the single-right-hand-side iteration: iteration counts within 1 and
 solutions within 1e-8 of the single solve (same algorithm, different reduction layout), within
-1e-8 of the oracle at tol 1e-10 (spec FP64 gate) and within 1e-5 with the FP32
+1e-8 of the oracle at tol 1e-10 (the FP64 parity gate) and within 1e-5 with the FP32
 preconditioner.  The adjoint half must equal single solves of A lambda = G, G = X on the source
 cells of each column.  At 128 x 128 x 64 with 64 right-hand sides every column must reach the
 tolerance on its true FP64 residual.

@@ -4,7 +4,7 @@ The GPU groups the rows of each smoothed level by their wavefront in the lower-t
 graph of A_l.  That grouping is integer data and must equal, row for row, the wavefronts computed
 here from the oracle's A_l (w(i) = 1 + max w(j) over coupled j < i, 0 when there is none).  Sweeps,
 V-cycles and every preconditioner must match the oracle built with gs_natural=True to 1e-11; PCG
-solves at tol 1e-10 agree to 1e-8 with equal iteration counts (spec FP64 gate), 1e-5 with the
+solves at tol 1e-10 agree to 1e-8 with equal iteration counts (the FP64 parity gate), 1e-5 with the
 FP32 preconditioner.  The natural order needs natural-order IC(0) and no cluster kernel; other
 combinations are rejected at setup.
 """

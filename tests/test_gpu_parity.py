@@ -4,7 +4,7 @@ Tolerances: structural choices (C/F splitting, colouring, sparsity patterns) mus
 identical; FP64 matrix values agree to 1e-12 relative (same formulas, summation in the
 same order; only rounding of fused multiply-adds differs); operator applications to
 1e-11; PCG solutions run to tol 1e-10 agree to 1e-8 relative with iteration counts
-within +-2 (spec parity gate), and every GPU solve reaches its tolerance on the
+within +-2 (the parity gate), and every GPU solve reaches its tolerance on the
 true FP64 residual.
 """
 import numpy as np
