@@ -519,7 +519,7 @@ def oracle_time(p, sample_iters=None):
 
 
 def reference_arm(args, rank, world):
-    """CPU oracle timed on the host cores (the reference arm for this build)."""
+    """CPU oracle timed on the host cores (the reference arm: the paper has no code of its own)."""
     import oracle as O
     if rank != 0:
         return

@@ -10,7 +10,7 @@
 //       smoother layout, whose rows one launch updates in parallel (Section 3.3);
 //   [3] triangular-solve races: an entry of the IC(0) factor whose row's level is not after its
 //       column's (forward levels for j < i, backward levels for j > i; Algorithm 3.1).
-// The checker bounds-checks every index before it uses one.
+// Every index is bounds-checked here before it is used.
 #include <vector>
 
 #include "handle.cuh"
