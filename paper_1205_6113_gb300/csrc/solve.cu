@@ -47,6 +47,16 @@ void with_u(int lanes, F&& f) {
     else f(std::integral_constant<int, 8>{});
 }
 
+// As with_u for the Gauss-Seidel colour steps, with batches of up to 16: a colour step lasts as long
+// as its widest chunk, and one batch per lane keeps it to one round of dependent gathers.  The
+// products are added in the same entry order whatever the batch, so the results do not change.
+template <class F>
+void with_u_gs(int lanes, F&& f) {
+    if (lanes <= 8) with_u(lanes, f);
+    else if (lanes <= 12) f(std::integral_constant<int, 12>{});
+    else f(std::integral_constant<int, 16>{});
+}
+
 // Calls f(std::integral_constant<int, ND>{}) with the padded diagonal count (4, 6 or 8).
 template <class F>
 void with_nd(int nd, F&& f) {
@@ -717,7 +727,7 @@ void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
         return;
     }
     const int g = blocks_for_chunks(c1 - c0);
-    with_u(L.S.lanes, [&](auto u) {
+    with_u_gs(L.S.lanes, [&](auto u) {
         constexpr int U = decltype(u)::value;
         if constexpr (std::is_same<VT, double>::value) {
             launch(k_gs<double, double, FT, VT, U>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), c0, c1, f, x);
