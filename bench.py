@@ -527,15 +527,13 @@ def reference_arm(args, rank, world):
     A = O.tpfa_problem(p)
     orc = O.Oracle(A)
     sample = 4
-    times, full_iters = [], None
-    for k in range(args.warmup + args.steps):
-        maxit = MAXIT if k == 0 else sample
+    full_iters = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=MAXIT)["iters"]     # untimed: the full count
+    times = []
+    for k in range(args.warmup + max(1, args.steps)):
         t = time.perf_counter()
-        r = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=maxit)
+        r = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=sample)
         dt = time.perf_counter() - t
-        if k == 0:
-            full_iters = r["iters"]
-        elif k >= args.warmup:
+        if k >= args.warmup:
             times.append(dt / r["iters"])
     per_it_ms = float(np.mean(times)) * 1e3
     value = per_it_ms * full_iters
