@@ -667,6 +667,10 @@ def main():
         "clocks": out["clocks"],
         "gpu_launches": launches,
         "launches_per_iteration": per_it,
+        "hierarchy": {"n": [int(l["n"]) for l in out["levels"]], "nnz": [int(l["nnz"]) for l in out["levels"]],
+                      "colours": [int(l["ncolours"]) for l in out["levels"][:-1]],
+                      "operator_complexity": round(sum(l["nnz"] for l in out["levels"]) / out["levels"][0]["nnz"], 3),
+                      "grid_complexity": round(sum(l["n"] for l in out["levels"]) / out["levels"][0]["n"], 3)},
     }
     if not args.no_cpu_baseline and world == 1:
         _, r, setup_s, solve_s = oracle_time(p)
