@@ -4,7 +4,9 @@
 //
 // Kernel layout: every matrix is SELL-C (C in {32, 16, 8, 4}): one warp per chunk of C rows with
 // 32 / C lanes per row, entries column-major inside a chunk so that each load instruction of a
-// warp reads 32 consecutive elements.
+// warp reads 32 consecutive elements.  On a structured fine grid the diagonal form (one thread per
+// row, no column indices) replaces SELL for the fine-level kernels.  Every kernel is launched with
+// programmatic dependent launch and loads its matrix data before waiting for its predecessor.
 // Reductions (dot products) finish in a fixed order (per-block tree, then the last block sums the
 // block partials in index order), so iteration counts are reproducible run to run.
 #include <algorithm>
