@@ -48,8 +48,8 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // loads in flight instead of a chain of dependent ones.  Padding (col < 0) is skipped without a
 // load.  Products are added in entry order.  The caller picks U >= the most entries a lane holds
 // (4, 6 or 8, and 12 or 16 for the Gauss-Seidel colour steps; Sell::lanes), so one batch covers a
-// row and no product is spent on padding beyond
-// the chunk width -- FP64 issue rate is scarce on this part.  With WAIT, the first batch of the
+// row and no product is spent on padding beyond the chunk width -- FP64 issue rate is scarce on
+// this part.  With WAIT, the first batch of the
 // matrix row is loaded before pdl_wait() and the vector only after it; after_wait() runs right
 // after the wait, so that loads the caller issues there overlap the gathers.
 struct NoHook {
