@@ -543,7 +543,8 @@ def reference_arm(args, rank, world):
             "impl": "reference",
             "config": {"workload": WORKLOAD, "n": p.n, "nnz": A.nnz, "precond": "B_co", "tol": TOL,
                        "l2": "cpu"},
-            "cpu_baseline": {"value": round(value, 2), "unit": "ms", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 2), "unit": "ms", "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle",
                              "sample": "each step: %d B_co PCG iterations of the oracle on the %s matrix, "
                                        "scaled by its full iteration count (%d)" % (sample, WORKLOAD, full_iters)},
             "e2e": {"value": round(value, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -674,7 +675,8 @@ def main():
     }
     if not args.no_cpu_baseline and world == 1:
         _, r, setup_s, solve_s = oracle_time(p)
-        line["cpu_baseline"] = {"value": round(solve_s * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": round(solve_s * 1e3, 1), "unit": "ms", "cores": 1,
+                                "host_cores": os.cpu_count(), "kind": "oracle",
                                 "sample": "one full B_co PCG solve (%d iterations) of the %s matrix on one host "
                                           "core, solve phase only (oracle setup %.1f s excluded)"
                                           % (r["iters"], WORKLOAD, setup_s),

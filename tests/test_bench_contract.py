@@ -20,5 +20,5 @@ def test_reference_arm_json_line():
     assert line["value"] > 0 and line["value"] == line["ms_per_step"]
     assert line["config"]["workload"] == "correlated3d_128x128x64"
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["host_cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
