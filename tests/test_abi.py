@@ -68,6 +68,11 @@ def test_pure_host_entry_points(lib):
         nx, ny, nz = shape
         A = O.mhfem(nx, ny, nz, np.zeros(nx * ny * nz), 0.1, mask)
         assert cpc.mhfem_size(nx, ny, nz, mask) == (A.n, A.nnz)
+    nu = ctypes.c_int64(0)
+    assert L.cpc_mhfem_size(1024, 1024, 1024, 1, ctypes.byref(nu)) == -1      # 2^30 cells: nnz over int32
+    assert L.cpc_mhfem_size(0, 4, 4, 1, ctypes.byref(nu)) == -1
+    assert L.cpc_mhfem_size(4, 4, 4, 1, None) == -1
+    assert L.cpc_mhfem_assemble(4, 4, 4, None, 0.1, 1, None, None, None, None) == 1
     # option validation happens before any device work: a valid 1 x 1 host CSR with bad options
     rp, ci, va = (ctypes.c_int32 * 2)(0, 1), (ctypes.c_int32 * 1)(0), (ctypes.c_double * 1)(1.0)
     csr = cpc._Csr(1, 1, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(ci, ctypes.c_void_p),
