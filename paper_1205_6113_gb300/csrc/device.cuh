@@ -2,6 +2,8 @@
 // batched SELL row product.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cpc {
@@ -43,15 +45,51 @@ inline SV<MT, DT> view(const Sell& S, const MT* val, const DT* diag) {
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// sum_w val[o_w] * x[col[o_w]] over one SELL row (entries o = o0, o0+32, ... < e).  U column
-// indices and values are loaded first, then the U gathers, so that each thread keeps U independent
-// loads in flight instead of a chain of dependent ones.  Padding (col < 0) is skipped without a
-// load.  Products are added in entry order.  The caller picks U >= the most entries a lane holds
-// (4, 6 or 8, and 12 or 16 for the Gauss-Seidel colour steps; Sell::lanes), so one batch covers a
-// row and no product is spent on padding beyond the chunk width -- FP64 issue rate is scarce on
-// this part.  With WAIT, the first batch of the
-// matrix row is loaded before pdl_wait() and the vector only after it; after_wait() runs right
-// after the wait, so that loads the caller issues there overlap the gathers.
+// One batch of exactly M entries per lane (entries o, o + 32, ... with oo < e; the others load
+// nothing and add 0): loads, then (WAIT) the wait and the caller's hook, then the gathers, then the
+// products in entry order.
+template <int M, bool WAIT, class VT, class MT, class XT, class H>
+__device__ __forceinline__ void sell_batch(const int* __restrict__ col, const MT* __restrict__ val, int o, int e,
+                                           const XT* x, VT& acc, H& after_wait) {
+    int c[M];
+    VT v[M], xv[M];
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        const int oo = o + u * 32;
+        c[u] = oo < e ? col[oo] : -1;
+        v[u] = oo < e ? Cv<VT>::f(val[oo]) : VT(0);
+    }
+    if (WAIT) {
+        pdl_wait();
+        after_wait();           // the caller's own loads of predecessor data, in flight with the gathers
+    }
+#pragma unroll
+    for (int u = 0; u < M; ++u) xv[u] = c[u] >= 0 ? Cv<VT>::f(x[c[u]]) : VT(0);
+#pragma unroll
+    for (int u = 0; u < M; ++u) acc += v[u] * xv[u];
+}
+
+template <int M, bool WAIT, int U, class VT, class MT, class XT, class H>
+__device__ __forceinline__ void sell_batch_of(int m, const int* __restrict__ col, const MT* __restrict__ val, int o,
+                                              int e, const XT* x, VT& acc, H& after_wait) {
+    if constexpr (M <= U) {
+        if (m == M) sell_batch<M, WAIT>(col, val, o, e, x, acc, after_wait);
+        else sell_batch_of<M + 1, WAIT, U>(m, col, val, o, e, x, acc, after_wait);
+    }
+}
+
+// sum_w val[o_w] * x[col[o_w]] over one SELL row (entries o = o0, o0+32, ... < e) of the chunk
+// that the calling warp owns.  Entries are taken in batches: each lane loads a batch's column indices
+// and values first, then its gathers, so it keeps the batch's loads in flight instead of a chain of
+// dependent ones.  A batch holds m <= U entries per lane, m = the chunk's entries per lane left
+// (the same for the whole warp, from the chunk start that lane 0 holds): a narrow chunk issues no
+// loads and, above all, no FP64 products for padding, and FP64 issue is scarce on this part (FP32
+// arithmetic keeps full batches of U, masked per lane: fewer registers, no dispatch).  Lanes
+// with fewer entries than m load nothing for the extra ones and add 0.  Products are added in entry
+// order.  U (4, 6 or 8, and 12 or 16 for the Gauss-Seidel colour steps) is at least the widest
+// chunk's entries per lane (Sell::lanes), so one batch usually covers a row.  With WAIT, the first
+// batch's matrix data is loaded before pdl_wait() and the vector only after it; after_wait() runs
+// right after the wait, so that loads the caller issues there overlap the gathers.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
@@ -60,36 +98,32 @@ template <class VT, bool WAIT = false, int U = 8, class MT, class XT, class H = 
 __device__ __forceinline__ VT sell_dot(const int* __restrict__ col, const MT* __restrict__ val, int o, int e,
                                        const XT* x, H&& after_wait = H{}) {
     VT acc = VT(0);
-    if (WAIT) {
-        int c[U];
-        VT v[U], xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int oo = o + u * 32;
-            c[u] = oo < e ? col[oo] : -1;
-            v[u] = oo < e ? Cv<VT>::f(val[oo]) : VT(0);
+    if constexpr (!std::is_same<VT, double>::value) {
+        // FP32 arithmetic is not short of issue slots: full batches of U, masked per lane (fewer
+        // registers and no dispatch on the batch size)
+        if (WAIT) {
+            sell_batch<U, true>(col, val, o, e, x, acc, after_wait);
+            o += U * 32;
         }
-        pdl_wait();
-        after_wait();           // the caller's own loads of predecessor data, in flight with the gathers
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? Cv<VT>::f(x[c[u]]) : VT(0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc += v[u] * xv[u];
-        o += U * 32;
+        for (; o < e; o += U * 32) sell_batch<U, false>(col, val, o, e, x, acc, after_wait);
+        return acc;
     }
-    for (; o < e; o += U * 32) {
-        int c[U];
-        VT v[U], xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int oo = o + u * 32;
-            c[u] = oo < e ? col[oo] : -1;
-            v[u] = oo < e ? Cv<VT>::f(val[oo]) : VT(0);
+    const int cb = __shfl_sync(0xffffffffu, o, 0);            // lane 0: sub-lane 0, row 0 of the chunk
+    int left = (e - cb + 31) >> 5;                              // entries per lane, warp-uniform
+    if (WAIT) {
+        const int m = left < U ? left : U;
+        if (m == 0) {
+            pdl_wait();
+            after_wait();
+        } else {
+            sell_batch_of<1, true, U>(m, col, val, o, e, x, acc, after_wait);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? Cv<VT>::f(x[c[u]]) : VT(0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc += v[u] * xv[u];
+        o += U * 32;
+        left -= U;
+    }
+    for (; left > 0; o += U * 32, left -= U) {
+        const int m = left < U ? left : U;
+        sell_batch_of<1, false, U>(m, col, val, o, e, x, acc, after_wait);
     }
     return acc;
 }
