@@ -333,6 +333,31 @@ def gpu_arm(args, rank, world):
         sname = "k_spmv (fine A, SELL-32, FP64)"
     spmv = dict(kernel=sname, bytes_per_launch=sbytes, avg_launch_ms=round(float(np.mean(sms)), 5),
                 achieved=round(sbytes / (np.mean(sms) * 1e-3) / 1e9, 1))
+    # the coarse colour steps (the largest share of kernel time): one forward sweep per level timed
+    # live; algorithmic bytes per sweep = 12 B per off-diagonal entry + 28 B per row (1 / a_ii,
+    # slot -> row, f, x written, x read); these steps are bound by dependent-launch latency
+    coarse = []
+    for l in range(1, s_bco.nlevels - 1):
+        inf = s_bco.level_info(l)
+        xl = torch.randn(inf["n"], dtype=torch.float64, device=dev)
+        yl = torch.zeros_like(xl)
+        for _ in range(3):
+            s_bco.level_apply(l, 1, xl, yl)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            s_bco.level_apply(l, 1, xl, yl)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sweep_ms = e0.elapsed_time(e1) / reps
+        nbytes = 12 * (inf["nnz"] - inf["n"]) + 28 * inf["n"]
+        coarse.append(dict(level=l, n=inf["n"], colours=inf["ncolours"],
+                           us_per_step=round(sweep_ms * 1e3 / inf["ncolours"], 2),
+                           achieved=round(nbytes / (sweep_ms * 1e-3) / 1e9, 1)))
+    coarse_gs = dict(kernel="k_gs (coarse colour steps, FP64, one forward sweep per level)", bound="latency",
+                     unit="GB/s", levels=coarse)
     bpi = bytes_per_iteration(s_bco, "bco")
     headline_ms = float(np.mean(ms))
     out.update(dict(p=p, arms=arms, clocks=clk, e2e_ms=e2e_ms, true_res=true_res, setups=setups,
@@ -340,7 +365,7 @@ def gpu_arm(args, rank, world):
                                   frac=round(achieved / peak, 4), traffic=TRAFFIC_K_GS_FINE,
                                   kernel=kname,
                                   bytes_per_launch=kbytes, avg_launch_ms=round(k_avg, 5), peak_kind=peak_kind,
-                                  spmv=spmv),
+                                  spmv=spmv, coarse_gs=coarse_gs),
                     headline_ms=headline_ms, bytes_per_iter=bpi, nodes=None, nlevels=s_bco.nlevels,
                     levels=[s_bco.level_info(l) for l in range(s_bco.nlevels)]))
     out["solve_gbs"] = bpi * iters[-1] / (headline_ms * 1e-3) / 1e9
