@@ -255,6 +255,50 @@ def test_splitting_and_interpolation_invariants(small3d):
                 assert np.count_nonzero(P[i]) > 0
 
 
+@pytest.mark.parametrize("shape,seed", [((4, 3, 2), 61), ((5, 4, 3), 62)])
+def test_direct_interpolation_with_positive_couplings(shape, seed):
+    """The positive-coupling branch of direct interpolation (Section 3.2 reading: positive
+    off-diagonals lumped into the diagonal), pinned on the mixed-hybrid matrix, whose face rows
+    couple positively to the opposite faces of each cell.  Two facts fix the weights of an F row
+    i with interpolation set C_i, whatever formula produced them:
+    (a) they are proportional to the couplings: P_ij / P_ik = a_ij / a_ik for j, k in C_i;
+    (b) smooth error satisfies (A e)_i ~ 0 with positive neighbours taken at e_i and the negative
+        ones averaged over C_i, so where A annihilates constants (zero row sum, no Dirichlet face)
+        constants are interpolated exactly: sum_j P_ij = 1.  (Rows next to a Dirichlet face have
+        lost a coupling and a nonzero row sum; (a) still holds there.)
+    A sign slip in the lumped diagonal, a dropped positive term, or positive entries counted
+    among the negative ones breaks (b) on rows that have positive couplings; this test checks
+    that such rows exist and are F rows with nonempty interpolation."""
+    p = inputs.small_3d(*shape, seed=seed)
+    A = O.mhfem(p.nx, p.ny, p.nz, p.logk, p.kz_ratio, p.dirichlet)
+    orc = O.Oracle(A, coarse_max=8)
+    assert orc.nlevels >= 2
+    D = A.to_dense()
+    S = strength_dense(D, 0.25)
+    cf, _ = orc.level_cf_colour(0)
+    P = orc.level_P(0).to_dense()
+    cidx = np.cumsum(cf == 1) - 1
+    checked = 0
+    for i in np.where(cf == 0)[0]:
+        off = np.delete(D[i], i)
+        if not (off > 0).any():
+            continue
+        interp = np.where(S[i] & (cf == 1))[0]
+        w = P[i, cidx[interp]]
+        if len(interp) == 0:
+            assert not P[i].any()
+            continue
+        assert np.count_nonzero(P[i]) == len(interp)
+        # (a) proportional to the couplings (all negative: strength is on -a_ij)
+        assert np.all(D[i, interp] < 0) and np.all(w > 0)
+        assert np.allclose(w / w.sum(), D[i, interp] / D[i, interp].sum(), rtol=1e-13, atol=0)
+        # (b) constants on rows that annihilate them
+        if abs(D[i].sum()) <= 1e-13 * D[i, i]:
+            assert abs(w.sum() - 1.0) < 1e-13, i
+            checked += 1
+    assert checked >= 10
+
+
 def test_colouring_is_proper(small3d):
     _, _, orc, _ = small3d
     for l in range(orc.nlevels - 1):
