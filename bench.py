@@ -2,9 +2,12 @@
 
 Headline (``value``): milliseconds per combined-preconditioned (B_co) PCG solve, FP64, on the
 128 x 128 x 64 correlated-lognormal two-point-flux matrix (1,048,576 unknowns), inputs resident
-in HBM.  The same run times the AMG-alone (S~, two V-cycles) and IC(0)-alone preconditioners and
-the FP32 / FP32+BF16 preconditioner variants, the end-to-end solve through host buffers, the
-dominant kernel against the measured HBM roofline, and the CPU oracle as a reported baseline.
+in HBM.  The same run times, per matrix (the 64 x 64 plane, the 1M-unknown correlated field, the
+256 x 256 x 128 channel field and the mixed-hybrid system), B_co against AMG alone (S~, two
+V-cycles) and IC(0) alone, FP64 and with the FP32 preconditioner; the end-to-end solve through
+host buffers; the error of the FP64 and FP32-preconditioned solutions against the FP64 oracle;
+the dominant kernel against the measured HBM roofline; and the CPU oracle as a reported baseline
+(one core, and OpenMP over the host's cores).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -38,6 +41,9 @@ L2_FLUSH_BYTES = 512 << 20
 # committed ncu capture (profiles/k_gs_pk_fine_correlated3d_128x128x64.md); None until a capture
 # of the current kernel exists.
 TRAFFIC_K_GS_FINE = 48355584
+# The same for one forward sweep of every coarse level (the k_gs launches of the sweep, summed);
+# None until a capture of the current hierarchy exists.
+TRAFFIC_COARSE_SWEEP = None
 
 
 def peaks():
@@ -185,10 +191,11 @@ def gpu_arm(args, rank, world):
             import torch.distributed as dist
             dist.barrier()
 
-    def time_solves(solver, steps, warmup, tol=TOL):
+    def time_solves(solver, steps, warmup, tol=TOL, rhs=None):
+        rhs = b if rhs is None else rhs
         iters = []
         for _ in range(warmup):
-            _, it, st, _ = solver.solve(b, tol=tol, maxit=MAXIT, hist=False)
+            _, it, st, _ = solver.solve(rhs, tol=tol, maxit=MAXIT, hist=False)
             if st != 0:
                 raise SolveFailed(st, it)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -198,7 +205,7 @@ def gpu_arm(args, rank, world):
         for k in range(steps):
             flush_l2()
             ev[k][0].record(stream)
-            _, it, st, _ = solver.solve(b, tol=tol, maxit=MAXIT, hist=False)
+            _, it, st, _ = solver.solve(rhs, tol=tol, maxit=MAXIT, hist=False)
             ev[k][1].record(stream)
             if st != 0:
                 raise SolveFailed(st, it)
@@ -238,10 +245,11 @@ def gpu_arm(args, rank, world):
     xh = x_host.numpy()
     true_res = float(np.linalg.norm(p.rhs() - csr_matvec(rowptr, col, val, xh)) / np.linalg.norm(p.rhs()))
 
-    # comparison arms (fewer steps: AMG-alone and IC(0)-alone)
-    arms = {}
+    # comparison arms on the benchmark matrix: every preconditioner and precision
     # (name, preconditioner, precision, IC(0) order, Gauss-Seidel order, timed solves)
-    for name, pre, prec, ico, gso, k in [
+    arms = {}
+    if world == 1:
+        arms = compare_matrix(cpc, (rowptr, col, val), b, p.rhs(), time_solves, [
             ("amg_fp64", "amg", "fp64", "natural", "multicolour", args.steps),
             ("ic0_fp64", "ic0", "fp64", "natural", "multicolour", 2),
             ("ic0_rbic_fp64", "ic0", "fp64", "colour", "multicolour", 2),
@@ -251,71 +259,67 @@ def gpu_arm(args, rank, world):
             ("amg_ilu_fp64", "amg_ilu", "fp64", "colour", "multicolour", args.steps),
             ("bco_fp32", "bco", "fp32", "colour", "multicolour", args.steps),
             ("bco_fp32_bf16", "bco", "fp32_bf16", "colour", "multicolour", args.steps),
-            ("amg_fp32", "amg", "fp32", "natural", "multicolour", args.steps)]:
-        if world > 1:
-            continue
-        t = time.perf_counter()
-        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order=ico, gs_order=gso)
-        setup = dict(zip(("ic0_ms", "amg_ms"), s.setup_time_ms()))
-        setup["wall_ms"] = (time.perf_counter() - t) * 1e3
-        try:
-            slow = name in ("ic0_fp64", "ic0_rbic_fp64", "bco_natgs_fp64")      # one warm-up solve
-            m, it, _ = time_solves(s, k, 1 if slow else args.warmup)
-        except SolveFailed as e:                 # AMG(ILU(0)) need not be SPD (Section 5): record it
-            arms[name] = dict(ms=None, iters=e.iters, status=e.status, setup=setup)
-            s.close()
-            continue
-        x, _, _, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
-        xr = x.cpu().numpy()
-        arms[name] = dict(ms=round(float(np.mean(m)), 3), iters=int(it[-1]), setup=setup,
-                          true_res=float(np.linalg.norm(p.rhs() - csr_matvec(rowptr, col, val, xr)) / np.linalg.norm(p.rhs())),
-                          hbm_frac_solve=None)
-        bpi = bytes_per_iteration(s, pre, sv=8 if prec == "fp64" else 4, sx=8 if prec == "fp64" else 4,
-                                  sv_coarse=(2 if prec == "fp32_bf16" else None))
-        arms[name]["gbs_solve"] = round(bpi * it[-1] / (np.mean(m) * 1e-3) / 1e9, 1)
-        s.close()
+            ("amg_fp32", "amg", "fp32", "natural", "multicolour", args.steps)], args)
+
+    # the same three-way comparison on the other matrices: the 64 x 64 plane (the plain method),
+    # the 256 x 256 x 128 channel field (1000:1 contrast, k_z / k = 0.01) and the mixed-hybrid
+    # system of the 128 x 128 x 64 field
+    matrices = {}
+    if world == 1 and not args.no_matrices:
+        matrices = other_matrices(cpc, dev, time_solves, args)
 
     # batched: 64 right-hand sides and their adjoints in one graph, FP32 preconditioner
     if world == 1 and not args.no_batched:
         out["batched"] = batched_arm(rowptr, col, val, p, dev, stream, args)
 
-    # the mixed-hybrid system of the same grid (second matrix family), assembled on the device
-    if world == 1 and not args.no_mhfem:
-        out["mhfem"] = mhfem_arm(p, dev, stream, args)
-
     # differentiable solve on the 256 x 256 x 128 channel problem: gradient of the well misfit
     if world == 1 and not args.no_adjoint:
         out["adjoint"] = adjoint_arm(dev, stream)
 
-    # dominant kernel (k_gs, the Gauss-Seidel colour sweep: largest share of the ncu launch list):
-    # its fine-level launches timed live -- one red and one black launch per event pair, L2 flushed.
-    # Algorithmic bytes per launch: half of (24 n + 12 nnz) = the colour's rows of A (values,
-    # columns), diagonal, perm, f, x written, and the other colour's x read once.
-    xv = torch.randn(p.n, dtype=torch.float64, device=dev)
-    yv = torch.zeros_like(xv)
+    # solutions of the FP64 and the FP32-preconditioned solver at tol 1e-10, for the comparison with
+    # the FP64 oracle (made after the GPU part)
+    xs = {}
+    if world == 1 and not args.no_cpu_baseline:
+        for prec in ("fp64", "fp32"):
+            s = s_bco if prec == "fp64" else cpc.Solver(rowptr, col, val, precond="bco", precision=prec,
+                                                          ic_order="colour")
+            x, it, st, _ = s.solve(b, tol=1e-10, maxit=MAXIT, hist=False)
+            xs[prec] = dict(x=x.cpu().numpy(), iters=it, status=st)
+            if s is not s_bco:
+                s.close()
+
+    # the dominant kernels, timed live on the solver's stream:
+    # (1) the coarse-level Gauss-Seidel colour steps (k_gs; the largest share of the solve's kernel
+    #     time): one forward sweep per coarse level replayed from a CUDA graph as in the solve.
+    #     Algorithmic bytes per sweep: 12 B per off-diagonal entry (value, column) + 28 B per row
+    #     (1 / a_ii, slot -> row, f read, x written, x read once).
+    peak, peak_kind = peaks()
+    coarse, cbytes, cus = [], 0, 0.0
+    for l in range(1, s_bco.nlevels - 1):
+        inf = s_bco.level_info(l)
+        us = s_bco.sweep_time_us(l, reps=20)
+        nbytes = 12 * (inf["nnz"] - inf["n"]) + 28 * inf["n"]
+        cbytes += nbytes
+        cus += us
+        coarse.append(dict(level=l, n=inf["n"], colours=inf["ncolours"], us_per_sweep=round(us, 2),
+                           us_per_step=round(us / inf["ncolours"], 2), achieved=round(nbytes / (us * 1e-6) / 1e9, 1)))
+    coarse_achieved = cbytes / (cus * 1e-6) / 1e9
+    # (2) the fine-level colour step (k_gs_pk): one red + one black launch per sweep
     info0 = s_bco.level_info(0)
-    for _ in range(3):
-        s_bco.level_apply(0, 5, xv, yv)
-    kms = []
-    for _ in range(20):
-        flush_l2()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s_bco.level_apply(0, 5, xv, yv)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        kms.append(e0.elapsed_time(e1) / info0["ncolours"])
     lay0 = s_bco.level_layout(0)
+    fine_us = s_bco.sweep_time_us(0, reps=20) / info0["ncolours"]
     if lay0["ndiag"]:       # per row: nd diagonals, 1/a_ii, slot -> row, f_i, x_i written, the other colour's x once
         kbytes = info0["n"] * (8 * lay0["ndiag"] + 36) // info0["ncolours"]
-        kname = "k_gs_pk (Gauss-Seidel colour sweep, fine level, red/black, per-slot diagonal records, FP64)"
+        kname = "k_gs_pk (Gauss-Seidel colour step, fine level, red/black, per-slot diagonal records, FP64)"
     else:                   # per row / entry: SELL values + columns, 1/a_ii, f_i, x_i
         kbytes = (24 * info0["n"] + 12 * info0["nnz"]) // info0["ncolours"]
-        kname = "k_gs (Gauss-Seidel colour sweep, fine level, red/black, SELL, FP64)"
-    peak, peak_kind = peaks()
-    k_avg = float(np.mean(kms))
-    achieved = kbytes / (k_avg * 1e-3) / 1e9
-    # the fine SpMV (same SELL layout), for reference
+        kname = "k_gs (Gauss-Seidel colour step, fine level, red/black, SELL, FP64)"
+    fine = dict(kernel=kname, bytes_per_launch=kbytes, avg_launch_ms=round(fine_us * 1e-3, 5),
+                achieved=round(kbytes / (fine_us * 1e-6) / 1e9, 1),
+                frac=round(kbytes / (fine_us * 1e-6) / 1e9 / peak, 4), traffic=TRAFFIC_K_GS_FINE)
+    # (3) the fine SpMV of PCG (one launch per event pair, L2 flushed)
+    xv = torch.randn(p.n, dtype=torch.float64, device=dev)
+    yv = torch.zeros_like(xv)
     sms = []
     for _ in range(20):
         flush_l2()
@@ -332,44 +336,110 @@ def gpu_arm(args, rank, world):
         sbytes = a_pass_bytes(info0["n"], info0["nnz"])
         sname = "k_spmv (fine A, SELL-32, FP64)"
     spmv = dict(kernel=sname, bytes_per_launch=sbytes, avg_launch_ms=round(float(np.mean(sms)), 5),
-                achieved=round(sbytes / (np.mean(sms) * 1e-3) / 1e9, 1))
-    # the coarse colour steps (the largest share of kernel time): one forward sweep per level timed
-    # live; algorithmic bytes per sweep = 12 B per off-diagonal entry + 28 B per row (1 / a_ii,
-    # slot -> row, f, x written, x read); these steps are bound by dependent-launch latency
-    coarse = []
-    for l in range(1, s_bco.nlevels - 1):
-        inf = s_bco.level_info(l)
-        xl = torch.randn(inf["n"], dtype=torch.float64, device=dev)
-        yl = torch.zeros_like(xl)
-        for _ in range(3):
-            s_bco.level_apply(l, 1, xl, yl)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 20
-        e0.record(stream)
-        for _ in range(reps):
-            s_bco.level_apply(l, 1, xl, yl)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sweep_ms = e0.elapsed_time(e1) / reps
-        nbytes = 12 * (inf["nnz"] - inf["n"]) + 28 * inf["n"]
-        coarse.append(dict(level=l, n=inf["n"], colours=inf["ncolours"],
-                           us_per_step=round(sweep_ms * 1e3 / inf["ncolours"], 2),
-                           achieved=round(nbytes / (sweep_ms * 1e-3) / 1e9, 1)))
-    coarse_gs = dict(kernel="k_gs (coarse colour steps, FP64, one forward sweep per level)", bound="latency",
-                     unit="GB/s", levels=coarse)
+                achieved=round(sbytes / (np.mean(sms) * 1e-3) / 1e9, 1),
+                frac=round(sbytes / (np.mean(sms) * 1e-3) / 1e9 / peak, 4))
     bpi = bytes_per_iteration(s_bco, "bco")
     headline_ms = float(np.mean(ms))
-    out.update(dict(p=p, arms=arms, clocks=clk, e2e_ms=e2e_ms, true_res=true_res, setups=setups,
-                    roofline=dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
-                                  frac=round(achieved / peak, 4), traffic=TRAFFIC_K_GS_FINE,
-                                  kernel=kname,
-                                  bytes_per_launch=kbytes, avg_launch_ms=round(k_avg, 5), peak_kind=peak_kind,
-                                  spmv=spmv, coarse_gs=coarse_gs),
-                    headline_ms=headline_ms, bytes_per_iter=bpi, nodes=None, nlevels=s_bco.nlevels,
-                    levels=[s_bco.level_info(l) for l in range(s_bco.nlevels)]))
+    roofline = dict(bound="hbm", achieved=round(coarse_achieved, 1), peak=peak, unit="GB/s",
+                    frac=round(coarse_achieved / peak, 4), traffic=TRAFFIC_COARSE_SWEEP,
+                    kernel="k_gs (Gauss-Seidel colour steps of the coarse levels 1..%d, FP64): one forward sweep per "
+                           "level, aggregated; dependent-launch latency bounds these steps" % (s_bco.nlevels - 2),
+                    bytes_per_sweep=int(cbytes), us_per_sweep=round(cus, 2), peak_kind=peak_kind, levels=coarse,
+                    fine_gs=fine, spmv=spmv)
+    out.update(dict(p=p, arms=arms, matrices=matrices, clocks=clk, e2e_ms=e2e_ms, true_res=true_res,
+                    setups=setups, roofline=roofline, headline_ms=headline_ms, bytes_per_iter=bpi, xs=xs,
+                    nlevels=s_bco.nlevels, levels=[s_bco.level_info(l) for l in range(s_bco.nlevels)]))
     out["solve_gbs"] = bpi * iters[-1] / (headline_ms * 1e-3) / 1e9
     out["launches"] = s_bco.solve_launches()
+    return out
+
+
+def compare_matrix(cpc, csr, b, b_host, time_solves, configs, args, bytes_fn=True):
+    """Times each (name, preconditioner, precision, IC(0) order, Gauss-Seidel order, solves) on one
+    matrix; records ms, iterations, setup and the true FP64 residual of the last solve."""
+    import torch
+    rowptr, col, val = csr
+    res = {}
+    for name, pre, prec, ico, gso, k in configs:
+        t = time.perf_counter()
+        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order=ico, gs_order=gso)
+        torch.cuda.synchronize()
+        setup = dict(zip(("ic0_ms", "amg_ms"), [round(v, 2) for v in s.setup_time_ms()]))
+        setup["wall_ms"] = round((time.perf_counter() - t) * 1e3, 1)
+        try:
+            slow = pre == "ic0" or gso == "natural"
+            m, it, _ = time_solves(s, k, 1 if slow else args.warmup, rhs=b)
+        except SolveFailed as e:                 # AMG(ILU(0)) need not be SPD (Section 5): record it
+            res[name] = dict(ms=None, iters=e.iters, status=e.status, setup=setup)
+            s.close()
+            continue
+        x, _, _, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
+        xr = x.cpu().numpy()
+        res[name] = dict(ms=round(float(np.mean(m)), 3), iters=int(it[-1]), setup=setup,
+                         true_res=float(np.linalg.norm(b_host - csr_matvec(rowptr, col, val, xr)) / np.linalg.norm(b_host)))
+        if bytes_fn:
+            bpi = bytes_per_iteration(s, pre, sv=8 if prec == "fp64" else 4, sx=8 if prec == "fp64" else 4,
+                                      sv_coarse=(2 if prec == "fp32_bf16" else None))
+            res[name]["gbs_solve"] = round(bpi * it[-1] / (np.mean(m) * 1e-3) / 1e9, 1)
+        s.close()
+    return res
+
+
+def verdict(r):
+    """Which of B_co, AMG alone and IC(0) alone (FP64) reaches 1e-6 first, and B_co's margin."""
+    cand = {k: v["ms"] for k, v in r.items() if k in ("bco_fp64", "amg_fp64", "ic0_fp64", "ic0_rbic_fp64")
+            and v.get("ms") is not None}
+    if "bco_fp64" not in cand:
+        return None
+    best = min(cand, key=cand.get)
+    others = {k: v for k, v in cand.items() if k != "bco_fp64"}
+    runner = min(others, key=others.get) if others else None
+    return dict(fastest=best, bco_vs_best_other=round(others[runner] / cand["bco_fp64"], 3) if runner else None,
+                best_other=runner)
+
+
+def other_matrices(cpc, dev, time_solves, args):
+    import torch
+    out = {}
+    three_way = lambda k, ic_natural=True: [
+        ("bco_fp64", "bco", "fp64", "colour", "multicolour", k),
+        ("amg_fp64", "amg", "fp64", "natural", "multicolour", k),
+        ("ic0_rbic_fp64", "ic0", "fp64", "colour", "multicolour", 1)] + (
+        [("ic0_fp64", "ic0", "fp64", "natural", "multicolour", 1)] if ic_natural else []) + [
+        ("bco_natic_fp64", "bco", "fp64", "natural", "multicolour", max(1, min(k, 3))),
+        ("bco_fp32", "bco", "fp32", "colour", "multicolour", k),
+        ("amg_fp32", "amg", "fp32", "natural", "multicolour", k)]
+    # 64 x 64 plane: the plain method
+    p1 = inputs.lognormal_2d()
+    csr = cpc.tpfa_assemble(p1.nx, p1.ny, p1.nz, torch.tensor(p1.logk, device=dev), p1.kz_ratio, p1.dirichlet)
+    r = compare_matrix(cpc, csr, torch.tensor(p1.rhs(), device=dev), p1.rhs(), time_solves, three_way(args.steps),
+                       args, bytes_fn=False)
+    out["lognormal2d_64x64"] = dict(n=p1.n, results=r, verdict=verdict(r))
+    # 256 x 256 x 128 channel field (natural-order IC(0) alone left out: 638 wavefronts per
+    # triangular solve and thousands of iterations)
+    p4 = inputs.channel_facies()
+    csr = cpc.tpfa_assemble(p4.nx, p4.ny, p4.nz, torch.tensor(p4.logk, device=dev), p4.kz_ratio, p4.dirichlet)
+    r = compare_matrix(cpc, csr, torch.tensor(p4.rhs(), device=dev), p4.rhs(), time_solves,
+                       three_way(max(1, min(args.steps, 3)), ic_natural=False), args, bytes_fn=False)
+    out["channels3d_256x256x128"] = dict(n=p4.n, results=r, verdict=verdict(r))
+    del csr
+    # mixed-hybrid (p, lambda) system of the 128 x 128 x 64 field, assembled on the device
+    p2 = inputs.correlated_3d()
+    lk = torch.tensor(p2.logk, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cpc.mhfem_assemble(p2.nx, p2.ny, p2.nz, lk, p2.kz_ratio, p2.dirichlet)
+    torch.cuda.synchronize()
+    e0.record()
+    csr = cpc.mhfem_assemble(p2.nx, p2.ny, p2.nz, lk, p2.kz_ratio, p2.dirichlet)
+    e1.record()
+    torch.cuda.synchronize()
+    nu = int(csr[0].shape[0]) - 1
+    bh = np.zeros(nu)
+    bh[:p2.n] = p2.rhs()
+    r = compare_matrix(cpc, csr, torch.tensor(bh, device=dev), bh, time_solves,
+                       three_way(max(1, min(args.steps, 3)), ic_natural=False), args, bytes_fn=False)
+    out["correlated3d_128x128x64_mhfem"] = dict(n=nu, nnz=int(csr[1].shape[0]), assembly_ms=round(e0.elapsed_time(e1), 3),
+                                                 results=r, verdict=verdict(r))
     return out
 
 
@@ -432,47 +502,6 @@ def batched_arm(rowptr, col, val, p, dev, stream, args, K=64):
                 chunk_height_autotuned=chunk)
 
 
-def mhfem_arm(p, dev, stream, args):
-    """The mixed-hybrid (p, lambda) system of the same grid (Section 4, Eq. alge_sys), assembled on
-    the device: cell sources, 0 on faces; B_co and AMG alone in FP64, B_co with the FP32
-    preconditioner.  IC(0) alone is left out (over a thousand iterations at this size)."""
-    import torch
-    from paper_1205_6113_gb300 import cpc
-    logk = torch.tensor(p.logk, device=dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cpc.mhfem_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    rowptr, col, val = cpc.mhfem_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    asm_ms = e0.elapsed_time(e1)
-    nu = int(rowptr.shape[0]) - 1
-    b = torch.zeros(nu, dtype=torch.float64, device=dev)
-    b[:p.n] = torch.tensor(p.rhs(), device=dev)
-    out = dict(workload=WORKLOAD + "_mhfem", unknowns=nu, nnz=int(col.shape[0]), assembly_ms=round(asm_ms, 3))
-    steps = max(1, min(args.steps, 3))
-    for name, pre, prec in [("bco_fp64", "bco", "fp64"), ("amg_fp64", "amg", "fp64"), ("bco_fp32", "bco", "fp32")]:
-        t = time.perf_counter()
-        s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order="colour")
-        setup_ms = (time.perf_counter() - t) * 1e3
-        x, it, st, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
-        ms = []
-        for _ in range(steps):
-            torch.cuda.synchronize()
-            e0.record(stream)
-            x, it, st, _ = s.solve(b, tol=TOL, maxit=MAXIT, hist=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        xr = x.cpu().numpy()
-        res = float(np.linalg.norm(b.cpu().numpy() - csr_matvec(rowptr, col, val, xr)) / np.linalg.norm(b.cpu().numpy()))
-        out[name] = dict(ms=round(float(np.mean(ms)), 3), iters=int(it), status=int(st), setup_wall_ms=round(setup_ms, 1),
-                         levels=s.nlevels, true_res=res)
-        s.close()
-    return out
-
-
 def adjoint_arm(dev, stream, tol=1e-8):
     """dJ/dlog k for J = 1/2 sum_w (mean_w p - d_w)^2 on channels3d_256x256x128: assembly + setup,
     forward solve, adjoint solve (same handle) and the gradient kernel, each timed with CUDA events."""
@@ -530,31 +559,39 @@ def csr_matvec(rowptr, col, val, x):
     return np.bincount(rows, weights=v * x[c], minlength=len(rp) - 1)
 
 
-def oracle_time(p, sample_iters=None):
-    """The oracle (single thread, FP64) on the same matrix: setup once, then one B_co PCG solve."""
+def oracle_time(p, openmp=False, tol=TOL):
+    """The oracle (FP64) on the same matrix and with the same B_co as the headline (red-black IC(0)
+    ordering): setup once, then one PCG solve.  openmp: the -fopenmp build on every host core."""
     import oracle as O
     A = O.tpfa_problem(p)
     t = time.perf_counter()
-    orc = O.Oracle(A)
+    orc = O.Oracle(A, ic_colour_order=True, openmp=openmp)
     setup_s = time.perf_counter() - t
     t = time.perf_counter()
-    r = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=sample_iters or MAXIT)
+    r = orc.pcg(p.rhs(), op=O.BCO, tol=tol, maxit=MAXIT)
     solve_s = time.perf_counter() - t
-    return orc, r, setup_s, solve_s
+    return orc, r, setup_s, solve_s, O.threads(openmp)
 
 
 def reference_arm(args, rank, world):
-    """CPU oracle timed on the host cores (the reference arm: the paper has no code of its own)."""
+    """CPU oracle timed on the host cores (the reference arm: the paper has no code of its own):
+    the headline's B_co (red-black IC(0) ordering), single-threaded.  Each step is one full PCG
+    solve when warm-up plus timed steps fit in about two minutes; otherwise each step runs the
+    number of PCG iterations that fits, and the time per iteration is scaled by the full
+    iteration count."""
     import oracle as O
     if rank != 0:
         return
     p = inputs.workload(WORKLOAD)
     A = O.tpfa_problem(p)
-    orc = O.Oracle(A)
-    sample = 4
+    orc = O.Oracle(A, ic_colour_order=True)
+    t = time.perf_counter()
     full_iters = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=MAXIT)["iters"]     # untimed: the full count
+    full_s = time.perf_counter() - t
+    nsteps = args.warmup + max(1, args.steps)
+    sample = full_iters if nsteps * full_s <= 120.0 else max(1, int(120.0 / (nsteps * full_s / full_iters)))
     times = []
-    for k in range(args.warmup + max(1, args.steps)):
+    for k in range(nsteps):
         t = time.perf_counter()
         r = orc.pcg(p.rhs(), op=O.BCO, tol=TOL, maxit=sample)
         dt = time.perf_counter() - t
@@ -562,16 +599,18 @@ def reference_arm(args, rank, world):
             times.append(dt / r["iters"])
     per_it_ms = float(np.mean(times)) * 1e3
     value = per_it_ms * full_iters
+    what = ("one full B_co PCG solve (%d iterations)" % full_iters if sample == full_iters else
+            "%d B_co PCG iterations, scaled by the full iteration count (%d)" % (sample, full_iters))
     line = {"metric": METRIC, "value": round(value, 2), "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(value, 2), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": p.n, "nnz": A.nnz, "precond": "B_co", "tol": TOL,
-                       "l2": "cpu"},
+            "config": {"workload": WORKLOAD, "n": p.n, "nnz": A.nnz, "precond": "B_co",
+                       "ic_order": "red-black (2-colour)", "tol": TOL, "l2": "cpu"},
             "cpu_baseline": {"value": round(value, 2), "unit": "ms", "cores": 1, "host_cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": "each step: %d B_co PCG iterations of the oracle on the %s matrix, "
-                                       "scaled by its full iteration count (%d)" % (sample, WORKLOAD, full_iters)},
+                             "sample": "each step: %s of the oracle on the %s matrix, one host core"
+                                       % (what, WORKLOAD)},
             "e2e": {"value": round(value, 2), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -598,7 +637,8 @@ def profile_mode(name):
     """One preconditioner application plus one fine-level sweep between cudaProfilerStart/Stop
     (for `ncu --profile-from-start off`), after two untimed warm-up applications.  With
     name = "blockcg_fp32": one block PCG solve of the 64 right-hand sides of the batched workload
-    (FP32 preconditioner) after one untimed warm-up solve."""
+    (FP32 preconditioner) after one untimed warm-up solve.  With name = "sweeps_fp64": one
+    forward Gauss-Seidel sweep of every coarse level, after two untimed ones."""
     import torch
     from paper_1205_6113_gb300 import cpc
     pre, prec = name.split("_")
@@ -618,7 +658,21 @@ def profile_mode(name):
         torch.cuda.profiler.stop()
         print(json.dumps({"profiled": name, "block_iterations": int(it), "status": int(st)}))
         return
-    s = cpc.Solver(rowptr, col, val, precond=pre, precision=prec, ic_order="colour")
+    s = cpc.Solver(rowptr, col, val, precond=pre if pre != "sweeps" else "bco", precision=prec, ic_order="colour")
+    if pre == "sweeps":     # one forward Gauss-Seidel sweep of every coarse level (k_gs launches only)
+        xs = [torch.randn(s.level_info(l)["n"], dtype=torch.float64, device=dev) for l in range(s.nlevels - 1)]
+        ys = [torch.zeros_like(x) for x in xs]
+        for _ in range(2):
+            for l in range(1, s.nlevels - 1):
+                s.level_apply(l, 5, xs[l], ys[l])
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for l in range(1, s.nlevels - 1):
+            s.level_apply(l, 5, xs[l], ys[l])
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profiled": name, "colours": [s.level_info(l)["ncolours"] for l in range(1, s.nlevels - 1)]}))
+        return
     r = torch.tensor(p.rhs(), device=dev)
     z = torch.empty_like(r)
     y = torch.zeros_like(r)
@@ -646,7 +700,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-mhfem", action="store_true")
+    ap.add_argument("--no-matrices", action="store_true")
     ap.add_argument("--profile", default=None, help="e.g. bco_fp64: one application for ncu, then exit")
     args = ap.parse_args()
     if args.profile:
@@ -671,12 +725,14 @@ def main():
     iters = out["headline"]["iters"][-1]
     per_it, fixed = out["launches"]
     launches = int(sum(fixed + it * per_it for it in out["headline"]["iters"]))
+    arms = out["arms"]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world, "steps": k,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": p.n, "nnz": int(out["levels"][0]["nnz"]), "precond": "B_co",
-                   "precision": "fp64", "ic_order": "red-black (2-colour)", "tol": TOL, "iters": iters, "levels": out["nlevels"],
+                   "precision": "fp64", "ic_order": "red-black (2-colour)", "theta": 0.12, "tol": TOL,
+                   "iters": iters, "levels": out["nlevels"],
                    "l2": "flushed (512 MiB write) before every timed solve",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": round(float(np.mean(out["e2e_ms"])), 3), "unit": "ms",
@@ -684,12 +740,12 @@ def main():
         "roofline": out["roofline"],
         "solve_hbm": {"bytes_per_iter": int(out["bytes_per_iter"]), "gbs": round(out["solve_gbs"], 1),
                       "frac": round(out["solve_gbs"] / out["roofline"]["peak"], 4)},
-        "arms": out["arms"],
+        "arms": arms,
         "setup_ms": out["setups"],
         "true_res": out["true_res"],
+        "matrices": out.get("matrices"),
         "adjoint": out.get("adjoint"),
         "batched": out.get("batched"),
-        "mhfem": out.get("mhfem"),
         "clocks": out["clocks"],
         "gpu_launches": launches,
         "launches_per_iteration": per_it,
@@ -698,14 +754,36 @@ def main():
                       "operator_complexity": round(sum(l["nnz"] for l in out["levels"]) / out["levels"][0]["nnz"], 3),
                       "grid_complexity": round(sum(l["n"] for l in out["levels"]) / out["levels"][0]["n"], 3)},
     }
+    headline_ms = round(value, 3)
+    if arms:
+        r = dict(arms)
+        r["bco_fp64"] = dict(ms=headline_ms, iters=iters)
+        line["verdict"] = verdict(r)
+        line["fp32_vs_fp64"] = {"bco_fp32_ms": arms.get("bco_fp32", {}).get("ms"), "bco_fp64_ms": headline_ms,
+                                "speedup": round(headline_ms / arms["bco_fp32"]["ms"], 3)
+                                if arms.get("bco_fp32", {}).get("ms") else None}
     if not args.no_cpu_baseline and world == 1:
-        _, r, setup_s, solve_s = oracle_time(p)
+        import oracle as O
+        orc, r, setup_s, solve_s, _ = oracle_time(p)
         line["cpu_baseline"] = {"value": round(solve_s * 1e3, 1), "unit": "ms", "cores": 1,
                                 "host_cores": os.cpu_count(), "kind": "oracle",
-                                "sample": "one full B_co PCG solve (%d iterations) of the %s matrix on one host "
-                                          "core, solve phase only (oracle setup %.1f s excluded)"
-                                          % (r["iters"], WORKLOAD, setup_s),
+                                "sample": "one full B_co PCG solve (%d iterations, red-black IC(0) ordering as on the "
+                                          "GPU) of the %s matrix on one host core, solve phase only (oracle setup "
+                                          "%.1f s excluded)" % (r["iters"], WORKLOAD, setup_s),
                                 "iters": r["iters"]}
+        _, r2, setup2, solve2, nthr = oracle_time(p, openmp=True)
+        line["cpu_baseline"]["openmp"] = {"value": round(solve2 * 1e3, 1), "unit": "ms", "cores": nthr,
+                                          "iters": r2["iters"], "setup_s": round(setup2, 2),
+                                          "parallel": "sparse products, vector updates, dot products and the rows "
+                                                      "of each Gauss-Seidel colour; IC(0) solves and the coarsest "
+                                                      "solve sequential"}
+        # error of the GPU solutions against the FP64 oracle's, all run to tol 1e-10
+        ref = orc.pcg(p.rhs(), op=O.BCO, tol=1e-10, maxit=MAXIT)
+        xo = ref["x"]
+        line["error_vs_oracle"] = {"tol": 1e-10, "oracle_iters": ref["iters"]}
+        for prec, v in out["xs"].items():
+            line["error_vs_oracle"][prec] = {"rel_err": float(np.linalg.norm(v["x"] - xo) / np.linalg.norm(xo)),
+                                             "iters": int(v["iters"]), "status": int(v["status"])}
     print(json.dumps(line), flush=True)
 
 

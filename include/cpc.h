@@ -84,7 +84,7 @@ typedef struct {
                                finest level's Gauss-Seidel colouring                (default 0)   */
     int32_t gs_order;       /* CPC_GS_*; CPC_GS_NATURAL needs ic_order = 0 and tail_nnz_max <= 0
                                                                                     (default 0)   */
-    double theta;           /* strength threshold of the AMG coarsening            (0.25)        */
+    double theta;           /* strength threshold of the AMG coarsening            (0.12)        */
     int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (512)         */
     int32_t max_levels;     /* at most this many levels                            (20)          */
     int32_t autotune;       /* 1: each coarse level's SELL chunk height C (and so its threads per
@@ -156,10 +156,12 @@ int cpc_tpfa_gradient(int32_t nx, int32_t ny, int32_t nz, const double* logk, do
  * Scratch: a 64 KiB array inside the library image (one int per block of 1024 cells), held by
  * every GPU that loads the library until the process exits.  Grids of more than 16,777,216 cells
  * (nx * ny * nz) are rejected with CPC_EINVAL.  The first call on each device looks up the
- * array's device address with that device current; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents (every call rewrites
- * what it reads), so calls whose work overlaps on the GPU race: order them on one stream.
- * Returns CPC_OK, CPC_EINVAL or CPC_ECUDA.  Asynchronous on `stream`.
+ * array's device address with that device current (and again after the device's context has
+ * been replaced, e.g. by cudaDeviceReset); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (every call rewrites what it
+ * reads), so calls whose work overlaps on the GPU race: order them on one stream.
+ * Returns CPC_OK, CPC_EINVAL or CPC_ECUDA; on failure cpc_last_error(NULL) says why.
+ * Asynchronous on `stream`.
  */
 int cpc_tpfa_assemble_noalloc(int32_t nx, int32_t ny, int32_t nz, const double* logk,
                               double kz_ratio, int32_t dirichlet_mask, int32_t* rowptr,
@@ -248,6 +250,13 @@ int cpc_setup_time_ms(const cpc_handle* h, double* ms_ic0, double* ms_amg);
  * captured loop body (one PCG iteration) and *fixed launches outside the loop.  Builds the solve
  * graph if it does not exist yet. */
 int cpc_solve_launches(cpc_handle* h, int64_t* per_iteration, int64_t* fixed);
+
+/* Profiling: *us = microseconds per forward Gauss-Seidel sweep (colours ascending, one dependent
+ * launch per colour, Section 3.3) of level `level` (0 <= level < levels - 1), in the handle's
+ * preconditioner precision, replayed from a CUDA graph as inside the solve: `reps` sweeps
+ * (1..1000) per replay, best of three replays after a warm-up.  Overwrites the level's work
+ * vectors.  Synchronous. */
+int cpc_sweep_time_us(cpc_handle* h, int32_t level, int32_t reps, double* us);
 
 /* Number of AMG levels (finest = 0). */
 int cpc_num_levels(const cpc_handle* h);

@@ -24,6 +24,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.cpp")
 LIB = os.path.join(HERE, "_liboracle.so")
+LIB_OMP = os.path.join(HERE, "_liboracle_omp.so")
 
 BCO, S, ST, B, STILDE, BHAT, A, I, S_ILU, AMG_ILU = range(10)
 OPS = {"bco": BCO, "amg": STILDE, "ilu": B, "bhat": BHAT, "none": I, "amg_ilu": AMG_ILU}
@@ -32,51 +33,61 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "IC(0) breakdown", 3: "not converge
           4: "CG breakdown", 7: "AMG setup failure"}
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.cpp with g++ (plain FP64, no FMA contraction)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, SRC])
-        os.replace(tmp, LIB)
-    return LIB
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.cpp with g++ (plain FP64, no FMA contraction).  The default library is
+    single-threaded; with openmp a second library is built with -fopenmp, whose parallel loops
+    serve only to time the oracle on all host cores."""
+    target = LIB_OMP if openmp else LIB
+    if force or not os.path.exists(target) or os.path.getmtime(target) < os.path.getmtime(SRC):
+        tmp = target + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off"]
+                              + (["-fopenmp"] if openmp else []) + ["-o", tmp, SRC])
+        os.replace(tmp, target)
+    return target
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
+def lib(openmp: bool = False):
+    if openmp not in _libs:
+        L = ctypes.CDLL(build(openmp=openmp))
         P = ctypes.c_void_p
         i32, f64 = ctypes.c_int, ctypes.c_double
-        _lib.orc_tpfa_nnz.restype = i32
-        _lib.orc_tpfa_nnz.argtypes = [i32, i32, i32]
-        _lib.orc_tpfa.restype = i32
-        _lib.orc_tpfa.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
-        _lib.orc_tpfa_gradient.restype = i32
-        _lib.orc_tpfa_gradient.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
-        _lib.orc_create.restype = P
-        _lib.orc_create.argtypes = [i32, P, P, P, f64, i32, i32, i32, i32, P]
-        _lib.orc_destroy.argtypes = [P]
-        _lib.orc_nlevels.restype = i32
-        _lib.orc_nlevels.argtypes = [P]
+        L.orc_threads.restype = i32
+        L.orc_threads.argtypes = []
+        L.orc_tpfa_nnz.restype = i32
+        L.orc_tpfa_nnz.argtypes = [i32, i32, i32]
+        L.orc_tpfa.restype = i32
+        L.orc_tpfa.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
+        L.orc_tpfa_gradient.restype = i32
+        L.orc_tpfa_gradient.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
+        L.orc_create.restype = P
+        L.orc_create.argtypes = [i32, P, P, P, f64, i32, i32, i32, i32, P]
+        L.orc_destroy.argtypes = [P]
+        L.orc_nlevels.restype = i32
+        L.orc_nlevels.argtypes = [P]
         for name in ("orc_level_sizes", "orc_level_A", "orc_level_P", "orc_level_cf_colour",
                      "orc_ic0_values", "orc_level_apply", "orc_apply", "orc_pcg", "orc_mhfem_size",
                      "orc_mhfem"):
-            getattr(_lib, name).restype = i32
-        _lib.orc_level_sizes.argtypes = [P, i32, P]
-        _lib.orc_level_A.argtypes = [P, i32, P, P, P]
-        _lib.orc_level_P.argtypes = [P, i32, P, P, P]
-        _lib.orc_level_cf_colour.argtypes = [P, i32, P, P]
-        _lib.orc_ic0_values.argtypes = [P, P]
-        _lib.orc_level_apply.argtypes = [P, i32, i32, P, P]
-        _lib.orc_apply.argtypes = [P, i32, P, P]
-        _lib.orc_mhfem_size.argtypes = [i32, i32, i32, P, f64, i32, P]
-        _lib.orc_mhfem.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
-        _lib.orc_pcg.argtypes = [P, i32, P, P, f64, i32, P, P, P, P, i32, P]
-    return _lib
+            getattr(L, name).restype = i32
+        L.orc_level_sizes.argtypes = [P, i32, P]
+        L.orc_level_A.argtypes = [P, i32, P, P, P]
+        L.orc_level_P.argtypes = [P, i32, P, P, P]
+        L.orc_level_cf_colour.argtypes = [P, i32, P, P]
+        L.orc_ic0_values.argtypes = [P, P]
+        L.orc_level_apply.argtypes = [P, i32, i32, P, P]
+        L.orc_apply.argtypes = [P, i32, P, P]
+        L.orc_mhfem_size.argtypes = [i32, i32, i32, P, f64, i32, P]
+        L.orc_mhfem.argtypes = [i32, i32, i32, P, f64, i32, P, P, P]
+        L.orc_pcg.argtypes = [P, i32, P, P, f64, i32, P, P, P, P, i32, P]
+        _libs[openmp] = L
+    return _libs[openmp]
+
+
+def threads(openmp: bool = False) -> int:
+    """Threads the oracle's parallel loops use (1 for the default library)."""
+    return int(lib(openmp).orc_threads())
 
 
 def _p(a: np.ndarray):
@@ -193,11 +204,12 @@ class OracleError(RuntimeError):
 class Oracle:
     """The oracle's solver state: AMG hierarchy, IC(0) factor and the preconditioners."""
 
-    def __init__(self, A: Csr, theta=0.25, coarse_max=512, max_levels=20, gs_natural=False,
-                 ic_colour_order=False):
+    def __init__(self, A: Csr, theta=0.12, coarse_max=512, max_levels=20, gs_natural=False,
+                 ic_colour_order=False, openmp=False):
         self.Amat = A
+        self._lib = lib(openmp)
         st = ctypes.c_int(0)
-        self._h = lib().orc_create(A.n, _p(A.rowptr), _p(A.col), _p(A.val), float(theta),
+        self._h = self._lib.orc_create(A.n, _p(A.rowptr), _p(A.col), _p(A.val), float(theta),
                                    int(coarse_max), int(max_levels), int(gs_natural),
                                    int(ic_colour_order), ctypes.byref(st))
         if not self._h:
@@ -207,16 +219,16 @@ class Oracle:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._lib.orc_destroy(h)
             self._h = None
 
     @property
     def nlevels(self) -> int:
-        return lib().orc_nlevels(self._h)
+        return self._lib.orc_nlevels(self._h)
 
     def level_sizes(self, l):
         s = np.zeros(5, np.int32)
-        if lib().orc_level_sizes(self._h, l, _p(s)):
+        if self._lib.orc_level_sizes(self._h, l, _p(s)):
             raise IndexError(l)
         return dict(n=int(s[0]), nnz=int(s[1]), ncolours=int(s[2]), nc=int(s[3]), nnzP=int(s[4]))
 
@@ -225,7 +237,7 @@ class Oracle:
         ptr = np.zeros(s["n"] + 1, np.int32)
         col = np.zeros(s["nnz"], np.int32)
         val = np.zeros(s["nnz"], np.float64)
-        lib().orc_level_A(self._h, l, _p(ptr), _p(col), _p(val))
+        self._lib.orc_level_A(self._h, l, _p(ptr), _p(col), _p(val))
         return Csr(s["n"], ptr, col, val)
 
     def level_P(self, l) -> Csr:
@@ -233,7 +245,7 @@ class Oracle:
         ptr = np.zeros(s["n"] + 1, np.int32)
         col = np.zeros(s["nnzP"], np.int32)
         val = np.zeros(s["nnzP"], np.float64)
-        if lib().orc_level_P(self._h, l, _p(ptr), _p(col), _p(val)):
+        if self._lib.orc_level_P(self._h, l, _p(ptr), _p(col), _p(val)):
             raise IndexError(l)
         return Csr(s["n"], ptr, col, val, m=s["nc"])
 
@@ -241,26 +253,26 @@ class Oracle:
         n = self.level_sizes(l)["n"]
         cf = np.zeros(n, np.int32)
         colour = np.zeros(n, np.int32)
-        if lib().orc_level_cf_colour(self._h, l, _p(cf), _p(colour)):
+        if self._lib.orc_level_cf_colour(self._h, l, _p(cf), _p(colour)):
             raise IndexError(l)
         return cf, colour
 
     def ic0_values(self) -> np.ndarray:
         lu = np.zeros(self.Amat.nnz, np.float64)
-        lib().orc_ic0_values(self._h, _p(lu))
+        self._lib.orc_ic0_values(self._h, _p(lu))
         return lu
 
     def level_apply(self, l, op, x) -> np.ndarray:
         x = _f64(x)
         y = np.zeros_like(x)
-        if lib().orc_level_apply(self._h, l, op, _p(x), _p(y)):
+        if self._lib.orc_level_apply(self._h, l, op, _p(x), _p(y)):
             raise ValueError("level_apply(%d, %d)" % (l, op))
         return y
 
     def apply(self, op, r) -> np.ndarray:
         r = _f64(r)
         z = np.zeros_like(r)
-        if lib().orc_apply(self._h, op, _p(r), _p(z)):
+        if self._lib.orc_apply(self._h, op, _p(r), _p(z)):
             raise ValueError(op)
         return z
 
@@ -274,7 +286,7 @@ class Oracle:
         beta = np.zeros(cap)
         out = np.zeros(2)
         it = ctypes.c_int(0)
-        st = lib().orc_pcg(self._h, op, _p(b), _p(x), float(tol), int(maxit), ctypes.byref(it),
+        st = self._lib.orc_pcg(self._h, op, _p(b), _p(x), float(tol), int(maxit), ctypes.byref(it),
                            _p(hist), _p(alpha), _p(beta), cap, _p(out))
         k = it.value
         return dict(x=x, iters=k, status=st, res_hist=hist[:k + 1].copy(), alpha=alpha[:k].copy(),

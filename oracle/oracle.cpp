@@ -29,6 +29,13 @@
  * reservoir matrices are not available).
  *
  * Compile with -ffp-contract=off so that results do not depend on the host's FMA contraction.
+ *
+ * The default build is single-threaded: the OpenMP pragmas below are ignored without -fopenmp.
+ * Built with -fopenmp (a second library, used only to time the oracle on all host cores), the
+ * row loops of the sparse products, the vector updates and the rows of one colour of a
+ * multicolour Gauss-Seidel sweep (mutually uncoupled, so the result is the same) run in parallel,
+ * and the dot products reduce in a different order; the IC(0) triangular solves, the
+ * natural-order Gauss-Seidel sweep and the coarsest solve stay sequential.
  */
 #include <algorithm>
 #include <climits>
@@ -37,6 +44,9 @@
 #include <cstring>
 #include <utility>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -223,6 +233,7 @@ Csr mhfem_assemble(int nx, int ny, int nz, const double* logk, double kzr, int d
 // Basic sparse helpers
 // ---------------------------------------------------------------------------------------------
 void spmv(const Csr& A, const double* x, double* y) {
+#pragma omp parallel for schedule(static) if (A.n > 20000)
     for (int i = 0; i < A.n; ++i) {
         double s = 0.0;
         for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += A.val[p] * x[A.col[p]];
@@ -232,6 +243,7 @@ void spmv(const Csr& A, const double* x, double* y) {
 
 // r = f - A u
 void residual(const Csr& A, const double* f, const double* u, double* r) {
+#pragma omp parallel for schedule(static) if (A.n > 20000)
     for (int i = 0; i < A.n; ++i) {
         double s = 0.0;
         for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += A.val[p] * u[A.col[p]];
@@ -359,7 +371,7 @@ Csr permute_sym(const Csr& A, const vector<int>& order) {   // order[new] = old
 // ---------------------------------------------------------------------------------------------
 // AMG setup (Section 3.2).  Rules shared with the CUDA path (both written from this statement):
 //  strength   j strongly influences i (j in S_i) iff j != i and -a_ij >= theta * max_{k != i}(-a_ik)
-//             with that maximum > 0;
+//             with that maximum > 0 (the paper leaves theta open; the callers' default is 0.12);
 //  PMIS       weight (|S^T_i|, fmix32(i)) compared lexicographically; points with |S^T_i| = 0 are F;
 //             each round, undecided points whose weight beats every undecided point of
 //             S_i u S^T_i become C, then undecided points with a C point in S_i become F;
@@ -658,8 +670,7 @@ void gs_apply(const Level& L, bool natural, bool backward, const double* r, doub
     if (natural) for (int i = 0; i < n; ++i) ord[i] = i;
     else ord = L.order;
     for (int q = 0; q < n; ++q) pos[ord[q]] = q;
-    for (int s = 0; s < n; ++s) {
-        const int q = backward ? n - 1 - s : s;
+    auto row = [&](int q) {
         const int i = ord[q];
         double acc = r[i];
         for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
@@ -669,6 +680,21 @@ void gs_apply(const Level& L, bool natural, bool backward, const double* r, doub
             if (solved) acc -= A.val[p] * d[j];
         }
         d[i] = acc / A.val[L.diag[i]];
+    };
+    if (natural) {
+        for (int s = 0; s < n; ++s) row(backward ? n - 1 - s : s);
+        return;
+    }
+    // colour-major order: the rows of one colour are consecutive in ord and not coupled to each
+    // other, so within a colour the order of the row updates does not matter
+    vector<int> seg(L.ncolours + 1, 0);
+    for (int i = 0; i < n; ++i) seg[L.colour[i] + 1]++;
+    for (int c = 0; c < L.ncolours; ++c) seg[c + 1] += seg[c];
+    for (int cc = 0; cc < L.ncolours; ++cc) {
+        const int c = backward ? L.ncolours - 1 - cc : cc;
+        const int q0 = seg[c], q1 = seg[c + 1];
+#pragma omp parallel for schedule(static) if (q1 - q0 > 4000)
+        for (int t = q0; t < q1; ++t) row(backward ? q0 + q1 - 1 - t : t);
     }
 }
 
@@ -718,6 +744,7 @@ void vcycle(const Oracle& O, int l, const double* f, double* u, Cycle cy) {
     residual(L.A, f, u, r.data());                              // (1) pre-smoothing
     if (ilu) apply_B(O, r.data(), d.data());
     else gs_apply(L, O.gs_natural, cy.pre_bwd, r.data(), d.data());
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) u[i] += d[i];
     residual(L.A, f, u, r.data());                              // (2a) restriction
     const int nc = L.P.m;
@@ -726,10 +753,12 @@ void vcycle(const Oracle& O, int l, const double* f, double* u, Cycle cy) {
     vcycle(O, l + 1, fc.data(), e.data(), cy);                  // (2b) zero initial guess
     vector<double> pe(n);
     spmv(L.P, e.data(), pe.data());                             // (2c) prolongation
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) u[i] += pe[i];
     residual(L.A, f, u, r.data());                              // (3) post-smoothing
     if (ilu) apply_B(O, r.data(), d.data());
     else gs_apply(L, O.gs_natural, cy.post_bwd, r.data(), d.data());
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) u[i] += d[i];
 }
 
@@ -747,8 +776,10 @@ void apply_B(const Oracle& O, const double* r, double* z) {
     const int n = O.A.n;
     if (O.ic_order.empty()) { ilu0_solve(O.Aic, O.lu, O.lu_diag, r, z); return; }
     vector<double> rp(n), zp(n);
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int q = 0; q < n; ++q) rp[q] = r[O.ic_order[q]];
     ilu0_solve(O.Aic, O.lu, O.lu_diag, rp.data(), zp.data());
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int q = 0; q < n; ++q) z[O.ic_order[q]] = zp[q];
 }
 
@@ -759,9 +790,11 @@ void apply_bco(const Oracle& O, const double* r, double* z) {
     apply_S(O, r, u1.data(), false);                            // (1) u1 = 0 + S (r - A 0)
     residual(O.A, r, u1.data(), t.data());                      // (2) u2 = u1 + B (r - A u1)
     apply_B(O, t.data(), c.data());
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) u2[i] = u1[i] + c[i];
     residual(O.A, r, u2.data(), t.data());                      // (3) u3 = u2 + S^T (r - A u2)
     apply_S(O, t.data(), c.data(), true);
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) z[i] = u2[i] + c[i];
 }
 
@@ -773,6 +806,7 @@ void apply_stilde(const Oracle& O, const double* r, double* z, bool ilu_fine = f
     apply_S(O, r, u1.data(), false, ilu_fine);
     residual(O.A, r, u1.data(), t.data());
     apply_S(O, t.data(), c.data(), true, ilu_fine);
+#pragma omp parallel for schedule(static) if (n > 20000)
     for (int i = 0; i < n; ++i) z[i] = u1[i] + c[i];
 }
 
@@ -807,6 +841,7 @@ int apply_op(const Oracle& O, int op, const double* r, double* z) {
 
 double dot(const double* a, const double* b, int n) {
     double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s) if (n > 20000)
     for (int i = 0; i < n; ++i) s += a[i] * b[i];
     return s;
 }
@@ -818,6 +853,15 @@ double dot(const double* a, const double* b, int n) {
 // 3 not converged within maxit, 4 CG breakdown, 7 AMG setup failure.
 // =============================================================================================
 extern "C" {
+
+// Threads the parallel loops use (1 in the default single-threaded build).
+int orc_threads() {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 int orc_tpfa_nnz(int nx, int ny, int nz) {
     // 2-D/3-D structured pattern: diagonal plus two entries per interior face
@@ -989,6 +1033,7 @@ int orc_pcg(void* h, int op, const double* b, double* x, double tol, int maxit, 
         const double pq = dot(p.data(), q.data(), n);
         if (!(pq > 0.0) || !std::isfinite(pq)) { status = 4; break; }
         const double alpha = rz / pq;
+#pragma omp parallel for schedule(static) if (n > 20000)
         for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
         *iters = k + 1;
         const double res = std::sqrt(dot(r.data(), r.data(), n)) / bnorm;
@@ -999,6 +1044,7 @@ int orc_pcg(void* h, int op, const double* b, double* x, double tol, int maxit, 
         const double rz_new = dot(r.data(), z.data(), n);
         const double beta = rz_new / rz;
         if (k < cap) beta_out[k] = beta;
+#pragma omp parallel for schedule(static) if (n > 20000)
         for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         rz = rz_new;
     }

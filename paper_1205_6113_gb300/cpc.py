@@ -67,6 +67,7 @@ SIGNATURES = [
     ("cpc_spmv", _I32, [_P, _P, _P]),
     ("cpc_setup_time_ms", _I32, [_P, _P, _P]),
     ("cpc_solve_launches", _I32, [_P, _P, _P]),
+    ("cpc_sweep_time_us", _I32, [_P, _I32, _I32, _P]),
     ("cpc_num_levels", _I32, [_P]),
     ("cpc_level_info", _I32, [_P, _I32, _P]),
     ("cpc_level_layout", _I32, [_P, _I32, _P]),
@@ -187,7 +188,7 @@ class Solver:
     numpy arrays on the host.
     """
 
-    def __init__(self, rowptr, col, val, precond="bco", precision="fp64", ic_order="natural", theta=0.25,
+    def __init__(self, rowptr, col, val, precond="bco", precision="fp64", ic_order="natural", theta=0.12,
                  coarse_max=512, max_levels=20, tail_nnz_max=0, autotune=False, gs_order="multicolour",
                  stream=None):
         torch = _torch()
@@ -340,6 +341,12 @@ class Solver:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(load().cpc_solve_launches(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
         return a.value, b.value
+
+    def sweep_time_us(self, l, reps=20):
+        """Microseconds per forward Gauss-Seidel sweep of level l, replayed from a CUDA graph."""
+        us = ctypes.c_double()
+        _check(load().cpc_sweep_time_us(self._h, l, reps, ctypes.byref(us)), self._h)
+        return us.value
 
     @property
     def nlevels(self) -> int:

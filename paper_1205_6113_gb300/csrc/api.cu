@@ -43,6 +43,10 @@ int guarded(cpc_handle* h, F&& f) {
 
 }  // namespace
 
+namespace cpc {
+void set_global_error(const std::string& msg) { g_setup_err = msg; }
+}  // namespace cpc
+
 extern "C" {
 
 int cpc_default_options(cpc_options* opt) {
@@ -52,7 +56,7 @@ int cpc_default_options(cpc_options* opt) {
     opt->precision = CPC_PREC_FP64;
     opt->ic_order = 0;
     opt->gs_order = CPC_GS_MULTICOLOUR;
-    opt->theta = 0.25;
+    opt->theta = 0.12;
     opt->coarse_max = 512;
     opt->autotune = 0;
     opt->max_levels = 20;
@@ -234,6 +238,11 @@ int cpc_solve_launches(cpc_handle* h, int64_t* per_iteration, int64_t* fixed) {
         *per_iteration = h->h.body_nodes[h->h.opt.precond];
         *fixed = 1;
     });
+}
+
+int cpc_sweep_time_us(cpc_handle* h, int32_t level, int32_t reps, double* us) {
+    if (!h || !us) return CPC_EINVAL;
+    return guarded(h, [&] { *us = cpc::sweep_time_us(h->h, level, reps); });
 }
 
 int cpc_num_levels(const cpc_handle* h) { return h ? (int)h->h.lev.size() : -1; }

@@ -123,7 +123,7 @@ __device__ __forceinline__ void brow8(const int* __restrict__ col, const MT* __r
 
 // Gauss-Seidel over the slots [s0, s1) of one colour, all columns.
 template <int J, class MT, class DT, class FT, class VT, bool LONG = false>
-__global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, const FT* __restrict__ f, VT* x, int Kp) {
+__global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, const FT* f, VT* x, int Kp) {
     const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
     if (s >= s1) return;
     pdl_launch_dependents();
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(BTPB) kb_gs(BV<MT, DT> A, int s0, int s1, cons
 // order through shared memory.  A step of a few thousand rows then costs a quarter of a row's
 // chain of dependent loads instead of a whole one.
 template <int J, class MT, class DT, class FT, class VT>
-__global__ void __launch_bounds__(BTPB) kb_gs_wide(BV<MT, DT> A, int s0, const FT* __restrict__ f, VT* x, int Kp) {
+__global__ void __launch_bounds__(BTPB) kb_gs_wide(BV<MT, DT> A, int s0, const FT* f, VT* x, int Kp) {
     __shared__ VT part[BWARPS][32 * J];
     const int s = s0 + blockIdx.x;
     pdl_launch_dependents();
@@ -185,8 +185,8 @@ __global__ void __launch_bounds__(BTPB) kb_gs_wide(BV<MT, DT> A, int s0, const F
 
 // out = f - A x (resid) over all slots; with DIAG the split diagonal is included.
 template <int J, class MT, class DT, class FT, class XT, class RT>
-__global__ void __launch_bounds__(BTPB) kb_resid(BV<MT, DT> A, int nslots, const FT* __restrict__ f,
-                                                  const XT* __restrict__ x, RT* __restrict__ out, int Kp) {
+__global__ void __launch_bounds__(BTPB) kb_resid(BV<MT, DT> A, int nslots, const FT* f,
+                                                  const XT* x, RT* __restrict__ out, int Kp) {
     pdl_launch_dependents();
     pdl_wait();
     const int lane = threadIdx.x & 31;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(BTPB) kb_resid(BV<MT, DT> A, int nslots, const
 
 // y = M x for full rows (restriction), optionally zeroing yz (the next level's initial guess).
 template <int J, class MT, class VT>
-__global__ void __launch_bounds__(BTPB) kb_apply(BV<MT, MT> M, int nslots, const VT* __restrict__ x,
+__global__ void __launch_bounds__(BTPB) kb_apply(BV<MT, MT> M, int nslots, const VT* x,
                                                   VT* __restrict__ y, VT* __restrict__ yz, int Kp) {
     pdl_launch_dependents();
     pdl_wait();
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(BTPB) kb_apply(BV<MT, MT> M, int nslots, const
 
 // x += P e
 template <int J, class MT, class VT>
-__global__ void __launch_bounds__(BTPB) kb_prolong(BV<MT, MT> P, int nslots, const VT* __restrict__ e,
+__global__ void __launch_bounds__(BTPB) kb_prolong(BV<MT, MT> P, int nslots, const VT* e,
                                                     VT* __restrict__ x, int Kp) {
     pdl_launch_dependents();
     pdl_wait();
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(BTPB) kb_prolong(BV<MT, MT> P, int nslots, con
 
 // x = A_c^{-1} f (dense), one warp per row, lanes over columns.
 template <int J, class AT, class FT, class VT>
-__global__ void __launch_bounds__(BTPB) kb_coarse(int n, const AT* __restrict__ Ainv, const FT* __restrict__ f,
+__global__ void __launch_bounds__(BTPB) kb_coarse(int n, const AT* __restrict__ Ainv, const FT* f,
                                                    VT* __restrict__ x, int Kp) {
     pdl_launch_dependents();
     pdl_wait();
@@ -285,7 +285,7 @@ __global__ void kb_zero(int64_t n, VT* x) {
 
 // Triangular solves of one IC(0) level, all columns: y = t - L y; w = (y - U w) / d, z += w.
 template <int J, class MT, class TT, class VT>
-__global__ void __launch_bounds__(BTPB) kb_lsolve(BV<MT, MT> L, int s0, int s1, const TT* __restrict__ t, VT* y, int Kp) {
+__global__ void __launch_bounds__(BTPB) kb_lsolve(BV<MT, MT> L, int s0, int s1, const TT* t, VT* y, int Kp) {
     pdl_launch_dependents();
     pdl_wait();
     const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(BTPB) kb_lsolve(BV<MT, MT> L, int s0, int s1, 
 }
 
 template <int J, class MT, class VT>
-__global__ void __launch_bounds__(BTPB) kb_usolve(BV<MT, MT> U, int s0, int s1, const VT* __restrict__ y, VT* w,
+__global__ void __launch_bounds__(BTPB) kb_usolve(BV<MT, MT> U, int s0, int s1, const VT* y, VT* w,
                                                    VT* zadd, int Kp) {
     pdl_launch_dependents();
     pdl_wait();
@@ -377,7 +377,7 @@ __device__ __forceinline__ void bd_dot(const VT (&v)[ND], const DiaOff& off, int
 }
 
 template <int J, class MT, class DT, class FT, class VT, int ND>
-__global__ void __launch_bounds__(BTPB) kb_gs_dia(BD<MT, DT> A, int s0, int s1, const FT* __restrict__ f, VT* x, int Kp) {
+__global__ void __launch_bounds__(BTPB) kb_gs_dia(BD<MT, DT> A, int s0, int s1, const FT* f, VT* x, int Kp) {
     const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
     if (s >= s1) return;
     pdl_launch_dependents();
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(BTPB) kb_gs_dia(BD<MT, DT> A, int s0, int s1, 
 
 // out = f - A x, diagonal form (grid-stride over slots).
 template <int J, class MT, class DT, class FT, class XT, class RT, int ND>
-__global__ void __launch_bounds__(BTPB) kb_resid_dia(BD<MT, DT> A, const FT* __restrict__ f, const XT* __restrict__ x,
+__global__ void __launch_bounds__(BTPB) kb_resid_dia(BD<MT, DT> A, const FT* f, const XT* x,
                                                       RT* __restrict__ out, int Kp) {
     pdl_launch_dependents();
     pdl_wait();
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(BTPB) kb_resid_dia(BD<MT, DT> A, const FT* __r
 // B_co step (2) with red-black IC(0), black rows only (see the single right-hand-side path):
 // z_b += (r_b - (A z)_b) / u_bb on the fine colour 1, diagonal form.
 template <int J, class MT, class DT, class VT, int ND>
-__global__ void __launch_bounds__(BTPB) kb_bco_black_dia(BD<MT, DT> A, int s0, int s1, const double* __restrict__ r,
+__global__ void __launch_bounds__(BTPB) kb_bco_black_dia(BD<MT, DT> A, int s0, int s1, const double* r,
                                                           const VT* __restrict__ uinv, VT* __restrict__ z, int Kp) {
     const int s = s0 + blockIdx.x * BWARPS + (threadIdx.x >> 5);
     if (s >= s1) return;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(BTPB) kb_bco_black_dia(BD<MT, DT> A, int s0, i
 // First colour step of a sweep from a zero guess fused with the zero fill: x = f / a_ii on colour 0,
 // 0 elsewhere (colour-0 rows see only zeros).
 template <class FT, class VT>
-__global__ void kb_zero_first(int n, int Kp, const FT* __restrict__ f, const int* __restrict__ colour,
+__global__ void kb_zero_first(int n, int Kp, const FT* f, const int* __restrict__ colour,
                               const VT* __restrict__ dnat, VT* __restrict__ x) {
     pdl_launch_dependents();
     pdl_wait();
@@ -473,7 +473,7 @@ __global__ void kb_zero_first(int n, int Kp, const FT* __restrict__ f, const int
 
 // f_c = R r and the coarse level's first colour step from zero: x_c = f_c / a_ii on colour 0, 0 elsewhere.
 template <int J, class MT, class VT>
-__global__ void __launch_bounds__(BTPB) kb_restrict_first(BV<MT, MT> M, int nslots, const VT* __restrict__ x,
+__global__ void __launch_bounds__(BTPB) kb_restrict_first(BV<MT, MT> M, int nslots, const VT* x,
                                                            VT* __restrict__ y, VT* __restrict__ yx,
                                                            const int* __restrict__ colour, const VT* __restrict__ dnat,
                                                            int Kp) {
@@ -533,7 +533,7 @@ __device__ void col_finish(double (&v)[J], double* part, unsigned* ctr, int Kp, 
 }
 
 template <int J>
-__global__ void __launch_bounds__(BTPB) kb_init(int n, int Kp, const double* __restrict__ b, double* __restrict__ x,
+__global__ void __launch_bounds__(BTPB) kb_init(int n, int Kp, const double* b, double* __restrict__ x,
                                                  double* __restrict__ r, double* part, unsigned* ctr, double* S) {
     pdl_launch_dependents();
     pdl_wait();
@@ -581,7 +581,7 @@ __global__ void kb_guard(cudaGraphConditionalHandle cond) {
 }
 
 template <int J, class ZT>
-__global__ void __launch_bounds__(BTPB) kb_rz(int n, int Kp, const double* __restrict__ r, const ZT* __restrict__ z,
+__global__ void __launch_bounds__(BTPB) kb_rz(int n, int Kp, const double* r, const ZT* z,
                                                double* part, unsigned* ctr, double* S) {
     pdl_launch_dependents();
     pdl_wait();
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(BTPB) kb_rz(int n, int Kp, const double* __res
 }
 
 template <int J, class ZT>
-__global__ void __launch_bounds__(BTPB) kb_p(int n, int Kp, const ZT* __restrict__ z, double* __restrict__ p,
+__global__ void __launch_bounds__(BTPB) kb_p(int n, int Kp, const ZT* z, double* __restrict__ p,
                                               const double* S) {
     pdl_launch_dependents();
     pdl_wait();
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(BTPB) kb_p(int n, int Kp, const ZT* __restrict
 }
 
 template <int J>
-__global__ void __launch_bounds__(BTPB) kb_spmv_pq(BV<double, double> A, int nslots, int Kp, const double* __restrict__ p,
+__global__ void __launch_bounds__(BTPB) kb_spmv_pq(BV<double, double> A, int nslots, int Kp, const double* p,
                                                     double* __restrict__ q, double* part, unsigned* ctr, double* S) {
     pdl_launch_dependents();
     pdl_wait();
@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(BTPB) kb_spmv_pq(BV<double, double> A, int nsl
 }
 
 template <int J, int ND>
-__global__ void __launch_bounds__(BTPB) kb_spmv_pq_dia(BD<double, double> A, int Kp, const double* __restrict__ p,
+__global__ void __launch_bounds__(BTPB) kb_spmv_pq_dia(BD<double, double> A, int Kp, const double* p,
                                                         double* __restrict__ q, double* part, unsigned* ctr, double* S) {
     pdl_launch_dependents();
     pdl_wait();
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(BTPB) kb_spmv_pq_dia(BD<double, double> A, int
 
 template <int J>
 __global__ void __launch_bounds__(BTPB) kb_update(int n, int Kp, double* __restrict__ x, double* __restrict__ r,
-                                                   const double* __restrict__ p, const double* __restrict__ q,
+                                                   const double* p, const double* q,
                                                    double* part, unsigned* ctr, double* S) {
     pdl_launch_dependents();
     pdl_wait();
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(BTPB) kb_update(int n, int Kp, double* __restr
 }
 
 // [n][K] user layout <-> [n][Kp] internal layout
-__global__ void kb_pack(int n, int K, int Kp, const double* __restrict__ in, double* __restrict__ out) {
+__global__ void kb_pack(int n, int K, int Kp, const double* in, double* __restrict__ out) {
     pdl_launch_dependents();
     pdl_wait();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * Kp; t += (int64_t)gridDim.x * blockDim.x) {
@@ -751,7 +751,7 @@ __global__ void kb_pack(int n, int K, int Kp, const double* __restrict__ in, dou
     }
 }
 
-__global__ void kb_unpack(int n, int K, int Kp, const double* __restrict__ in, double* __restrict__ out) {
+__global__ void kb_unpack(int n, int K, int Kp, const double* in, double* __restrict__ out) {
     pdl_launch_dependents();
     pdl_wait();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * K; t += (int64_t)gridDim.x * blockDim.x) {
@@ -763,7 +763,7 @@ __global__ void kb_unpack(int n, int K, int Kp, const double* __restrict__ in, d
 
 // Adjoint sources from the forward solutions: b[i][c] = x[i][c] where b[i][c] != 0, else 0
 // (the gradient of J_c = 1/2 sum over the source cells of column c of x^2); also saves x.
-__global__ void kb_adjoint_rhs(int64_t nk, double* __restrict__ b, const double* __restrict__ x, double* __restrict__ xsave) {
+__global__ void kb_adjoint_rhs(int64_t nk, double* __restrict__ b, const double* x, double* __restrict__ xsave) {
     pdl_launch_dependents();
     pdl_wait();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nk; t += (int64_t)gridDim.x * blockDim.x) {
@@ -794,8 +794,8 @@ enum { KF_BAD = 0, KF_DONE, KF_COUNT };
 // whole warps: an FP64 warp instruction costs the same with idle lanes, and FP64 issue is the
 // bound of this kernel on this part.
 template <class UT>
-__global__ void __launch_bounds__(KK_TPB) kk_gram(int n, int Kp, const UT* __restrict__ U,
-                                                  const double* __restrict__ V, double* __restrict__ part) {
+__global__ void __launch_bounds__(KK_TPB) kk_gram(int n, int Kp, const UT* U,
+                                                  const double* V, double* __restrict__ part) {
     extern __shared__ double ksm[];
     double* us = ksm;                      // [KK_ROWS][Kp]
     double* vs = ksm + KK_ROWS * Kp;       // [KK_ROWS][Kp]
@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(KK_TPB) kk_gram(int n, int Kp, const UT* __res
 
 // out = sum over blocks of part, in block order; entry (i, j) and (j, i) both take the computed
 // upper entry (min, max), so the result is exactly symmetric.
-__global__ void kk_gram_sum(int G, int Kp, const double* __restrict__ part, double* __restrict__ out) {
+__global__ void kk_gram_sum(int G, int Kp, const double* part, double* __restrict__ out) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Kp * Kp; e += gridDim.x * blockDim.x) {
         const int i = e / Kp, j = e - (e / Kp) * Kp;
         const int a = min(i, j), b = max(i, j);
@@ -925,9 +925,9 @@ __device__ __forceinline__ double kk_lane(const double (&v)[J], int k) {
 // per block the column sums of r_ij^2 in warp order into part[block][Kp].
 template <int J>
 __global__ void __launch_bounds__(BTPB) kk_update(int n, int Kp, int K, double* __restrict__ X, double* __restrict__ R,
-                                                  const double* __restrict__ P, const double* __restrict__ Q,
-                                                  const double* __restrict__ alpha, double* __restrict__ part,
-                                                  const int* __restrict__ flag) {
+                                                  const double* P, const double* Q,
+                                                  const double* alpha, double* __restrict__ part,
+                                                  const int* flag) {
     if (flag[KF_BAD]) return;              // a K x K solve failed: keep the last good iterate
     extern __shared__ double ksm[];
     double* al = ksm;                      // [Kp][Kp]
@@ -977,8 +977,8 @@ __global__ void __launch_bounds__(BTPB) kk_update(int n, int Kp, int K, double* 
 
 // P = Z + P beta, in place (a warp reads its whole row of P before writing it).
 template <int J, class ZT>
-__global__ void __launch_bounds__(BTPB) kk_pupdate(int n, int Kp, int K, const ZT* __restrict__ Z, double* __restrict__ P,
-                                                   const double* __restrict__ beta, const int* __restrict__ flag) {
+__global__ void __launch_bounds__(BTPB) kk_pupdate(int n, int Kp, int K, const ZT* Z, double* __restrict__ P,
+                                                   const double* beta, const int* flag) {
     if (flag[KF_BAD]) return;
     extern __shared__ double ksm[];
     for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) ksm[e] = beta[e];
@@ -1003,7 +1003,7 @@ __global__ void __launch_bounds__(BTPB) kk_pupdate(int n, int Kp, int K, const Z
 }
 
 template <class ZT>
-__global__ void kk_copy(int64_t nk, const ZT* __restrict__ z, double* __restrict__ p) {
+__global__ void kk_copy(int64_t nk, const ZT* z, double* __restrict__ p) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x)
         p[e] = (double)z[e];
 }
@@ -1011,7 +1011,7 @@ __global__ void kk_copy(int64_t nk, const ZT* __restrict__ z, double* __restrict
 // Q = A P with A in CSR (warp per row, lanes over columns).
 template <int J>
 __global__ void __launch_bounds__(BTPB) kk_spmm(int n, int Kp, const int* __restrict__ ptr, const int* __restrict__ col,
-                                                const double* __restrict__ val, const double* __restrict__ P,
+                                                const double* __restrict__ val, const double* P,
                                                 double* __restrict__ Q) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = blockIdx.x * BWARPS + w; i < n; i += gridDim.x * BWARPS) {
@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(BTPB) kk_spmm(int n, int Kp, const int* __rest
 
 // Per block, the column sums of v_ij^2 in warp order into part[block][Kp].
 template <int J>
-__global__ void __launch_bounds__(BTPB) kk_colnorm(int n, int Kp, const double* __restrict__ V, double* __restrict__ part) {
+__global__ void __launch_bounds__(BTPB) kk_colnorm(int n, int Kp, const double* V, double* __restrict__ part) {
     __shared__ double ws[BWARPS * 128];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double s[J];
@@ -1056,7 +1056,7 @@ __global__ void __launch_bounds__(BTPB) kk_colnorm(int n, int Kp, const double* 
 // One block.  Column norms from the partials (block order).  init: bnorm_k = ||b_k||, a zero column
 // sets KF_BAD.  Otherwise res_k = ||r_k|| / ||b_k||; KF_DONE = 1 when every column is below tol,
 // and a residual that is not finite sets KF_BAD.
-__global__ void kk_check(int G, int Kp, int K, const double* __restrict__ part, double* __restrict__ vec, double tol,
+__global__ void kk_check(int G, int Kp, int K, const double* part, double* __restrict__ vec, double tol,
                          int init, int* flag) {
     __shared__ int all;
     if (threadIdx.x == 0) all = 1;

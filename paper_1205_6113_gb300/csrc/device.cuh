@@ -42,6 +42,11 @@ inline SV<MT, DT> view(const Sell& S, const MT* val, const DT* diag) {
 // successor is resident before this kernel ends; the successor loads what does not depend on its
 // predecessor (the matrix) and then waits in pdl_wait() until the predecessor grid has completed
 // and its memory is visible.  Without a programmatic predecessor both are no-ops.
+// A kernel of such a chain is resident while the kernels before it still write, so its reads of
+// data that an earlier kernel of the chain writes (vectors, partial sums, scalars) must not take
+// the non-coherent read-only path: pointers to such data are never declared const __restrict__
+// (which lets the compiler use that path), only pointers to the matrices and layouts built at
+// setup.  With read-only loads a kernel was seen to read values of the previous V-cycle.
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 

@@ -142,6 +142,7 @@ void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s);
 void solve_pcg(Handle& h, const double* b, double* x, double tol, int maxit, int* iters,
                double* res_hist, int hist_cap, int* status);
 void level_apply(Handle& h, int l, int op, const double* x, double* y);
+double sweep_time_us(Handle& h, int l, int reps);
 void destroy_graphs(Handle& h);
 void ensure_solve_graph(Handle& h, int which);
 

@@ -21,6 +21,7 @@
 #include <memory>
 
 #include "handle.cuh"
+#include "tpfa_cell.cuh"
 
 namespace cpc {
 
@@ -93,18 +94,14 @@ __global__ void k_fill_int(int* a, int64_t n, int v) {
 }
 
 // ============================================================================================
-// a0: two-point-flux assembly (Section 4, Eq. model with c = 0), unit cells.
-// Entry order per row: z-, y-, x-, diagonal, x+, y+, z+.  Diagonal = neighbour
-// transmissibilities in that order, then Dirichlet half-cell terms in face order x0..z1.
+// a0: two-point-flux assembly (Section 4, Eq. model with c = 0), unit cells; the row of a cell
+// (entry order, harmonic means, Dirichlet terms) is tpfa_fill_row in tpfa_cell.cuh.
 // ============================================================================================
-__device__ __forceinline__ double harmonic(double a, double b) { return (2.0 * a * b) / (a + b); }
-
 __global__ void k_tpfa_rowlen(int nx, int ny, int nz, int* len) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     int n = nx * ny * nz;
     if (c >= n) return;
-    int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
-    len[c] = 1 + (i > 0) + (i < nx - 1) + (j > 0) + (j < ny - 1) + (k > 0) + (k < nz - 1);
+    len[c] = tpfa_row_len(c, nx, ny, nz);
 }
 
 __global__ void k_tpfa_fill(int nx, int ny, int nz, const double* logk, double kzr, int dmask,
@@ -112,32 +109,7 @@ __global__ void k_tpfa_fill(int nx, int ny, int nz, const double* logk, double k
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     int n = nx * ny * nz;
     if (c >= n) return;
-    int i = c % nx, j = (c / nx) % ny, kk = c / (nx * ny);
-    const int sxy = nx * ny;
-    const double kc = exp(logk[c]);
-    const double kzc = kzr * kc;
-    int nb[6];
-    double t[6];
-    int cnt = 0;
-    if (kk > 0)      { nb[cnt] = c - sxy; t[cnt++] = harmonic(kzc, kzr * exp(logk[c - sxy])); }
-    if (j > 0)       { nb[cnt] = c - nx;  t[cnt++] = harmonic(kc, exp(logk[c - nx])); }
-    if (i > 0)       { nb[cnt] = c - 1;   t[cnt++] = harmonic(kc, exp(logk[c - 1])); }
-    const int nlow = cnt;
-    if (i < nx - 1)  { nb[cnt] = c + 1;   t[cnt++] = harmonic(kc, exp(logk[c + 1])); }
-    if (j < ny - 1)  { nb[cnt] = c + nx;  t[cnt++] = harmonic(kc, exp(logk[c + nx])); }
-    if (kk < nz - 1) { nb[cnt] = c + sxy; t[cnt++] = harmonic(kzc, kzr * exp(logk[c + sxy])); }
-    double d = 0.0;
-    for (int q = 0; q < cnt; ++q) d += t[q];
-    if ((dmask & 1) && i == 0)        d += 2.0 * kc;
-    if ((dmask & 2) && i == nx - 1)   d += 2.0 * kc;
-    if ((dmask & 4) && j == 0)        d += 2.0 * kc;
-    if ((dmask & 8) && j == ny - 1)   d += 2.0 * kc;
-    if ((dmask & 16) && kk == 0)      d += 2.0 * kzc;
-    if ((dmask & 32) && kk == nz - 1) d += 2.0 * kzc;
-    int p = rowptr[c];
-    for (int q = 0; q < nlow; ++q) { col[p] = nb[q]; val[p] = -t[q]; ++p; }
-    col[p] = c; val[p] = d; ++p;
-    for (int q = nlow; q < cnt; ++q) { col[p] = nb[q]; val[p] = -t[q]; ++p; }
+    tpfa_fill_row(c, nx, ny, nz, logk, kzr, dmask, rowptr[c], col, val);
 }
 
 // ============================================================================================

@@ -1,8 +1,9 @@
 """GPU (CUDA, through the C ABI) against the CPU oracle, element by element.
 
 Tolerances: structural choices (C/F splitting, colouring, sparsity patterns) must be
-identical; FP64 matrix values agree to 1e-12 relative (same formulas, summation in the
-same order; only rounding of fused multiply-adds differs); operator applications to
+identical; the hierarchy's FP64 values (interpolation, Galerkin products) are identical to the
+bit (same formulas, products added in the same order, no fused multiply-adds); operator
+applications (where the GPU's fused multiply-adds round differently) to
 1e-11; PCG solutions run to tol 1e-10 agree to 1e-8 relative with iteration counts
 within +-2 (the parity gate), and every GPU solve reaches its tolerance on the
 true FP64 residual.
@@ -76,7 +77,9 @@ def test_hierarchy_matches_oracle(case):
         Ao = orc.level_A(l)
         assert np.array_equal(ptr, Ao.rowptr), l
         assert np.array_equal(col, Ao.col), l
-        assert rel(val, Ao.val) < 1e-12, l
+        # both sides add the Galerkin products of an entry in the same order, without fused
+        # multiply-adds: the coarse operators are identical to the bit
+        assert np.array_equal(val, Ao.val), l
         if l + 1 < orc.nlevels:
             cf, colour = s.level_splitting(l)
             cfo, colo = orc.level_cf_colour(l)
@@ -85,7 +88,7 @@ def test_hierarchy_matches_oracle(case):
             pp, pc, pv = s.level_interp(l)
             Po = orc.level_P(l)
             assert np.array_equal(pp, Po.rowptr) and np.array_equal(pc, Po.col), l
-            assert rel(pv, Po.val) < 1e-13, l
+            assert np.array_equal(pv, Po.val), l
 
 
 def test_ic0_factor_matches_oracle(case):
@@ -137,9 +140,9 @@ def test_cluster_tail_matches_oracle(case, precision):
 
 
 def test_blocked_cholesky_on_a_large_coarsest_level():
-    """A coarsest level of 504 rows: the dense inverse goes through 16 panels of the blocked
-    Cholesky (diagonal block, triangular solve, trailing update).  The coarsest solve and a whole
-    B_co application must equal the oracle's dense Cholesky solve."""
+    """A coarsest level of 329 rows: the dense inverse goes through 11 panels of the blocked
+    Cholesky (diagonal block, triangular solve, trailing update), the last one ragged.  The
+    coarsest solve and a whole B_co application must equal the oracle's dense Cholesky solve."""
     p = inputs.small_3d(40, 40, 16, seed=51)
     A = O.tpfa_problem(p)
     orc = O.Oracle(A, coarse_max=512)
@@ -154,6 +157,30 @@ def test_blocked_cholesky_on_a_large_coarsest_level():
     z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
     assert rel(z, orc.apply(O.BCO, r)) < 1e-11
     s.close()
+
+
+def test_chained_cycles_read_fresh_data():
+    """Two V-cycles back to back (S~, and B_co's steps (1)-(3)) in one chain of dependent launches:
+    each kernel starts while its predecessor still writes, so a kernel that read the previous
+    cycle's vectors through the read-only cache got values of the previous cycle (2.5e-5 off the
+    oracle on this grid before the fix).  Repeated applications must be identical and equal the
+    oracle's, and the solve must match it far inside the parity gate."""
+    p = inputs.small_3d(40, 40, 16, seed=51)
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, coarse_max=512)
+    s = cpc.Solver(A.rowptr, A.col, A.val, coarse_max=512)
+    r = inputs.random_vector(A.n, seed=53)
+    for which, op in [("amg", O.STILDE), ("bco", O.BCO)]:
+        ref = orc.apply(op, r)
+        zs = [s.apply(torch.tensor(r, device=DEV), which=which).cpu().numpy() for _ in range(4)]
+        assert all(np.array_equal(zs[0], z) for z in zs[1:]), which
+        assert rel(zs[0], ref) < 1e-11, which
+    b = p.rhs()
+    ref = orc.pcg(b, op=O.BCO, tol=1e-10, maxit=300)
+    x, iters, status, _ = s.solve(torch.tensor(b, device=DEV), tol=1e-10, maxit=300)
+    s.close()
+    assert status == 0 and abs(iters - ref["iters"]) <= 1
+    assert np.linalg.norm(x.cpu().numpy() - ref["x"]) <= 1e-12 * np.linalg.norm(ref["x"])
 
 
 def test_autotuned_layout_matches_oracle(case):

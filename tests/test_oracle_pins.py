@@ -225,7 +225,7 @@ def test_splitting_and_interpolation_invariants(small3d):
     _, _, orc, _ = small3d
     for l in range(orc.nlevels - 1):
         D = orc.level_A(l).to_dense()
-        S = strength_dense(D, 0.25)
+        S = strength_dense(D, 0.12)
         cf, _ = orc.level_cf_colour(l)
         P = orc.level_P(l).to_dense()
         C = cf == 1
@@ -274,7 +274,7 @@ def test_direct_interpolation_with_positive_couplings(shape, seed):
     orc = O.Oracle(A, coarse_max=8)
     assert orc.nlevels >= 2
     D = A.to_dense()
-    S = strength_dense(D, 0.25)
+    S = strength_dense(D, 0.12)
     cf, _ = orc.level_cf_colour(0)
     P = orc.level_P(0).to_dense()
     cidx = np.cumsum(cf == 1) - 1
