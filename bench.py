@@ -38,12 +38,13 @@ MAXIT = 5000
 METRIC = "PCG ms to 1e-6 rel. residual (combined vs AMG/ILU alone, FP32 vs FP64 prec), %HBM peak"
 L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-level Gauss-Seidel launch from the
-# committed ncu capture (profiles/k_gs_pk_fine_correlated3d_128x128x64.md); None until a capture
+# committed ncu capture (profiles/dram_bco_fp64_correlated3d_128x128x64.md); None until a capture
 # of the current kernel exists.
-TRAFFIC_K_GS_FINE = 48355584
-# The same for one forward sweep of every coarse level (the k_gs launches of the sweep, summed);
-# None until a capture of the current hierarchy exists.
-TRAFFIC_COARSE_SWEEP = None
+TRAFFIC_K_GS_FINE = 48238848
+# The same for one forward sweep of every coarse level (the k_gs launches of the sweep, summed,
+# cold cache; profiles/dram_bco_fp64_correlated3d_128x128x64.md); None until a capture of the
+# current hierarchy exists.
+TRAFFIC_COARSE_SWEEP = 225700000
 
 
 def peaks():
@@ -304,10 +305,25 @@ def gpu_arm(args, rank, world):
         coarse.append(dict(level=l, n=inf["n"], colours=inf["ncolours"], us_per_sweep=round(us, 2),
                            us_per_step=round(us / inf["ncolours"], 2), achieved=round(nbytes / (us * 1e-6) / 1e9, 1)))
     coarse_achieved = cbytes / (cus * 1e-6) / 1e9
-    # (2) the fine-level colour step (k_gs_pk): one red + one black launch per sweep
+    # (2) the fine-level colour step (k_gs_pk): one red + one black launch per sweep, L2 flushed
+    #     before each sweep (the fine level's 90 MB would otherwise stay in L2 between sweeps,
+    #     which it does not inside a solve)
     info0 = s_bco.level_info(0)
     lay0 = s_bco.level_layout(0)
-    fine_us = s_bco.sweep_time_us(0, reps=20) / info0["ncolours"]
+    xv = torch.randn(p.n, dtype=torch.float64, device=dev)
+    yv = torch.zeros_like(xv)
+    for _ in range(3):
+        s_bco.level_apply(0, 5, xv, yv)
+    kms = []
+    for _ in range(20):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_bco.level_apply(0, 5, xv, yv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms.append(e0.elapsed_time(e1) / info0["ncolours"])
+    fine_us = float(np.mean(kms)) * 1e3
     if lay0["ndiag"]:       # per row: nd diagonals, 1/a_ii, slot -> row, f_i, x_i written, the other colour's x once
         kbytes = info0["n"] * (8 * lay0["ndiag"] + 36) // info0["ncolours"]
         kname = "k_gs_pk (Gauss-Seidel colour step, fine level, red/black, per-slot diagonal records, FP64)"
@@ -318,8 +334,6 @@ def gpu_arm(args, rank, world):
                 achieved=round(kbytes / (fine_us * 1e-6) / 1e9, 1),
                 frac=round(kbytes / (fine_us * 1e-6) / 1e9 / peak, 4), traffic=TRAFFIC_K_GS_FINE)
     # (3) the fine SpMV of PCG (one launch per event pair, L2 flushed)
-    xv = torch.randn(p.n, dtype=torch.float64, device=dev)
-    yv = torch.zeros_like(xv)
     sms = []
     for _ in range(20):
         flush_l2()
@@ -634,7 +648,8 @@ def whole_job_ms_per_solve(ms_per_step: float, world: int) -> float:
 
 
 def profile_mode(name):
-    """One preconditioner application plus one fine-level sweep between cudaProfilerStart/Stop
+    """One preconditioner application plus one fine-level sweep and one fine SpMV between
+    cudaProfilerStart/Stop
     (for `ncu --profile-from-start off`), after two untimed warm-up applications.  With
     name = "blockcg_fp32": one block PCG solve of the 64 right-hand sides of the batched workload
     (FP32 preconditioner) after one untimed warm-up solve.  With name = "sweeps_fp64": one
@@ -686,6 +701,7 @@ def profile_mode(name):
     s.apply(r, z=z)
     if sweep:
         s.level_apply(0, 5, r, y)
+        s.spmv(r, y)                # the fine SpMV of PCG (diagonal form)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print(json.dumps({"profiled": name, "launches_per_iteration": s.solve_launches()[0]}))

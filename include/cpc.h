@@ -85,7 +85,7 @@ typedef struct {
     int32_t gs_order;       /* CPC_GS_*; CPC_GS_NATURAL needs ic_order = 0 and tail_nnz_max <= 0
                                                                                     (default 0)   */
     double theta;           /* strength threshold of the AMG coarsening            (0.12)        */
-    int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (512)         */
+    int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (2048)        */
     int32_t max_levels;     /* at most this many levels                            (20)          */
     int32_t autotune;       /* 1: each coarse level's SELL chunk height C (and so its threads per
                                row, 32 / C) is picked at setup by timing a Gauss-Seidel sweep of

@@ -204,7 +204,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """The oracle's solver state: AMG hierarchy, IC(0) factor and the preconditioners."""
 
-    def __init__(self, A: Csr, theta=0.12, coarse_max=512, max_levels=20, gs_natural=False,
+    def __init__(self, A: Csr, theta=0.12, coarse_max=2048, max_levels=20, gs_natural=False,
                  ic_colour_order=False, openmp=False):
         self.Amat = A
         self._lib = lib(openmp)

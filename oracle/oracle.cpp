@@ -379,7 +379,8 @@ Csr permute_sym(const Csr& A, const vector<int>& order) {   // order[new] = old
 //             P_ij = -(sum_{k != i} min(a_ik,0) / sum_{j in C_i} a_ij) * a_ij / (a_ii + sum_{k != i} max(a_ik,0));
 //             C point: P_{i,c(i)} = 1; coarse points numbered in ascending fine index;
 //  Galerkin   A_c = R (A P) with R = P^T (explicit transpose);
-//  stop       n_l <= coarse_max, max_levels reached, or no coarsening; coarsest solved exactly;
+//  stop       n_l <= coarse_max (callers' default 2048), max_levels reached, or no coarsening;
+//             coarsest solved exactly;
 //  colouring  if the pattern graph of A_l is bipartite: breadth-first parity from the smallest
 //             index of each component (red-black on a structured grid); otherwise greedy
 //             colouring in decreasing priority (peel round, fmix32(i ^ COLOUR_SEED)): each point

@@ -189,7 +189,7 @@ class Solver:
     """
 
     def __init__(self, rowptr, col, val, precond="bco", precision="fp64", ic_order="natural", theta=0.12,
-                 coarse_max=512, max_levels=20, tail_nnz_max=0, autotune=False, gs_order="multicolour",
+                 coarse_max=2048, max_levels=20, tail_nnz_max=0, autotune=False, gs_order="multicolour",
                  stream=None):
         torch = _torch()
         lib = load()

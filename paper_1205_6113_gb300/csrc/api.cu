@@ -57,7 +57,7 @@ int cpc_default_options(cpc_options* opt) {
     opt->ic_order = 0;
     opt->gs_order = CPC_GS_MULTICOLOUR;
     opt->theta = 0.12;
-    opt->coarse_max = 512;
+    opt->coarse_max = 2048;
     opt->autotune = 0;
     opt->max_levels = 20;
     opt->tail_nnz_max = 0;

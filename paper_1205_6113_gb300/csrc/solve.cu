@@ -1057,7 +1057,7 @@ float time_gs_sweep(const Sell& S, int n) {
         for (size_t c = 0; c + 1 < S.seg.size(); ++c) {
             const int c0 = S.seg[c], c1 = S.seg[c + 1];
             if (c1 <= c0) continue;
-            with_u(S.lanes, [&](auto u) {
+            with_u_gs(S.lanes, [&](auto u) {         // the batch widths of the solve's colour steps
                 launch(k_gs<double, double, double, double, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB,
                        cs, view(S, (const double*)S.val.p, (const double*)S.dinv.p), c0, c1, (const double*)f.p, x.p);
             });

@@ -52,7 +52,7 @@ def test_pure_host_entry_points(lib):
     L = cpc.load()
     opt = cpc._Options()
     assert L.cpc_default_options(ctypes.byref(opt)) == 0
-    assert opt.precond == 0 and opt.theta == 0.12 and opt.coarse_max == 512 and opt.max_levels == 20 and opt.autotune == 0
+    assert opt.precond == 0 and opt.theta == 0.12 and opt.coarse_max == 2048 and opt.max_levels == 20 and opt.autotune == 0
     assert opt.gs_order == 0 and opt.ic_order == 0 and opt.tail_nnz_max == 0
     assert L.cpc_default_options(None) == 1
     assert L.cpc_tpfa_nnz(128, 128, 64) == 7274496
