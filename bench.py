@@ -137,7 +137,12 @@ def bytes_per_iteration(s, precond, sv=8, sx=8, sv_coarse=None):
         for l in range(nl - 1):
             i = info[l]
             svl = sv if l == 0 else sv_coarse
-            b += 3 * a_pass(l, svl)                                     # pre sweep, residual, post sweep
+            if l == 0 and lay0["ndiag"] and i["ncolours"] == 2 and not ilu_fine:
+                # pre and post sweep; the residual after the sweep reads only the first colour's
+                # rows and writes zeros for the second (k_resid_dia_first)
+                b += 2 * a_pass(l, svl) + dia_pass_bytes(i["n"] // 2, lay0["ndiag"], svl, sx) + i["n"] // 2 * sx
+            else:
+                b += 3 * a_pass(l, svl)                                 # pre sweep, residual, post sweep
             if l == 0 and ilu_fine:                                     # + the two IC(0) solves
                 b += 2 * a_pass_bytes(i["n"], i["nnz"], svl, sx)
             b += 2 * a_pass_bytes(i["n"], i["nnzP"], 4 if sx == 4 else 8, sx)   # restriction, prolongation

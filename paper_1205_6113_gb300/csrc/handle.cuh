@@ -143,6 +143,10 @@ void solve_pcg(Handle& h, const double* b, double* x, double tol, int maxit, int
                double* res_hist, int hist_cap, int* status);
 void level_apply(Handle& h, int l, int op, const double* x, double* y);
 double sweep_time_us(Handle& h, int l, int reps);
+// Warps (SELL chunks) per block of the colour-step kernel, and how many of its blocks the GPU
+// holds at once (all SMs) for an operator whose lanes hold at most `lanes` entries (FP64).
+constexpr int GS_WARPS_PER_BLOCK = 4;
+int gs_resident_blocks(int lanes);
 void destroy_graphs(Handle& h);
 void ensure_solve_graph(Handle& h, int which);
 

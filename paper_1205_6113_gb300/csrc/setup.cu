@@ -1156,6 +1156,17 @@ void setup_level_sells(Level& L, cudaStream_t s, bool last, bool tune) {
         };
         const int ca = choose_chunk((double)(L.A.nnz - L.n) / std::max(1, L.n));
         build_grouped(ca, L.S);
+        if (!tune && ca < 32) {
+            // One wave: a colour step whose CTAs do not all fit on the GPU at once runs in two
+            // waves, and only the first wave's matrix loads overlap the previous step.  If the
+            // widest colour needs more CTAs than fit and twice the chunk height (half the lanes
+            // per row, about twice the entries per lane) would fit, take twice the chunk height.
+            int widest = 0;
+            for (size_t c = 0; c + 1 < L.S.seg.size(); ++c) widest = std::max(widest, L.S.seg[c + 1] - L.S.seg[c]);
+            const int blocks = (widest + GS_WARPS_PER_BLOCK - 1) / GS_WARPS_PER_BLOCK;
+            const int blocks2 = (widest / 2 + GS_WARPS_PER_BLOCK) / GS_WARPS_PER_BLOCK;
+            if (blocks > gs_resident_blocks(L.S.lanes) && blocks2 <= gs_resident_blocks(16)) build_grouped(2 * ca, L.S);
+        }
         if (tune) {
             float best = time_gs_sweep(L.S, L.n);
             for (int C : {ca / 2, ca * 2}) {

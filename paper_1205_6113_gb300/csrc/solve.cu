@@ -21,7 +21,7 @@ namespace cpc {
 
 namespace {
 
-constexpr int WPB = 4;                  // warps (= SELL chunks) per block
+constexpr int WPB = GS_WARPS_PER_BLOCK;  // warps (= SELL chunks) per block
 constexpr int SELL_TPB = WPB * 32;
 constexpr int VEC_TPB = 256;
 
@@ -189,6 +189,32 @@ __global__ void __launch_bounds__(SELL_TPB) k_resid_dia(DV<MT, DT> A, int s0, in
     if (s >= s1) return;
     pdl_launch_dependents();
     const int row = dia_row(A, s);
+    RT v[ND];
+    dia_load<ND, RT>(A, s, v);
+    const RT dg = Cv<RT>::f(A.diag[s]);
+    pdl_wait();
+    if (row < 0) return;
+    const RT fr = Cv<RT>::f(f[row]);
+    const RT dx = dg * Cv<RT>::f(x[row]);
+    const RT dot = dia_dot<ND, RT>(v, A.off, row, A.n, x);
+    r[row] = fr - (dx + dot);
+}
+
+// r = f - A x after a forward sweep on a two-colour level in diagonal form: slots below s1 (the
+// first colour) get the full residual; the rows of the last colour were just solved from their
+// current neighbours, so their residual is zero up to rounding and is written as 0 without
+// loading their matrix entries.
+template <class MT, class DT, class FT, class XT, class RT, int ND>
+__global__ void __launch_bounds__(SELL_TPB) k_resid_dia_first(DV<MT, DT> A, int s1, const FT* f, const XT* x, RT* r) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= A.nslots) return;
+    pdl_launch_dependents();
+    const int row = dia_row(A, s);
+    if (s >= s1) {
+        pdl_wait();
+        if (row >= 0) r[row] = RT(0);
+        return;
+    }
     RT v[ND];
     dia_load<ND, RT>(A, s, v);
     const RT dg = Cv<RT>::f(A.diag[s]);
@@ -743,7 +769,20 @@ void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
 }
 
 template <class FT, class VT>
-void rec_resid_level(Level& L, const FT* f, const VT* x, VT* r, cudaStream_t s) {
+void rec_resid_level(Level& L, const FT* f, const VT* x, VT* r, cudaStream_t s, bool after_sweep = false) {
+    if (L.S.ndiag && after_sweep && L.ncolours == 2) {      // the last colour's residual is zero
+        const int s1 = L.S.seg[1] * L.S.C;
+        with_nd(L.S.ndiag, [&](auto nd) {
+            constexpr int ND = decltype(nd)::value;
+            if constexpr (std::is_same<VT, double>::value)
+                launch(k_resid_dia_first<double, double, FT, VT, VT, ND>, slot_blocks(L.S.nslots), SELL_TPB, s,
+                       dview(L.S, L.n, (const double*)L.S.dval.p, (const double*)L.S.diag.p, false), s1, f, x, r);
+            else
+                launch(k_resid_dia_first<float, float, FT, VT, VT, ND>, slot_blocks(L.S.nslots), SELL_TPB, s,
+                       dview(L.S, L.n, (const float*)L.S.dval32.p, (const float*)L.S.diag32.p, false), s1, f, x, r);
+        });
+        return;
+    }
     if (L.S.ndiag) {
         with_nd(L.S.ndiag, [&](auto nd) {
             constexpr int ND = decltype(nd)::value;
@@ -831,7 +870,7 @@ void rec_vcycle(Handle& h, int l, const FT* f, VT* x, bool zero_guess, cudaStrea
         }
         for (int c = c0; c < L.ncolours; ++c) rec_gs(L, c, f, x, s);       // (1) S_l: colours ascending
     }
-    rec_resid_level(L, f, x, lr<VT>(L), s);                              // (2a) r = f - A u
+    rec_resid_level(L, f, x, lr<VT>(L), s, !ilu_here);                  // (2a) r = f - A u
     if (l + 1 >= h.tail_start) {                                         // (2a) f_c = R r, x_c = 0
         with_u(L.SR.lanes, [&](auto u) {
             launch(k_restrict_zero<VT, VT, decltype(u)::value>, blocks_for_chunks(L.SR.nchunks), SELL_TPB, s,
@@ -1134,6 +1173,17 @@ void level_apply(Handle& h, int l, int op, const double* x, double* y) {
 // Microseconds per forward Gauss-Seidel sweep (colours ascending) of level l in the
 // preconditioner's precision on the level's own work vectors, replayed from a CUDA graph as in the
 // solve: reps sweeps per replay, the best of three replays after one warm-up.
+int gs_resident_blocks(int lanes) {
+    int dev = 0, sms = 0, per_sm = 0;
+    CPC_CK(cudaGetDevice(&dev));
+    CPC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    with_u_gs(lanes, [&](auto u) {
+        CPC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_gs<double, double, double, double, decltype(u)::value>, SELL_TPB, 0));
+    });
+    return std::max(1, sms * per_sm);
+}
+
 double sweep_time_us(Handle& h, int l, int reps) {
     const int nl = (int)h.lev.size();
     if (l < 0 || l >= nl - 1) fail(CPC_EINVAL, "level has no smoother");
