@@ -229,6 +229,7 @@ def gpu_arm(args, rank, world):
     s_bco = cpc.Solver(rowptr, col, val, precond="bco", precision="fp64", ic_order="colour")
     setups["bco_fp64"] = dict(zip(("ic0_ms", "amg_ms"), s_bco.setup_time_ms()))
     setups["bco_fp64"]["wall_ms"] = (time.perf_counter() - t) * 1e3
+    setups["bco_fp64"]["amg_phases_ms"] = {k: round(v, 2) for k, v in s_bco.setup_phases_ms().items()}
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     ms, iters, wall = time_solves(s_bco, args.steps, args.warmup)

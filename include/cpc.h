@@ -244,6 +244,13 @@ int cpc_spmv(cpc_handle* h, const double* x, double* y);
 /* Setup timings in milliseconds (GPU events): IC(0) factorisation and AMG hierarchy. */
 int cpc_setup_time_ms(const cpc_handle* h, double* ms_ic0, double* ms_amg);
 
+/* The AMG setup of cpc_setup_time_ms split into its phases (GPU events, milliseconds): ms[0]
+ * coarsening (strength, C/F splitting, interpolation and the Galerkin products A_l = P_l^T A_{l+1}
+ * P_l of Section 3.2, all levels), ms[1] smoothing colours (or natural-order wavefronts) of all
+ * levels, ms[2] the coarsest level's dense Cholesky inverse (Algorithm 3.2, step 2(b)), ms[3] the
+ * kernels' layouts.  At most cap (<= 4) values are written.  Host memory. */
+int cpc_setup_phases_ms(const cpc_handle* h, double* ms, int32_t cap);
+
 /* ---- inspection (tests and diagnostics; all synchronous, outputs in HOST memory) ---------- */
 
 /* Kernel launches of one cpc_solve with the handle's preconditioner: *per_iteration nodes in the

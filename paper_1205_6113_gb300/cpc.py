@@ -68,6 +68,7 @@ SIGNATURES = [
     ("cpc_setup_time_ms", _I32, [_P, _P, _P]),
     ("cpc_solve_launches", _I32, [_P, _P, _P]),
     ("cpc_sweep_time_us", _I32, [_P, _I32, _I32, _P]),
+    ("cpc_setup_phases_ms", _I32, [_P, _P, _I32]),
     ("cpc_num_levels", _I32, [_P]),
     ("cpc_level_info", _I32, [_P, _I32, _P]),
     ("cpc_level_layout", _I32, [_P, _I32, _P]),
@@ -341,6 +342,12 @@ class Solver:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(load().cpc_solve_launches(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
         return a.value, b.value
+
+    def setup_phases_ms(self):
+        """AMG setup phases in ms: coarsening, colouring, coarsest inverse, layouts."""
+        ms = np.zeros(4)
+        _check(load().cpc_setup_phases_ms(self._h, ctypes.c_void_p(ms.ctypes.data), 4), self._h)
+        return dict(zip(("coarsening", "colouring", "coarsest_inverse", "layouts"), [float(v) for v in ms]))
 
     def sweep_time_us(self, l, reps=20):
         """Microseconds per forward Gauss-Seidel sweep of level l, replayed from a CUDA graph."""

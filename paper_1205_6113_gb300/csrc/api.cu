@@ -240,6 +240,12 @@ int cpc_solve_launches(cpc_handle* h, int64_t* per_iteration, int64_t* fixed) {
     });
 }
 
+int cpc_setup_phases_ms(const cpc_handle* h, double* ms, int32_t cap) {
+    if (!h || !ms || cap < 0) return CPC_EINVAL;
+    for (int i = 0; i < cap && i < 4; ++i) ms[i] = h->h.ms_phase[i];
+    return CPC_OK;
+}
+
 int cpc_sweep_time_us(cpc_handle* h, int32_t level, int32_t reps, double* us) {
     if (!h || !us) return CPC_EINVAL;
     return guarded(h, [&] { *us = cpc::sweep_time_us(h->h, level, reps); });

@@ -100,6 +100,7 @@ struct Handle {
     std::vector<DBuf<int>> tail_seg;
     Batched bat;
     float ms_ic0 = 0.f, ms_amg = 0.f;
+    float ms_phase[4] = {0.f, 0.f, 0.f, 0.f};   // AMG setup: coarsening, colouring, coarsest inverse, layouts
     std::string err;
     ~Handle();
 };

@@ -1516,13 +1516,21 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         setup_ic0(h, s);
     }
     CPC_CK(cudaEventRecord(e1, s));
-    // AMG hierarchy
+    // AMG hierarchy; phase boundaries are timed for cpc_setup_phases_ms
+    cudaEvent_t ph[3];
+    for (auto& e : ph) CPC_CK(cudaEventCreate(&e));
+    struct PhGuard {
+        cudaEvent_t* e;
+        ~PhGuard() { for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]); }
+    } phguard{ph};
     for (int l = 0;; ++l) {
         const bool stop = h.lev[l].n <= h.opt.coarse_max || (int)h.lev.size() >= h.opt.max_levels;
         if (stop || !coarsen(h, l, s)) break;
     }
+    CPC_CK(cudaEventRecord(ph[0], s));
     if (h.opt.gs_order == CPC_GS_NATURAL) wavefront_levels(h, s);
     else colour_levels(h, s);
+    CPC_CK(cudaEventRecord(ph[1], s));
     const int nl = (int)h.lev.size();
     {
         Level& Lc = h.lev[nl - 1];
@@ -1537,6 +1545,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         dense_chol_inverse(h.nc, M.get(), h.Ainv.p, f.get(), s);
         if (d2h(f.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
     }
+    CPC_CK(cudaEventRecord(ph[2], s));
     for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1, h.opt.autotune == 1 && l > 0);
     {   // fine A in natural order for the SpMVs
         DBuf<int> slots;
@@ -1594,6 +1603,14 @@ void setup_handle(Handle& h, const cpc_csr& in) {
     CPC_CK(cudaEventElapsedTime(&b, e1, e2));
     if (!colour_ic) h.ms_ic0 = a;
     h.ms_amg = b;
+    {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        CPC_CK(cudaEventElapsedTime(&t[0], e1, ph[0]));
+        CPC_CK(cudaEventElapsedTime(&t[1], ph[0], ph[1]));
+        CPC_CK(cudaEventElapsedTime(&t[2], ph[1], ph[2]));
+        CPC_CK(cudaEventElapsedTime(&t[3], ph[2], e2));
+        for (int i = 0; i < 4; ++i) h.ms_phase[i] = t[i];
+    }
 
     // precision of the preconditioner data
     const int prec = h.opt.precision;

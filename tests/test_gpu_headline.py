@@ -120,3 +120,28 @@ def test_full_size_benchmark_tolerance(full):
         assert status == 0 and abs(iters - ref["iters"]) <= 2, which
         assert np.linalg.norm(b - A.matvec(x)) <= 1e-6 * np.linalg.norm(b), which
         assert np.linalg.norm(x - ref["x"]) <= 1e-5 * np.linalg.norm(ref["x"]), which
+
+
+def test_channel_field_full_size_parity():
+    """The 256 x 256 x 128 channel field (8,388,608 unknowns, 1000:1 facies contrast, k_z / k =
+    0.01), the largest workload: the GPU hierarchy built from the oracle's matrix equals the
+    oracle's (splitting, colouring, patterns and values to the bit), and one B_co application
+    equals the oracle's to 1e-11.  The oracle's setup here takes about half a minute."""
+    p = inputs.channel_facies()
+    A = O.tpfa_problem(p)
+    orc = O.Oracle(A, ic_colour_order=True)
+    s = cpc.Solver(A.rowptr, A.col, A.val, precond="bco", precision="fp64", ic_order="colour")
+    assert s.nlevels == orc.nlevels >= 5
+    for l in range(orc.nlevels):
+        ptr, col, val = s.level_matrix(l)
+        Ao = orc.level_A(l)
+        assert np.array_equal(ptr, Ao.rowptr) and np.array_equal(col, Ao.col), l
+        assert np.array_equal(val, Ao.val), l
+        if l + 1 < orc.nlevels:
+            cf, colour = s.level_splitting(l)
+            cfo, colo = orc.level_cf_colour(l)
+            assert np.array_equal(cf, cfo) and np.array_equal(colour, colo), l
+    r = inputs.random_vector(A.n, seed=72)
+    z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    s.close()
+    assert rel(z, orc.apply(O.BCO, r)) < 1e-11
