@@ -882,8 +882,9 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 // Blocked right-looking factorisation with panels of NB = 32 columns:
 //   k_chol_diag   factor the 32 x 32 diagonal block in shared memory (one block),
 //   k_chol_trsm   L21 = A21 L11^{-T}, one thread per row below the block,
-//   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, one 32 x 32 tile per block;
-// then one warp per column of A_c^{-1} = L^{-T} L^{-1}.  L is left in the lower triangle of M.
+//   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles;
+// then W = L^{-1} by row panels (k_trinv_panel, k_trinv_update) and A_c^{-1} = W^T W (k_lauum).
+// L is left in the lower triangle of M.
 // ============================================================================================
 constexpr int CHOL_NB = 32;
 
@@ -942,58 +943,158 @@ __global__ void k_chol_trsm(int n, int jb, double* M, const int* fail) {
     }
 }
 
-// Trailing update of the lower triangle: a_ik -= sum_m l_im l_km over the panel columns, for
-// jb + nb <= k <= i; block (bi, bk) with bk <= bi covers a 32 x 32 tile.
-__global__ void __launch_bounds__(CHOL_NB * CHOL_NB) k_chol_syrk(int n, int jb, double* M, const int* fail) {
-    __shared__ double Li[CHOL_NB][CHOL_NB + 1], Lk[CHOL_NB][CHOL_NB + 1];
+// FP64 tile products for the dense factorisation and inverse: one 256-thread block computes a
+// 64 x 64 tile, each thread a 4 x 4 block of it, from 32-wide slices of the operands staged in
+// shared memory.  FP64 issue bounds these kernels on this part, so every FMA reads its operands
+// from registers loaded once per slice.
+constexpr int DT_T = 64;           // tile edge
+constexpr int DT_K = 32;           // slice depth
+
+// Loads rows [r0, r0 + 64) x columns [c0, c0 + 32) of a row-major matrix with leading dimension ld
+// (zero outside rows < nr, columns < nc) into S[64][33] (row r, column c at S[r][c]).
+__device__ __forceinline__ void dt_load_rows(double (*S)[DT_K + 1], const double* M, int ld, int r0, int c0, int nr,
+                                             int nc) {
+    for (int t = threadIdx.x; t < DT_T * DT_K; t += 256) {
+        const int r = t / DT_K, c = t % DT_K;
+        S[r][c] = (r0 + r < nr && c0 + c < nc) ? M[(size_t)(r0 + r) * ld + c0 + c] : 0.0;
+    }
+}
+
+// Loads rows [k0, k0 + 32) x columns [c0, c0 + 64) into S[64][33] transposed (S[c][k]).
+__device__ __forceinline__ void dt_load_cols(double (*S)[DT_K + 1], const double* M, int ld, int k0, int c0, int nk,
+                                             int nc) {
+    for (int t = threadIdx.x; t < DT_T * DT_K; t += 256) {
+        const int k = t / DT_T, c = t % DT_T;
+        S[c][k] = (k0 + k < nk && c0 + c < nc) ? M[(size_t)(k0 + k) * ld + c0 + c] : 0.0;
+    }
+}
+
+// acc[a][b] += sum_k X[ty * 4 + a][k] * Y[tx * 4 + b][k] over one slice.
+__device__ __forceinline__ void dt_mac(const double (*X)[DT_K + 1], const double (*Y)[DT_K + 1], double (&acc)[4][4],
+                                       int tx, int ty) {
+#pragma unroll 4
+    for (int k = 0; k < DT_K; ++k) {
+        double xa[4], yb[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xa[a] = X[ty * 4 + a][k];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) yb[b] = Y[tx * 4 + b][k];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += xa[a] * yb[b];
+    }
+}
+
+// Trailing update of the lower triangle: a_ik -= sum_m l_im l_km over the panel columns
+// [jb, jb + nb), for jb + nb <= k <= i; block (bi, bk) with bk <= bi covers a 64 x 64 tile.
+__global__ void __launch_bounds__(256) k_chol_syrk(int n, int jb, double* M, const int* fail) {
+    __shared__ double Li[DT_T][DT_K + 1], Lk[DT_T][DT_K + 1];
     if (*(volatile int*)fail) return;
-    const int nb = min(CHOL_NB, n - jb);
-    const int t0 = jb + nb;
     const int bi = blockIdx.y, bk = blockIdx.x;
     if (bk > bi) return;
-    const int r = threadIdx.x / CHOL_NB, c = threadIdx.x % CHOL_NB;
-    const int i0 = t0 + bi * CHOL_NB, k0 = t0 + bk * CHOL_NB;
-    Li[r][c] = (i0 + r < n && c < nb) ? M[(size_t)(i0 + r) * n + jb + c] : 0.0;
-    Lk[r][c] = (k0 + r < n && c < nb) ? M[(size_t)(k0 + r) * n + jb + c] : 0.0;
+    const int nb = min(CHOL_NB, n - jb);
+    const int t0 = jb + nb;
+    const int i0 = t0 + bi * DT_T, k0 = t0 + bk * DT_T;
+    dt_load_rows(Li, M, n, i0, jb, n, jb + nb);
+    dt_load_rows(Lk, M, n, k0, jb, n, jb + nb);
     __syncthreads();
-    const int i = i0 + r, k = k0 + c;
-    if (i >= n || k > i) return;
-    double acc = 0.0;
-    for (int m = 0; m < nb; ++m) acc += Li[r][m] * Lk[c][m];
-    M[(size_t)i * n + k] -= acc;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    dt_mac(Li, Lk, acc, tx, ty);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty * 4 + a, k = k0 + tx * 4 + b;
+            if (i < n && k <= i) M[(size_t)i * n + k] -= acc[a][b];
+        }
 }
 
-// L^T into the strict upper triangle (the lower triangle and the diagonal hold L).
-__global__ void k_chol_mirror(int n, double* __restrict__ M) {
+// Inverse of the lower factor, W = L^{-1}, by row panels (a triangular solve L W = I): panel p's
+// rows of W are L_pp^{-1} times the panel's rows of the running right-hand side R (R = I to start,
+// held in W), one thread per column j < e = the panel's end; W is lower triangular, so columns
+// from e on stay zero.
+__global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const double* L, double* W, const int* fail) {
+    __shared__ double Lpp[CHOL_NB][CHOL_NB + 1];
+    const int nb = min(CHOL_NB, n - jb);
+    for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += blockDim.x) {
+        const int r = t / CHOL_NB, c = t % CHOL_NB;
+        Lpp[r][c] = (r < nb && c <= r) ? L[(size_t)(jb + r) * n + jb + c] : 0.0;
+    }
+    __syncthreads();
+    if (*(volatile int*)fail) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= jb + nb) return;
+    double w[CHOL_NB];
+#pragma unroll
+    for (int r = 0; r < CHOL_NB; ++r) {
+        if (r < nb) {
+            double acc = W[(size_t)(jb + r) * n + j];
+            for (int m = 0; m < r; ++m) acc -= Lpp[r][m] * w[m];
+            w[r] = acc / Lpp[r][r];
+            W[(size_t)(jb + r) * n + j] = w[r];
+        }
+    }
+}
+
+// Rows below panel p: R_ij -= sum_m l_i,jb+m w_jb+m,j for i >= e, j < e (e = the panel's end).
+__global__ void __launch_bounds__(256) k_trinv_update(int n, int jb, const double* L, double* W, const int* fail) {
+    __shared__ double Ls[DT_T][DT_K + 1], Ws[DT_T][DT_K + 1];
+    if (*(volatile int*)fail) return;
+    const int nb = min(CHOL_NB, n - jb);
+    const int e = jb + nb;
+    const int i0 = e + blockIdx.y * DT_T, j0 = blockIdx.x * DT_T;
+    dt_load_rows(Ls, L, n, i0, jb, n, e);           // rows i, panel columns
+    dt_load_cols(Ws, W, n, jb, j0, e, e);           // panel rows of W, columns j < e (transposed)
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    dt_mac(Ls, Ws, acc, tx, ty);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+            if (i < n && j < e) W[(size_t)i * n + j] -= acc[a][b];
+        }
+}
+
+// A^{-1} = W^T W: block (bi, bj) with bj <= bi computes the 64 x 64 tile
+// x_ij = sum_k w_ki w_kj over k >= max(i0, j0) = i0 (W is lower triangular) and writes it at
+// (i, j) and (j, i).
+__global__ void __launch_bounds__(256) k_lauum(int n, const double* W, double* X, const int* fail) {
+    __shared__ double Wi[DT_T][DT_K + 1], Wj[DT_T][DT_K + 1];
+    if (*(volatile int*)fail) return;
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bj > bi) return;
+    const int i0 = bi * DT_T, j0 = bj * DT_T;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int k0 = i0; k0 < n; k0 += DT_K) {
+        dt_load_cols(Wi, W, n, k0, i0, n, n);
+        dt_load_cols(Wj, W, n, k0, j0, n, n);
+        __syncthreads();
+        dt_mac(Wi, Wj, acc, tx, ty);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+            if (i < n && j < n) {
+                X[(size_t)i * n + j] = acc[a][b];
+                X[(size_t)j * n + i] = acc[a][b];
+            }
+        }
+}
+
+__global__ void k_identity(int n, double* W) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * n) return;
-    const int i = (int)(t / n), k = (int)(t % n);
-    if (k < i) M[(size_t)k * n + i] = M[t];
-}
-
-// Column c of A^{-1} (stored as row c; A^{-1} is symmetric): L y = e_c, then L^T x = y, in place.
-__global__ void k_chol_inverse(int n, const double* __restrict__ L, double* __restrict__ Ainv) {
-    const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (c >= n) return;
-    double* x = Ainv + (size_t)c * n;
-    for (int r = lane; r < c; r += 32) x[r] = 0.0;
-    for (int r = c; r < n; ++r) {                      // forward: rows of L are contiguous
-        const double* lr = L + (size_t)r * n;
-        double acc = 0.0;
-        for (int k = c + lane; k < r; k += 32) acc += lr[k] * x[k];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) x[r] = ((r == c ? 1.0 : 0.0) - acc) / lr[r];
-        __syncwarp();
-    }
-    for (int r = n - 1; r >= 0; --r) {                 // backward: column r of L = row r of the upper part
-        const double* ur = L + (size_t)r * n;
-        double acc = 0.0;
-        for (int k = r + 1 + lane; k < n; k += 32) acc += ur[k] * x[k];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) x[r] = (x[r] - acc) / ur[r];
-        __syncwarp();
-    }
+    const int i = (int)(t / n), j = (int)(t % n);
+    W[t] = i == j ? 1.0 : 0.0;
 }
 
 void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t s) {
@@ -1003,12 +1104,22 @@ void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t 
         const int below = n - jb - nb;
         if (below > 0) {
             k_chol_trsm<<<(below + 127) / 128, 128, 0, s>>>(n, jb, M, fail);
-            const int tiles = (below + CHOL_NB - 1) / CHOL_NB;
-            k_chol_syrk<<<dim3(tiles, tiles), CHOL_NB * CHOL_NB, 0, s>>>(n, jb, M, fail);
+            const int tiles = (below + DT_T - 1) / DT_T;
+            k_chol_syrk<<<dim3(tiles, tiles), 256, 0, s>>>(n, jb, M, fail);
         }
     }
-    k_chol_mirror<<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, M);
-    k_chol_inverse<<<(n + 7) / 8, 256, 0, s>>>(n, M, Ainv);
+    // W = L^{-1} in a scratch of its own, then A^{-1} = W^T W
+    Tmp<double> W((size_t)n * n, s);
+    k_identity<<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, W.get());
+    for (int jb = 0; jb < n; jb += CHOL_NB) {
+        const int e = std::min(jb + CHOL_NB, n);
+        k_trinv_panel<<<(e + 127) / 128, 128, 0, s>>>(n, jb, M, W.get(), fail);
+        if (e < n)
+            k_trinv_update<<<dim3((e + DT_T - 1) / DT_T, (n - e + DT_T - 1) / DT_T), 256, 0, s>>>(n, jb, M, W.get(),
+                                                                                                 fail);
+    }
+    const int tiles_all = (n + DT_T - 1) / DT_T;
+    k_lauum<<<dim3(tiles_all, tiles_all), 256, 0, s>>>(n, W.get(), Ainv, fail);
     CPC_LAUNCH_CK();
 }
 
