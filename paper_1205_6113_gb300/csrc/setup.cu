@@ -414,14 +414,23 @@ __global__ void k_peel_mark(int n, const int* deg, int* rnd, int* dmin, int r, i
     }
 }
 
-__global__ void k_peel_update(int n, const int* ptr, const int* col, int* deg, const int* rnd, int r, int* dmin) {
+// Each point taken in round r lowers the degree of its neighbours still left by one (the pattern
+// is symmetric, so this equals each remaining point counting its neighbours taken in round r, in
+// work proportional to the rows taken instead of the rows left).
+__global__ void k_peel_push(int n, const int* ptr, const int* col, int* deg, const int* rnd, int r) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || rnd[i] != r) return;
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+        const int j = col[p];
+        if (j != i && rnd[j] < 0) atomicSub(&deg[j], 1);
+    }
+}
+
+// The smallest degree left for round r + 1.
+__global__ void k_peel_min(int n, const int* deg, const int* rnd, int r, int* dmin) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || rnd[i] >= 0) return;
-    int c = 0;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p) c += col[p] != i && rnd[col[p]] == r;
-    const int d = deg[i] - c;
-    deg[i] = d;
-    atomicMin(&dmin[(r + 1) & 1], d);
+    atomicMin(&dmin[(r + 1) & 1], deg[i]);
 }
 
 // ============================================================================================
@@ -435,23 +444,27 @@ __device__ __forceinline__ bool jp_beats(int rj, int j, int ri, uint32_t hi) {
     return rj > ri || (rj == ri && fmix32((uint32_t)j ^ COLOUR_SEED) > hi);
 }
 
-// blk[i]: the uncoloured neighbour of higher priority that stopped point i last time (-1: none);
-// while it stays uncoloured the point is skipped without scanning its row.
-__global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd, int* colour, int* blk, int* done) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    volatile int* vc = colour;
-    if (vc[i] >= 0) return;
-    const int b = blk[i];
-    if (b >= 0 && vc[b] < 0) return;
+// blk[i]: the position in row i of the uncoloured neighbour of higher priority that stopped point
+// i last time (-1: none yet).  While that neighbour stays uncoloured the point is skipped; once it
+// is coloured the scan resumes after it: the entries before it were of lower priority or already
+// coloured, and stay so.  Returns true when point i is coloured (by this call or before).
+__device__ bool jp_try(int i, const int* ptr, const int* col, const int* rnd, volatile int* vc, int* blk) {
+    if (vc[i] >= 0) return true;
+    const int p0 = ptr[i], p1 = ptr[i + 1];
+    int p = blk[i];
+    if (p >= 0) {
+        if (vc[col[p]] < 0) return false;
+        ++p;
+    } else {
+        p = p0;
+    }
     const int ri = rnd[i];
     const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
-    const int p0 = ptr[i], p1 = ptr[i + 1];
-    for (int p = p0; p < p1; ++p) {
+    for (; p < p1; ++p) {
         const int j = col[p];
         if (j != i && jp_beats(rnd[j], j, ri, hi) && vc[j] < 0) {
-            blk[i] = j;
-            return;
+            blk[i] = p;
+            return false;
         }
     }
     for (int base = 0;; base += 64) {
@@ -464,10 +477,17 @@ __global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd
         }
         if (used != ~0ull) {
             vc[i] = base + __ffsll((long long)~used) - 1;
-            break;
+            return true;
         }
     }
-    atomicAdd(done, 1);
+}
+
+__global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd, int* colour, int* blk, int* done) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    volatile int* vc = colour;
+    if (vc[i] >= 0) return;
+    if (jp_try(i, ptr, col, rnd, vc, blk)) atomicAdd(done, 1);
 }
 
 // Breadth-first parity 2-colouring, propagated: every vertex adopts the smallest (root, parity^1)
@@ -880,8 +900,8 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 // ============================================================================================
 // Coarsest level: dense Cholesky A_c = L L^T and the explicit inverse (Algorithm 3.2, step 2(b)).
 // Blocked right-looking factorisation with panels of NB = 32 columns:
-//   k_chol_diag   factor the 32 x 32 diagonal block in shared memory (one block),
-//   k_chol_trsm   L21 = A21 L11^{-T}, one thread per row below the block,
+//   k_chol_diag   factor the 32 x 32 diagonal block with one warp and invert it,
+//   k_chol_trsm   L21 = A21 L11^{-T} as a tile product with that inverse,
 //   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles;
 // then W = L^{-1} by row panels (k_trinv_panel, k_trinv_update) and A_c^{-1} = W^T W (k_lauum).
 // L is left in the lower triangle of M.
@@ -894,53 +914,75 @@ __global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const doub
     for (int p = ptr[i]; p < ptr[i + 1]; ++p) M[(size_t)i * n + col[p]] = val[p];
 }
 
-__global__ void __launch_bounds__(CHOL_NB * CHOL_NB) k_chol_diag(int n, int jb, double* M, int* fail) {
+// Factor the nb x nb diagonal block (nb <= 32) with one warp in shared memory (lane c updates
+// column c), write L11 back, and write Li = L11^{-1} (lower triangular, 32 x 32 with zeros beyond
+// nb) for the tile products of the panel: each lane solves L11 x = e_c for its column.
+__global__ void __launch_bounds__(32) k_chol_diag(int n, int jb, double* M, double* Li, int* fail) {
     __shared__ double D[CHOL_NB][CHOL_NB + 1];
-    __shared__ int bad;
+    __shared__ double rd[CHOL_NB];
+    const int lane = threadIdx.x;
     const int nb = min(CHOL_NB, n - jb);
-    const int r = threadIdx.x / CHOL_NB, c = threadIdx.x % CHOL_NB;
-    if (threadIdx.x == 0) bad = *(volatile int*)fail;
-    if (r < nb && c <= r) D[r][c] = M[(size_t)(jb + r) * n + jb + c];
-    __syncthreads();
-    if (bad) return;
+    if (*(volatile int*)fail) return;
+    for (int r = 0; r < CHOL_NB; ++r) D[r][lane] = (r < nb && lane <= r) ? M[(size_t)(jb + r) * n + jb + lane] : 0.0;
+    __syncwarp();
     for (int j = 0; j < nb; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = D[j][j];
-            if (!(d > 0.0) || !isfinite(d)) bad = 1;
-            else D[j][j] = sqrt(d);
+        const double d = D[j][j];
+        if (!(d > 0.0) || !isfinite(d)) {                    // every lane reads the same d
+            if (lane == 0) *fail = 1;
+            return;
         }
-        __syncthreads();
-        if (bad) break;
-        if (c == j && r > j && r < nb) D[r][j] /= D[j][j];
-        __syncthreads();
-        if (r > j && r < nb && c > j && c <= r) D[r][c] -= D[r][j] * D[c][j];
-        __syncthreads();
+        __syncwarp();
+        if (lane == j) D[j][j] = sqrt(d);
+        __syncwarp();
+        if (lane > j && lane < nb) D[lane][j] /= D[j][j];
+        __syncwarp();
+        if (lane > j && lane < nb)
+            for (int r = lane; r < nb; ++r) D[r][lane] -= D[r][j] * D[lane][j];
+        __syncwarp();
     }
-    if (bad) {
-        if (threadIdx.x == 0) *fail = 1;
-        return;
+    for (int r = lane; r < nb; ++r) M[(size_t)(jb + r) * n + jb + lane] = D[r][lane];
+    if (lane < nb) rd[lane] = 1.0 / D[lane][lane];
+    __syncwarp();
+    double x[CHOL_NB];
+#pragma unroll
+    for (int r = 0; r < CHOL_NB; ++r) {
+        double v = 0.0;
+        if (r >= lane && r < nb) {
+            v = r == lane ? 1.0 : 0.0;
+            for (int m = lane; m < r; ++m) v -= D[r][m] * x[m];
+            v *= rd[r];
+        }
+        x[r] = v;
     }
-    if (r < nb && c <= r) M[(size_t)(jb + r) * n + jb + c] = D[r][c];
+#pragma unroll
+    for (int r = 0; r < CHOL_NB; ++r) Li[r * CHOL_NB + lane] = x[r];
 }
 
-// Rows i >= jb + nb of the panel: l_i = a_i L11^{-T} by forward substitution (one thread per row).
-__global__ void k_chol_trsm(int n, int jb, double* M, const int* fail) {
-    __shared__ double L11[CHOL_NB][CHOL_NB + 1];
-    const int nb = min(CHOL_NB, n - jb);
-    for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += blockDim.x) {
-        const int r = t / CHOL_NB, c = t % CHOL_NB;
-        L11[r][c] = (r < nb && c <= r) ? M[(size_t)(jb + r) * n + jb + c] : 0.0;
-    }
-    __syncthreads();
+// Rows i >= jb + nb of the panel: l_i = a_i L11^{-T} = a_i Li^T, a tile product (16 rows x 32
+// columns per block of 128 threads; each thread 4 columns of one row).
+__global__ void __launch_bounds__(128) k_chol_trsm(int n, int jb, double* M, const double* Li, const int* fail) {
+    __shared__ double As[16][CHOL_NB + 1], Ls[CHOL_NB][CHOL_NB + 1];
     if (*(volatile int*)fail) return;
-    const int i = jb + nb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double* row = M + (size_t)i * n + jb;
-    for (int k = 0; k < nb; ++k) {
-        double acc = row[k];
-        for (int m = 0; m < k; ++m) acc -= row[m] * L11[k][m];
-        row[k] = acc / L11[k][k];
+    const int nb = min(CHOL_NB, n - jb);
+    const int i0 = jb + nb + blockIdx.x * 16;
+    for (int t = threadIdx.x; t < 16 * CHOL_NB; t += 128) {
+        const int r = t / CHOL_NB, c = t % CHOL_NB;
+        As[r][c] = (i0 + r < n && c < nb) ? M[(size_t)(i0 + r) * n + jb + c] : 0.0;
     }
+    for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += 128) Ls[t / CHOL_NB][t % CHOL_NB] = Li[t];
+    __syncthreads();
+    const int row = threadIdx.x / 8, c0 = (threadIdx.x % 8) * 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int m = 0; m < CHOL_NB; ++m) {
+        const double a = As[row][m];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += a * Ls[c0 + q][m];
+    }
+    const int i = i0 + row;
+    if (i < n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (c0 + q < nb) M[(size_t)i * n + jb + c0 + q] = acc[q];
 }
 
 // FP64 tile products for the dense factorisation and inverse: one 256-thread block computes a
@@ -1012,30 +1054,34 @@ __global__ void __launch_bounds__(256) k_chol_syrk(int n, int jb, double* M, con
 }
 
 // Inverse of the lower factor, W = L^{-1}, by row panels (a triangular solve L W = I): panel p's
-// rows of W are L_pp^{-1} times the panel's rows of the running right-hand side R (R = I to start,
-// held in W), one thread per column j < e = the panel's end; W is lower triangular, so columns
-// from e on stay zero.
-__global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const double* L, double* W, const int* fail) {
-    __shared__ double Lpp[CHOL_NB][CHOL_NB + 1];
-    const int nb = min(CHOL_NB, n - jb);
-    for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += blockDim.x) {
-        const int r = t / CHOL_NB, c = t % CHOL_NB;
-        Lpp[r][c] = (r < nb && c <= r) ? L[(size_t)(jb + r) * n + jb + c] : 0.0;
-    }
-    __syncthreads();
+// rows of W are Li = L_pp^{-1} times the panel's rows of the running right-hand side R (R = I to
+// start, held in W), for columns j < e = the panel's end; W is lower triangular, so columns from e
+// on stay zero.  A tile product: 32 rows x 16 columns per block of 128 threads, each thread 4 rows
+// of one column.
+__global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const double* Li, double* W, const int* fail) {
+    __shared__ double Rs[CHOL_NB][17], Ls[CHOL_NB][CHOL_NB + 1];
     if (*(volatile int*)fail) return;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= jb + nb) return;
-    double w[CHOL_NB];
-#pragma unroll
-    for (int r = 0; r < CHOL_NB; ++r) {
-        if (r < nb) {
-            double acc = W[(size_t)(jb + r) * n + j];
-            for (int m = 0; m < r; ++m) acc -= Lpp[r][m] * w[m];
-            w[r] = acc / Lpp[r][r];
-            W[(size_t)(jb + r) * n + j] = w[r];
-        }
+    const int nb = min(CHOL_NB, n - jb);
+    const int e = jb + nb;
+    const int j0 = blockIdx.x * 16;
+    for (int t = threadIdx.x; t < CHOL_NB * 16; t += 128) {
+        const int r = t / 16, c = t % 16;
+        Rs[r][c] = (r < nb && j0 + c < e) ? W[(size_t)(jb + r) * n + j0 + c] : 0.0;
     }
+    for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += 128) Ls[t / CHOL_NB][t % CHOL_NB] = Li[t];
+    __syncthreads();
+    const int col = threadIdx.x % 16, r0 = (threadIdx.x / 16) * 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int m = 0; m < CHOL_NB; ++m) {
+        const double v = Rs[m][col];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += Ls[r0 + q][m] * v;
+    }
+    const int j = j0 + col;
+    if (j < e)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (r0 + q < nb) W[(size_t)(jb + r0 + q) * n + j] = acc[q];
 }
 
 // Rows below panel p: R_ij -= sum_m l_i,jb+m w_jb+m,j for i >= e, j < e (e = the panel's end).
@@ -1098,12 +1144,15 @@ __global__ void k_identity(int n, double* W) {
 }
 
 void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t s) {
+    const int np = (n + CHOL_NB - 1) / CHOL_NB;
+    Tmp<double> Li((size_t)np * CHOL_NB * CHOL_NB, s);         // L_pp^{-1} of every panel
     for (int jb = 0; jb < n; jb += CHOL_NB) {
         const int nb = std::min(CHOL_NB, n - jb);
-        k_chol_diag<<<1, CHOL_NB * CHOL_NB, 0, s>>>(n, jb, M, fail);
+        double* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
+        k_chol_diag<<<1, 32, 0, s>>>(n, jb, M, li, fail);
         const int below = n - jb - nb;
         if (below > 0) {
-            k_chol_trsm<<<(below + 127) / 128, 128, 0, s>>>(n, jb, M, fail);
+            k_chol_trsm<<<(below + 15) / 16, 128, 0, s>>>(n, jb, M, li, fail);
             const int tiles = (below + DT_T - 1) / DT_T;
             k_chol_syrk<<<dim3(tiles, tiles), 256, 0, s>>>(n, jb, M, fail);
         }
@@ -1113,7 +1162,8 @@ void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t 
     k_identity<<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, W.get());
     for (int jb = 0; jb < n; jb += CHOL_NB) {
         const int e = std::min(jb + CHOL_NB, n);
-        k_trinv_panel<<<(e + 127) / 128, 128, 0, s>>>(n, jb, M, W.get(), fail);
+        const double* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
+        k_trinv_panel<<<(e + 15) / 16, 128, 0, s>>>(n, jb, li, W.get(), fail);
         if (e < n)
             k_trinv_update<<<dim3((e + DT_T - 1) / DT_T, (n - e + DT_T - 1) / DT_T), 256, 0, s>>>(n, jb, M, W.get(),
                                                                                                  fail);
@@ -1413,7 +1463,7 @@ void colour_levels(Handle& h, cudaStream_t s) {
             k_fill_int<<<1, 32, 0, q>>>(J.cnt->get(), 1, n);     // points left
             k_peel_init<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(), J.dmin->get());
         } else if (phase == ColourJob::JP) {
-            J.a1 = mk(n, q);                                     // blocking neighbour per point
+            J.a1 = mk(n, q);                                     // blocking entry per point
             k_fill_int<<<nblk(n), TPB, 0, q>>>(J.a1->get(), n, -1);
             k_fill_int<<<nblk(n), TPB, 0, q>>>(L.colour.p, n, -1);
             CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));   // points coloured
@@ -1447,8 +1497,9 @@ void colour_levels(Handle& h, cudaStream_t s) {
                     for (int k = 0; k < 16; ++k, ++J.rounds) {
                         k_peel_mark<<<nblk(n), TPB, 0, q>>>(n, J.a0->get(), J.rnd->get(), J.dmin->get(), J.rounds,
                                                             J.cnt->get());
-                        k_peel_update<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(),
-                                                              J.rounds, J.dmin->get());
+                        k_peel_push<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(),
+                                                            J.rounds);
+                        k_peel_min<<<nblk(n), TPB, 0, q>>>(n, J.a0->get(), J.rnd->get(), J.rounds, J.dmin->get());
                     }
                     break;
                 case ColourJob::JP:
