@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(SELL_TPB) k_spmv_dia(DV<MT, DT> A, const XT* x
 // Rows of one colour are not coupled, so they update in parallel exactly as in sequential order.
 template <class MT, class DT, class FT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_gs(SV<MT, DT> A, int c0, int c1, const FT* f, VT* x) {
-    const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
+    const int k = c0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (k >= c1) return;
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, C = A.C, r = lane & (C - 1), g = lane / C;
@@ -421,7 +421,7 @@ __global__ void k_copy(int64_t n, const A* a, B* __restrict__ b) {
 // Forward solve with the unit lower factor, rows of one level: y_i = t_i - sum_{j<i} l_ij y_j.
 template <class MT, class TT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_lsolve(SV<MT, MT> L, int c0, int c1, const TT* t, VT* y) {
-    const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
+    const int k = c0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (k >= c1) return;
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, C = L.C, r = lane & (C - 1), g = lane / C;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(SELL_TPB) k_lsolve(SV<MT, MT> L, int c0, int c
 template <class MT, class VT, int U>
 __global__ void __launch_bounds__(SELL_TPB) k_usolve(SV<MT, MT> Uf, int c0, int c1, const VT* y, VT* w,
                                                       VT* zadd) {
-    const int k = c0 + blockIdx.x * WPB + (threadIdx.x >> 5);
+    const int k = c0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (k >= c1) return;
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, C = Uf.C, r = lane & (C - 1), g = lane / C;
@@ -727,6 +727,22 @@ template <class VT> const VT* ainv(const Handle& h);
 template <> const double* ainv<double>(const Handle& h) { return h.Ainv.p; }
 template <> const float* ainv<float>(const Handle& h) { return h.Ainv32.p; }
 
+// Warps per block of a colour step (or a triangular-solve level) over `chunks` SELL chunks (one
+// warp each).  FP64 issue is
+// about two lanes per clock per SM on this part, so a warp's row product occupies its SM's FP64
+// pipe for 16 clocks per entry per lane: a colour step packed into four-warp blocks on a few SMs
+// waits on their FP64 pipes, while one-warp blocks spread it over every SM.  Steps wide enough to
+// give every SM four warps keep four-warp blocks (measured: one-warp blocks were slower there).
+int gs_block_warps(int chunks) {
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        CPC_CK(cudaGetDevice(&dev));
+        CPC_CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        return n;
+    }();
+    return chunks >= 4 * sms ? WPB : 1;
+}
+
 template <class FT, class VT>
 void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
     const int c0 = L.S.seg[c], c1 = L.S.seg[c + 1];
@@ -754,16 +770,17 @@ void rec_gs(Level& L, int c, const FT* f, VT* x, cudaStream_t s) {
         });
         return;
     }
-    const int g = blocks_for_chunks(c1 - c0);
+    const int w = gs_block_warps(c1 - c0);
+    const int g = (c1 - c0 + w - 1) / w, tpb = 32 * w;
     with_u_gs(L.S.lanes, [&](auto u) {
         constexpr int U = decltype(u)::value;
         if constexpr (std::is_same<VT, double>::value) {
-            launch(k_gs<double, double, FT, VT, U>, g, SELL_TPB, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), c0, c1, f, x);
+            launch(k_gs<double, double, FT, VT, U>, g, tpb, s, view(L.S, (const double*)L.S.val.p, (const double*)L.S.dinv.p), c0, c1, f, x);
         } else {
             if (L.vt == VT_BF16)
-                launch(k_gs<__nv_bfloat16, float, FT, VT, U>, g, SELL_TPB, s, view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
+                launch(k_gs<__nv_bfloat16, float, FT, VT, U>, g, tpb, s, view(L.S, (const __nv_bfloat16*)L.S.val16.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
             else
-                launch(k_gs<float, float, FT, VT, U>, g, SELL_TPB, s, view(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
+                launch(k_gs<float, float, FT, VT, U>, g, tpb, s, view(L.S, (const float*)L.S.val32.p, (const float*)L.S.dinv32.p), c0, c1, f, x);
         }
     });
 }
@@ -945,14 +962,16 @@ void rec_ic_solve(Handle& h, const TT* t, VT* y, VT* w, VT* zadd, cudaStream_t s
     }
     for (int g = 0; g + 1 < (int)L.seg.size(); ++g) {
         const int c0 = L.seg[g], c1 = L.seg[g + 1];
+        const int w = gs_block_warps(c1 - c0);
         with_u(L.lanes, [&](auto u) {
-            launch(k_lsolve<VT, TT, VT, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB, s, lv, c0, c1, t, y);
+            launch(k_lsolve<VT, TT, VT, decltype(u)::value>, (c1 - c0 + w - 1) / w, 32 * w, s, lv, c0, c1, t, y);
         });
     }
     for (int g = 0; g + 1 < (int)U.seg.size(); ++g) {
         const int c0 = U.seg[g], c1 = U.seg[g + 1];
+        const int wb = gs_block_warps(c1 - c0);
         with_u(U.lanes, [&](auto u) {
-            launch(k_usolve<VT, VT, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB, s, uv, c0, c1,
+            launch(k_usolve<VT, VT, decltype(u)::value>, (c1 - c0 + wb - 1) / wb, 32 * wb, s, uv, c0, c1,
                    (const VT*)y, w, zadd);
         });
     }
@@ -1096,8 +1115,9 @@ float time_gs_sweep(const Sell& S, int n) {
         for (size_t c = 0; c + 1 < S.seg.size(); ++c) {
             const int c0 = S.seg[c], c1 = S.seg[c + 1];
             if (c1 <= c0) continue;
-            with_u_gs(S.lanes, [&](auto u) {         // the batch widths of the solve's colour steps
-                launch(k_gs<double, double, double, double, decltype(u)::value>, blocks_for_chunks(c1 - c0), SELL_TPB,
+            const int w = gs_block_warps(c1 - c0);
+            with_u_gs(S.lanes, [&](auto u) {         // the launch shapes of the solve's colour steps
+                launch(k_gs<double, double, double, double, decltype(u)::value>, (c1 - c0 + w - 1) / w, 32 * w,
                        cs, view(S, (const double*)S.val.p, (const double*)S.dinv.p), c0, c1, (const double*)f.p, x.p);
             });
         }
