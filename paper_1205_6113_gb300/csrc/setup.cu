@@ -390,49 +390,8 @@ __global__ void k_interp_fill(int n, const int* ptr, const int* col, const doubl
 // ============================================================================================
 // Colouring priority: peel rounds (a smallest-last style ordering).  deg_i = off-diagonal count of
 // row i; in round r every remaining point with deg_i <= 2 min_{remaining} deg takes round r, then
-// each remaining point loses one degree per entry of its row taken in round r.  Two dmin slots
-// alternate: round r reads slot r % 2 and the update fills slot (r + 1) % 2.
+// each remaining point loses one degree per entry of its row taken in round r.
 // ============================================================================================
-__global__ void k_peel_init(int n, const int* ptr, const int* col, int* deg, int* rnd, int* dmin) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int d = 0;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p) d += col[p] != i;
-    deg[i] = d;
-    rnd[i] = -1;
-    atomicMin(dmin, d);
-}
-
-__global__ void k_peel_mark(int n, const int* deg, int* rnd, int* dmin, int r, int* left) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int dm = dmin[r & 1];
-    if (i == 0) dmin[(r + 1) & 1] = INT_MAX;
-    if (i >= n || dm == INT_MAX) return;
-    if (rnd[i] < 0 && deg[i] <= 2 * dm) {
-        rnd[i] = r;
-        atomicSub(left, 1);
-    }
-}
-
-// Each point taken in round r lowers the degree of its neighbours still left by one (the pattern
-// is symmetric, so this equals each remaining point counting its neighbours taken in round r, in
-// work proportional to the rows taken instead of the rows left).
-__global__ void k_peel_push(int n, const int* ptr, const int* col, int* deg, const int* rnd, int r) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || rnd[i] != r) return;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
-        const int j = col[p];
-        if (j != i && rnd[j] < 0) atomicSub(&deg[j], 1);
-    }
-}
-
-// The smallest degree left for round r + 1.
-__global__ void k_peel_min(int n, const int* deg, const int* rnd, int r, int* dmin) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || rnd[i] >= 0) return;
-    atomicMin(&dmin[(r + 1) & 1], deg[i]);
-}
-
 // ============================================================================================
 // Jones-Plassmann colouring with priority (peel round, fmix32(i ^ COLOUR_SEED)): a point whose
 // neighbours of higher priority are all coloured takes the smallest colour they leave free.  Its
@@ -444,50 +403,231 @@ __device__ __forceinline__ bool jp_beats(int rj, int j, int ri, uint32_t hi) {
     return rj > ri || (rj == ri && fmix32((uint32_t)j ^ COLOUR_SEED) > hi);
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident).  Arrivals count up on *ctr (zero
+// before the launch); barrier number e completes when it reaches e * gridDim.x.  The wait gives up
+// after GBAR_NS or as soon as another CTA has given up (*err != 0), setting *err = 1; then every
+// thread of the CTA gets false and the kernel returns.
+constexpr unsigned long long GBAR_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtime_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_bar(unsigned long long* ctr, unsigned long long& epoch, int* err) {
+    __shared__ int ok;
+    ++epoch;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
+        const unsigned long long target = epoch * gridDim.x;
+        const unsigned long long t0 = gtime_ns();
+        int good = 1;
+        for (;;) {
+            unsigned long long v;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            if (*(volatile int*)err != 0 || gtime_ns() - t0 > GBAR_NS) {
+                atomicCAS(err, 0, 1);
+                good = 0;
+                break;
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+constexpr int COL_TPB = 256;
+constexpr int COL_G = 16;                                       // lanes per point in k_colour
+
+template <class Op>
+__device__ int block_reduce(int v, Op op, int identity) {
+    __shared__ int part[COL_TPB / 32];
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) part[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < COL_TPB / 32 ? part[threadIdx.x] : identity;
+        for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;                                                   // valid in thread 0
+}
+
 // blk[i]: the position in row i of the uncoloured neighbour of higher priority that stopped point
 // i last time (-1: none yet).  While that neighbour stays uncoloured the point is skipped; once it
 // is coloured the scan resumes after it: the entries before it were of lower priority or already
-// coloured, and stay so.  Returns true when point i is coloured (by this call or before).
-__device__ bool jp_try(int i, const int* ptr, const int* col, const int* rnd, volatile int* vc, int* blk) {
-    if (vc[i] >= 0) return true;
+// coloured, and stay so.  The scan of uncoloured point i from row position `start` on, by a group
+// of COL_G lanes (gl = lane in the group, gm = the group's lane mask, gs = its first lane in the
+// warp), COL_G entries at a time, so that the point waits on one round of loads per COL_G entries
+// instead of one per entry: records the first blocking entry in row order and returns false, or
+// takes the smallest colour left free by its neighbours of higher priority and returns true
+// (group-uniform).
+__device__ bool jp_scan_group(int i, int start, const int* ptr, const int* col, const int* rnd, volatile int* vc,
+                              int* blk, int gl, unsigned gm, int gs) {
     const int p0 = ptr[i], p1 = ptr[i + 1];
-    int p = blk[i];
-    if (p >= 0) {
-        if (vc[col[p]] < 0) return false;
-        ++p;
-    } else {
-        p = p0;
-    }
     const int ri = rnd[i];
     const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
-    for (; p < p1; ++p) {
-        const int j = col[p];
-        if (j != i && jp_beats(rnd[j], j, ri, hi) && vc[j] < 0) {
-            blk[i] = p;
+    for (int base = start; base < p1; base += COL_G) {
+        const int p = base + gl;
+        bool hit = false;
+        if (p < p1) {
+            const int j = col[p];
+            hit = j != i && jp_beats(rnd[j], j, ri, hi) && vc[j] < 0;
+        }
+        const unsigned bits = (__ballot_sync(gm, hit) >> gs) & ((1u << COL_G) - 1u);
+        if (bits) {
+            if (gl == 0) blk[i] = base + __ffs(bits) - 1;
             return false;
         }
     }
-    for (int base = 0;; base += 64) {
+    for (int cb = 0;; cb += 64) {
         unsigned long long used = 0ull;
-        for (int p = p0; p < p1; ++p) {
+        for (int p = p0 + gl; p < p1; p += COL_G) {
             const int j = col[p];
             if (j == i || !jp_beats(rnd[j], j, ri, hi)) continue;
             const int c = vc[j];
-            if (c >= base && c < base + 64) used |= 1ull << (c - base);
+            if (c >= cb && c < cb + 64) used |= 1ull << (c - cb);
         }
+        for (int o = COL_G / 2; o > 0; o >>= 1) used |= __shfl_xor_sync(gm, used, o);
         if (used != ~0ull) {
-            vc[i] = base + __ffsll((long long)~used) - 1;
+            if (gl == 0) vc[i] = cb + __ffsll((long long)~used) - 1;
             return true;
         }
     }
 }
 
-__global__ void k_jp_round(int n, const int* ptr, const int* col, const int* rnd, int* colour, int* blk, int* done) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// Peel rounds, then Jones-Plassmann rounds, of one level in one cooperative launch: the rules and
+// results of separate launches per round, with a grid barrier where a round's launch ended.  A
+// peel round is one pass (points with deg <= 2 dmin take the round and count a decrement on each
+// neighbour in dec[]) and a second pass after a barrier (remaining points apply their decrements,
+// and the next dmin is their minimum); decrements counted on points taken in the same round are
+// never read.  Each warp takes 32 points at a time, one per lane, and checks them in parallel
+// (taken this round; uncoloured and no longer blocked); the points that need a row pass (the
+// decrements; the scan) are then worked two at a time, each by a group of COL_G lanes.
+// scal: [0], [1] dmin of even / odd rounds; [2..4] points coloured in Jones-Plassmann round t
+// (slot 2 + t % 3: a slot is cleared one round before it is added to and read one barrier after);
+// [5] peel rounds; [6] Jones-Plassmann rounds.  *err: 1 a barrier gave up, 2 peel rounds or 3
+// colouring rounds beyond their bound.
+__global__ void __launch_bounds__(COL_TPB) k_colour(int n, const int* ptr, const int* col, int* deg, int* dec,
+                                                    int* rnd, int* colour, int* blk, int* scal,
+                                                    unsigned long long* bar, int* err) {
+    unsigned long long epoch = 0;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31, gl = lane % COL_G, gs = lane - gl;
+    const unsigned gm = ((1u << COL_G) - 1u) << gs;
+    const int w0 = tid - lane, wstride = nt;                   // this warp's first point, warp stride
+    auto imin = [](int a, int b) { return a < b ? a : b; };
+    auto iadd = [](int a, int b) { return a + b; };
+    int m = INT_MAX;
+    for (int i = tid; i < n; i += nt) {
+        int d = 0;
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) d += col[p] != i;
+        deg[i] = d;
+        dec[i] = 0;
+        rnd[i] = -1;
+        colour[i] = -1;
+        blk[i] = -1;
+        m = imin(m, d);
+    }
+    m = block_reduce(m, imin, INT_MAX);
+    if (threadIdx.x == 0 && m != INT_MAX) atomicMin(&scal[0], m);
+    if (!grid_bar(bar, epoch, err)) return;
+    int r = 0;
+    for (;; ++r) {
+        const int dm = __ldcg(&scal[r & 1]);
+        if (dm == INT_MAX) break;
+        if (r > n + 16) {
+            if (tid == 0) atomicCAS(err, 0, 2);
+            return;
+        }
+        if (tid == 0) scal[(r + 1) & 1] = INT_MAX;
+        for (int base = w0; base < n; base += wstride) {       // warp-uniform trip count
+            const int i = base + lane;
+            const bool take = i < n && __ldcg(&rnd[i]) < 0 && __ldcg(&deg[i]) <= 2 * dm;
+            if (take) rnd[i] = r;
+            unsigned bits = __ballot_sync(0xffffffffu, take);
+            while (bits) {                                      // two taken points at a time
+                const int b0 = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int b1 = bits ? __ffs(bits) - 1 : -1;
+                if (bits) bits &= bits - 1;
+                const int mine = gs == 0 ? b0 : b1;
+                if (mine >= 0) {
+                    const int ip = base + mine;
+                    for (int p = ptr[ip] + gl; p < ptr[ip + 1]; p += COL_G)
+                        if (col[p] != ip) atomicSub(&dec[col[p]], 1);
+                }
+            }
+        }
+        if (!grid_bar(bar, epoch, err)) return;
+        m = INT_MAX;
+        for (int i = tid; i < n; i += nt) {
+            if (__ldcg(&rnd[i]) >= 0) continue;
+            const int d = __ldcg(&deg[i]) + __ldcg(&dec[i]);
+            deg[i] = d;
+            dec[i] = 0;
+            m = imin(m, d);
+        }
+        m = block_reduce(m, imin, INT_MAX);
+        if (threadIdx.x == 0 && m != INT_MAX) atomicMin(&scal[(r + 1) & 1], m);
+        if (!grid_bar(bar, epoch, err)) return;
+    }
     volatile int* vc = colour;
-    if (vc[i] >= 0) return;
-    if (jp_try(i, ptr, col, rnd, vc, blk)) atomicAdd(done, 1);
+    int64_t coloured = 0;
+    for (int t = 0;; ++t) {
+        if (t > n + 32) {
+            if (tid == 0) atomicCAS(err, 0, 3);
+            return;
+        }
+        if (tid == 0) scal[2 + (t + 1) % 3] = 0;
+        int cnt = 0;
+        for (int base = w0; base < n; base += wstride) {       // warp-uniform trip count
+            const int i = base + lane;
+            bool ready = false;
+            int start = 0;
+            if (i < n && vc[i] < 0) {
+                const int b = blk[i];
+                if (b < 0) {
+                    ready = true;                               // first scan of the row
+                    start = ptr[i];
+                } else if (vc[col[b]] >= 0) {
+                    ready = true;                               // its blocker has been coloured
+                    start = b + 1;
+                }
+            }
+            unsigned bits = __ballot_sync(0xffffffffu, ready);
+            while (bits) {                                      // two ready points at a time
+                const int b0 = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int b1 = bits ? __ffs(bits) - 1 : -1;
+                if (bits) bits &= bits - 1;
+                const int s0 = __shfl_sync(0xffffffffu, start, b0);
+                const int s1 = __shfl_sync(0xffffffffu, start, b1 < 0 ? 0 : b1);
+                const int mine = gs == 0 ? b0 : b1;
+                if (mine >= 0 && jp_scan_group(base + mine, gs == 0 ? s0 : s1, ptr, col, rnd, vc, blk, gl, gm, gs) &&
+                    gl == 0)
+                    ++cnt;
+            }
+        }
+        cnt = block_reduce(cnt, iadd, 0);
+        if (threadIdx.x == 0 && cnt) atomicAdd(&scal[2 + t % 3], cnt);
+        if (!grid_bar(bar, epoch, err)) return;
+        coloured += __ldcg(&scal[2 + t % 3]);
+        if (coloured >= n) {
+            if (tid == 0) {
+                scal[5] = r;
+                scal[6] = t + 1;
+            }
+            return;
+        }
+    }
 }
 
 // Breadth-first parity 2-colouring, propagated: every vertex adopts the smallest (root, parity^1)
@@ -1395,19 +1535,59 @@ void wavefront_levels(Handle& h, cudaStream_t s) {
 }
 
 // Smoothing colours of levels [0, nl - 1): the breadth-first parity 2-colouring if the pattern
-// graph is bipartite, else Jones-Plassmann with peel-round priority.  Every level is a small state
-// machine of round loops on its own stream; all levels advance one batch of launches at a time
-// (16 peel rounds, 32 Jones-Plassmann rounds: rounds after completion change nothing) and then read
-// their counters, so the setup waits for the longest chain of rounds, not their sum.
+// graph is bipartite, else Jones-Plassmann with peel-round priority.  The bipartite probe and the
+// parity propagation run as small state machines of round loops, one stream per level, all levels
+// advancing one batch of launches at a time (16 rounds: rounds after the fixed point change
+// nothing) before they read their counters.  The levels that are not bipartite are then coloured
+// one after another, each by one cooperative launch of k_colour that runs all its rounds.
 struct ColourJob {
-    enum Phase { TRI, BIP, BIP_CHECK, PEEL, JP, MAX, DONE };
+    enum Phase { TRI, BIP, BIP_CHECK, MAX, JP, DONE };
     int l = 0, n = 0, phase = TRI, rounds = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     int* pin = nullptr;                                         // pinned counter read back per batch
-    std::unique_ptr<Tmp<int>> a0, a1, a2, a3, cnt;              // phase buffers
-    std::unique_ptr<Tmp<int>> rnd, dmin;
+    std::unique_ptr<Tmp<int>> a0, cnt;                          // phase buffers
 };
+
+// Peel and Jones-Plassmann rounds of level L in one cooperative launch (k_colour).
+void colour_jp(Level& L, cudaStream_t s) {
+    const int n = L.n;
+    Tmp<int> deg(n, s), dec(n, s), rnd(n, s), blk(n, s), scal(8, s), err(1, s);
+    Tmp<unsigned long long> bar(1, s);
+    k_fill_int<<<1, 32, 0, s>>>(scal.get(), 2, INT_MAX);
+    CPC_CK(cudaMemsetAsync(scal.get() + 2, 0, sizeof(int) * 6, s));
+    CPC_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    CPC_CK(cudaMemsetAsync(bar.get(), 0, sizeof(unsigned long long), s));
+    int dev = 0, sms = 0, per_sm = 0;
+    CPC_CK(cudaGetDevice(&dev));
+    CPC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CPC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour, COL_TPB, 0));
+    if (per_sm < 1) fail(CPC_ESETUP, "colouring kernel does not fit on an SM");
+    // up to four CTAs per SM, one thread per point at most
+    const int grid = std::max(1, std::min(std::min(per_sm, 4) * sms, nblk(n, COL_TPB)));
+    int* pdeg = deg.get();
+    int* pdec = dec.get();
+    int* prnd = rnd.get();
+    int* pblk = blk.get();
+    int* pscal = scal.get();
+    int* perr = err.get();
+    unsigned long long* pbar = bar.get();
+    const int* ptr = L.A.ptr.p;
+    const int* col = L.A.col.p;
+    int* colour = L.colour.p;
+    int nn = n;
+    void* args[] = {&nn, (void*)&ptr, (void*)&col, &pdeg, &pdec, &prnd, &colour, &pblk, &pscal, &pbar, &perr};
+    CPC_CK(cudaLaunchCooperativeKernel((void*)k_colour, grid, COL_TPB, args, 0, s));
+    const int e = d2h(err.get(), s);
+    if (e == 1) fail(CPC_ESETUP, "colouring: a grid barrier gave up");
+    if (e == 2) fail(CPC_ESETUP, "peel rounds did not terminate");
+    if (e == 3) fail(CPC_ESETUP, "colouring did not terminate");
+    Tmp<int> mx(1, s);
+    CPC_CK(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+    k_max_int<<<nblk(n), TPB, 0, s>>>(colour, n, mx.get());
+    CPC_LAUNCH_CK();
+    L.ncolours = d2h(mx.get(), s) + 1;
+}
 
 void colour_levels(Handle& h, cudaStream_t s) {
     const int nl = (int)h.lev.size();
@@ -1447,32 +1627,17 @@ void colour_levels(Handle& h, cudaStream_t s) {
         CPC_CK(cudaEventRecord(J.ev, J.st));
     };
     auto enter = [&](ColourJob& J, int phase) {                 // allocate and initialise a phase
-        const Level& L = h.lev[J.l];
-        const int n = J.n;
-        cudaStream_t q = J.st;
         J.phase = phase;
         J.rounds = 0;
         if (phase == ColourJob::BIP) {
-            J.a0 = mk(n, q);                                     // (root, parity) words
-            k_bip_init<<<nblk(n), TPB, 0, q>>>(n, (unsigned*)J.a0->get());
-        } else if (phase == ColourJob::PEEL) {
-            J.a0 = mk(n, q);                                     // degrees
-            J.rnd = mk(n, q);
-            J.dmin = mk(2, q);
-            k_fill_int<<<1, 32, 0, q>>>(J.dmin->get(), 2, INT_MAX);
-            k_fill_int<<<1, 32, 0, q>>>(J.cnt->get(), 1, n);     // points left
-            k_peel_init<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(), J.dmin->get());
-        } else if (phase == ColourJob::JP) {
-            J.a1 = mk(n, q);                                     // blocking entry per point
-            k_fill_int<<<nblk(n), TPB, 0, q>>>(J.a1->get(), n, -1);
-            k_fill_int<<<nblk(n), TPB, 0, q>>>(L.colour.p, n, -1);
-            CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));   // points coloured
+            J.a0 = mk(J.n, J.st);                                // (root, parity) words
+            k_bip_init<<<nblk(J.n), TPB, 0, J.st>>>(J.n, (unsigned*)J.a0->get());
         }
     };
     for (auto& J : jobs) J.cnt = mk(1, J.st);
     for (int active = nj; active > 0;) {
         for (auto& J : jobs) {                                  // one batch per unfinished level
-            if (J.phase == ColourJob::DONE) continue;
+            if (J.phase == ColourJob::DONE || J.phase == ColourJob::JP) continue;
             const Level& L = h.lev[J.l];
             const int n = J.n;
             cudaStream_t q = J.st;
@@ -1493,21 +1658,6 @@ void colour_levels(Handle& h, cudaStream_t s) {
                     k_bip_check<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, (const unsigned*)J.a0->get(),
                                                         J.cnt->get());
                     break;
-                case ColourJob::PEEL:
-                    for (int k = 0; k < 16; ++k, ++J.rounds) {
-                        k_peel_mark<<<nblk(n), TPB, 0, q>>>(n, J.a0->get(), J.rnd->get(), J.dmin->get(), J.rounds,
-                                                            J.cnt->get());
-                        k_peel_push<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.a0->get(), J.rnd->get(),
-                                                            J.rounds);
-                        k_peel_min<<<nblk(n), TPB, 0, q>>>(n, J.a0->get(), J.rnd->get(), J.rounds, J.dmin->get());
-                    }
-                    break;
-                case ColourJob::JP:
-                    for (int k = 0; k < 32; ++k)
-                        k_jp_round<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.rnd->get(), L.colour.p,
-                                                           J.a1->get(), J.cnt->get());
-                    J.rounds += 32;
-                    break;
                 case ColourJob::MAX:
                     CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
                     k_max_int<<<nblk(n), TPB, 0, q>>>(L.colour.p, n, J.cnt->get());
@@ -1517,13 +1667,18 @@ void colour_levels(Handle& h, cudaStream_t s) {
             readback(J);
         }
         for (auto& J : jobs) {                                  // read the counters, advance phases
-            if (J.phase == ColourJob::DONE) continue;
+            if (J.phase == ColourJob::DONE || J.phase == ColourJob::JP) continue;
             CPC_CK(cudaEventSynchronize(J.ev));
             const int v = *J.pin;
             Level& L = h.lev[J.l];
             switch (J.phase) {
                 case ColourJob::TRI:
-                    enter(J, v ? ColourJob::PEEL : ColourJob::BIP);
+                    if (v) {
+                        J.phase = ColourJob::JP;                 // has a triangle: not bipartite
+                        --active;
+                    } else {
+                        enter(J, ColourJob::BIP);
+                    }
                     break;
                 case ColourJob::BIP:
                     if (v == 0) enter(J, ColourJob::BIP_CHECK);
@@ -1534,16 +1689,9 @@ void colour_levels(Handle& h, cudaStream_t s) {
                         k_bip_unpack<<<nblk(J.n), TPB, 0, J.st>>>(J.n, (const unsigned*)J.a0->get(), L.colour.p);
                         enter(J, ColourJob::MAX);
                     } else {
-                        enter(J, ColourJob::PEEL);
+                        J.phase = ColourJob::JP;
+                        --active;
                     }
-                    break;
-                case ColourJob::PEEL:
-                    if (v == 0) enter(J, ColourJob::JP);
-                    else if (J.rounds > J.n + 16) fail(CPC_ESETUP, "peel rounds did not terminate");
-                    break;
-                case ColourJob::JP:
-                    if (v == J.n) enter(J, ColourJob::MAX);
-                    else if (J.rounds > J.n + 32) fail(CPC_ESETUP, "colouring did not terminate");
                     break;
                 case ColourJob::MAX:
                     L.ncolours = v + 1;
@@ -1554,6 +1702,9 @@ void colour_levels(Handle& h, cudaStream_t s) {
         }
     }
     for (auto& J : jobs) CPC_CK(cudaStreamSynchronize(J.st));
+    // a cooperative grid takes the whole GPU: levels one after another, on the setup stream
+    for (auto& J : jobs)
+        if (J.phase == ColourJob::JP) colour_jp(h.lev[J.l], s);
 }
 
 // One coarsening step on level l; returns false when l becomes the coarsest level.
