@@ -444,6 +444,7 @@ __device__ bool grid_bar(unsigned long long* ctr, unsigned long long& epoch, int
 
 constexpr int COL_TPB = 256;
 constexpr int COL_G = 16;                                       // lanes per point in k_colour
+constexpr int COL_K = 4;                                        // points per lane whose loads overlap
 
 template <class Op>
 __device__ int block_reduce(int v, Op op, int identity) {
@@ -461,39 +462,62 @@ __device__ int block_reduce(int v, Op op, int identity) {
 }
 
 // blk[i]: the position in row i of the uncoloured neighbour of higher priority that stopped point
-// i last time (-1: none yet).  While that neighbour stays uncoloured the point is skipped; once it
-// is coloured the scan resumes after it: the entries before it were of lower priority or already
-// coloured, and stay so.  The scan of uncoloured point i from row position `start` on, by a group
-// of COL_G lanes (gl = lane in the group, gm = the group's lane mask, gs = its first lane in the
-// warp), COL_G entries at a time, so that the point waits on one round of loads per COL_G entries
-// instead of one per entry: records the first blocking entry in row order and returns false, or
-// takes the smallest colour left free by its neighbours of higher priority and returns true
-// (group-uniform).
-__device__ bool jp_scan_group(int i, int start, const int* ptr, const int* col, const int* rnd, volatile int* vc,
-                              int* blk, int gl, unsigned gm, int gs) {
+// i last time (-1: none yet).  While that neighbour stays uncoloured the point is skipped.  Once it
+// is coloured, the point's row is examined again by a group of COL_G lanes (gl = lane in the
+// group, gm = the group's lane mask, gs = its first lane in the warp), COL_U entries per lane per
+// pass, with all loads of a pass in flight together: the first uncoloured neighbour of higher
+// priority in row order is recorded and false returned; if there is none, the point takes the
+// smallest colour left free by its neighbours of higher priority (from the colours just loaded
+// when the row fits one pass) and true is returned (group-uniform).  Entries before the old
+// blocking entry are examined again although they cannot block (lower priority, or coloured for
+// good): with the loads in flight together that costs nothing, and their colours are needed.
+constexpr int COL_U = 4;
+
+__device__ bool jp_group(int i, const int* ptr, const int* col, const int* rnd, volatile int* vc, int* blk, int gl,
+                         unsigned gm, int gs) {
     const int p0 = ptr[i], p1 = ptr[i + 1];
     const int ri = rnd[i];
     const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
-    for (int base = start; base < p1; base += COL_G) {
-        const int p = base + gl;
-        bool hit = false;
-        if (p < p1) {
-            const int j = col[p];
-            hit = j != i && jp_beats(rnd[j], j, ri, hi) && vc[j] < 0;
+    constexpr int W = COL_U * COL_G;                             // entries per pass
+    int cj[COL_U];
+    bool up[COL_U];                                             // neighbour of higher priority
+    for (int base = p0; base < p1; base += W) {
+        int j[COL_U];
+#pragma unroll
+        for (int u = 0; u < COL_U; ++u) {
+            const int p = base + u * COL_G + gl;
+            j[u] = p < p1 ? col[p] : -1;
         }
-        const unsigned bits = (__ballot_sync(gm, hit) >> gs) & ((1u << COL_G) - 1u);
-        if (bits) {
-            if (gl == 0) blk[i] = base + __ffs(bits) - 1;
-            return false;
+#pragma unroll
+        for (int u = 0; u < COL_U; ++u) {
+            const bool e = j[u] >= 0 && j[u] != i;
+            const int rj = e ? rnd[j[u]] : 0;                   // both loads in flight together
+            cj[u] = e ? vc[j[u]] : 0;
+            up[u] = e && jp_beats(rj, j[u], ri, hi);
+        }
+#pragma unroll
+        for (int u = 0; u < COL_U; ++u) {
+            const unsigned bits = (__ballot_sync(gm, up[u] && cj[u] < 0) >> gs) & ((1u << COL_G) - 1u);
+            if (bits) {
+                if (gl == 0) blk[i] = base + u * COL_G + __ffs(bits) - 1;
+                return false;
+            }
         }
     }
+    const bool one = p1 - p0 <= W;                              // colours of the only pass still at hand
     for (int cb = 0;; cb += 64) {
         unsigned long long used = 0ull;
-        for (int p = p0 + gl; p < p1; p += COL_G) {
-            const int j = col[p];
-            if (j == i || !jp_beats(rnd[j], j, ri, hi)) continue;
-            const int c = vc[j];
-            if (c >= cb && c < cb + 64) used |= 1ull << (c - cb);
+        if (one) {
+#pragma unroll
+            for (int u = 0; u < COL_U; ++u)
+                if (up[u] && cj[u] >= cb && cj[u] < cb + 64) used |= 1ull << (cj[u] - cb);
+        } else {
+            for (int p = p0 + gl; p < p1; p += COL_G) {
+                const int j = col[p];
+                if (j == i || !jp_beats(rnd[j], j, ri, hi)) continue;
+                const int c = vc[j];
+                if (c >= cb && c < cb + 64) used |= 1ull << (c - cb);
+            }
         }
         for (int o = COL_G / 2; o > 0; o >>= 1) used |= __shfl_xor_sync(gm, used, o);
         if (used != ~0ull) {
@@ -503,172 +527,391 @@ __device__ bool jp_scan_group(int i, int start, const int* ptr, const int* col, 
     }
 }
 
-// Peel rounds, then Jones-Plassmann rounds, of one level in one cooperative launch: the rules and
-// results of separate launches per round, with a grid barrier where a round's launch ended.  A
-// peel round is one pass (points with deg <= 2 dmin take the round and count a decrement on each
-// neighbour in dec[]) and a second pass after a barrier (remaining points apply their decrements,
-// and the next dmin is their minimum); decrements counted on points taken in the same round are
-// never read.  Each warp takes 32 points at a time, one per lane, and checks them in parallel
-// (taken this round; uncoloured and no longer blocked); the points that need a row pass (the
-// decrements; the scan) are then worked two at a time, each by a group of COL_G lanes.
-// scal: [0], [1] dmin of even / odd rounds; [2..4] points coloured in Jones-Plassmann round t
-// (slot 2 + t % 3: a slot is cleared one round before it is added to and read one barrier after);
-// [5] peel rounds; [6] Jones-Plassmann rounds.  *err: 1 a barrier gave up, 2 peel rounds or 3
-// colouring rounds beyond their bound.
-__global__ void __launch_bounds__(COL_TPB) k_colour(int n, const int* ptr, const int* col, int* deg, int* dec,
-                                                    int* rnd, int* colour, int* blk, int* scal,
-                                                    unsigned long long* bar, int* err) {
-    unsigned long long epoch = 0;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31, gl = lane % COL_G, gs = lane - gl;
-    const unsigned gm = ((1u << COL_G) - 1u) << gs;
-    const int w0 = tid - lane, wstride = nt;                   // this warp's first point, warp stride
+// ---------------------------------------------------------------------------------------------
+// All levels are coloured by one cooperative launch of k_colour.  Each level runs its own state
+// machine, and all advance one step per grid barrier, so that the setup waits for the longest
+// chain of rounds, not their sum:
+//   init       degrees, round -1, colour -1, blocking entry -1, parity word, triangle probe
+//   parity     the breadth-first parity 2-colouring (only if no triangle was found): colour =
+//              distance parity from the smallest index of the component.  A union-find over the
+//              entries, each word (parent, parity relative to it), joins the two ends of every
+//              entry with opposite parities, always hooking the larger root under the smaller:
+//              the smallest index stays the root of its component, and for a bipartite graph the
+//              parity of a point relative to it is its distance parity (all paths agree)
+//   check      any entry joining two points of equal parity: not bipartite, colours reset, go to
+//              peel rounds
+//   peel       round r, step 1: points with deg <= 2 dmin take round r and count a decrement on
+//              each neighbour in dec[]; step 2: the remaining points apply their decrements and
+//              the next dmin is their minimum (decrements counted on points taken in the same
+//              round are never read)
+//   colour     Jones-Plassmann rounds (jp_group)
+// The CTAs of a step are shared among the levels with work in that step, in proportion to their
+// points (at least one each); a CTA works on one level.
+// ---------------------------------------------------------------------------------------------
+constexpr int COL_MAXL = 24;
+
+struct ColLev {
+    int n;
+    const int* ptr;
+    const int* col;
+    int* colour;
+    int *deg, *dec, *rnd, *blk;
+    unsigned* w;                              // union-find words
+    int* scal;                                // COL_NS counters, see below
+};
+
+// scal of a level: [0], [1] dmin of even / odd peel rounds; [2..4] points coloured in colour
+// round t (slot t % 3: a slot is cleared one round before it is added to and read one barrier
+// after); [5] triangle found; [6] not bipartite; [7] peel rounds; [8] colour rounds.
+enum { CS_DMIN = 0, CS_JP = 2, CS_TRI = 5, CS_BAD = 6, CS_PEEL_ROUNDS = 7, CS_JP_ROUNDS = 8, COL_NS = 12 };
+enum { CP_INIT, CP_UNION, CP_FIND, CP_CHECK, CP_RESET, CP_MARK, CP_MIN, CP_JP, CP_DONE };
+
+// Union-find words: parent << 1 | parity relative to the parent (a root: itself, parity 0).
+// Returns the root of x and x's parity relative to it, halving the path on the way (a point is
+// re-pointed to its grandparent with the composed parity, only if its word is still the one read).
+__device__ int uf_find(unsigned* uf, int x, int& par) {
+    volatile unsigned* v = uf;
+    int cur = x;
+    unsigned w = v[cur];
+    par = 0;
+    while ((int)(w >> 1) != cur) {
+        const int p = (int)(w >> 1);
+        const unsigned wp = v[p];
+        if ((int)(wp >> 1) == p) {                              // p is the root
+            par ^= (int)(w & 1u);
+            return p;
+        }
+        const unsigned nw = (wp & ~1u) | ((w ^ wp) & 1u);       // grandparent, composed parity
+        atomicCAS(&uf[cur], w, nw);
+        par ^= (int)((w ^ wp) & 1u);
+        cur = (int)(wp >> 1);
+        w = v[cur];
+    }
+    return cur;
+}
+
+// Joins a and b with opposite parities (the larger root is hooked under the smaller); false if
+// it has not succeeded within a bound of attempts (other joins keep winning the race).
+__device__ bool uf_join(unsigned* uf, int a, int b) {
+    for (int attempt = 0; attempt < (1 << 20); ++attempt) {
+        int pa, pb;
+        int ra = uf_find(uf, a, pa), rb = uf_find(uf, b, pb);
+        if (ra == rb) return true;
+        if (ra > rb) {
+            const int t = ra; ra = rb; rb = t;
+            const int u = pa; pa = pb; pb = u;
+        }
+        const unsigned x = (unsigned)(pa ^ pb ^ 1) & 1u;
+        if (atomicCAS(&uf[rb], (unsigned)rb << 1, ((unsigned)ra << 1) | x) == ((unsigned)rb << 1)) return true;
+    }
+    return false;
+}
+
+// A triangle at point i (adjacent neighbours j, k among its first 8 entries) proves that the
+// graph is not bipartite; finding none proves nothing.
+__device__ bool tri_probe(int i, const int* ptr, const int* col) {
+    const int p0 = ptr[i], p1 = min(ptr[i + 1], ptr[i] + 8);
+    for (int a = p0; a < p1; ++a) {
+        const int j = col[a];
+        if (j == i) continue;
+        for (int b = a + 1; b < p1; ++b) {
+            const int k = col[b];
+            if (k == i) continue;
+            int lo = ptr[j], hi = ptr[j + 1] - 1;              // columns ascending: binary search for k
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int c = col[mid];
+                if (c == k) return true;
+                if (c < k) lo = mid + 1; else hi = mid - 1;
+            }
+        }
+    }
+    return false;
+}
+
+// The work of one step of one level on the threads [t0, t0 + T) of its CTAs (t = t0 + local
+// index; whole CTAs, so that the block reductions see every thread of the CTA).
+__device__ void col_step(const ColLev& V, int phase, int rnd_no, int dm, int t, int T) {
     auto imin = [](int a, int b) { return a < b ? a : b; };
     auto iadd = [](int a, int b) { return a + b; };
-    int m = INT_MAX;
-    for (int i = tid; i < n; i += nt) {
-        int d = 0;
-        for (int p = ptr[i]; p < ptr[i + 1]; ++p) d += col[p] != i;
-        deg[i] = d;
-        dec[i] = 0;
-        rnd[i] = -1;
-        colour[i] = -1;
-        blk[i] = -1;
-        m = imin(m, d);
-    }
-    m = block_reduce(m, imin, INT_MAX);
-    if (threadIdx.x == 0 && m != INT_MAX) atomicMin(&scal[0], m);
-    if (!grid_bar(bar, epoch, err)) return;
-    int r = 0;
-    for (;; ++r) {
-        const int dm = __ldcg(&scal[r & 1]);
-        if (dm == INT_MAX) break;
-        if (r > n + 16) {
-            if (tid == 0) atomicCAS(err, 0, 2);
-            return;
-        }
-        if (tid == 0) scal[(r + 1) & 1] = INT_MAX;
-        for (int base = w0; base < n; base += wstride) {       // warp-uniform trip count
-            const int i = base + lane;
-            const bool take = i < n && __ldcg(&rnd[i]) < 0 && __ldcg(&deg[i]) <= 2 * dm;
-            if (take) rnd[i] = r;
-            unsigned bits = __ballot_sync(0xffffffffu, take);
-            while (bits) {                                      // two taken points at a time
-                const int b0 = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int b1 = bits ? __ffs(bits) - 1 : -1;
-                if (bits) bits &= bits - 1;
-                const int mine = gs == 0 ? b0 : b1;
-                if (mine >= 0) {
-                    const int ip = base + mine;
-                    for (int p = ptr[ip] + gl; p < ptr[ip + 1]; p += COL_G)
-                        if (col[p] != ip) atomicSub(&dec[col[p]], 1);
-                }
-            }
-        }
-        if (!grid_bar(bar, epoch, err)) return;
-        m = INT_MAX;
-        for (int i = tid; i < n; i += nt) {
-            if (__ldcg(&rnd[i]) >= 0) continue;
-            const int d = __ldcg(&deg[i]) + __ldcg(&dec[i]);
-            deg[i] = d;
-            dec[i] = 0;
+    const int n = V.n;
+    const int* ptr = V.ptr;
+    const int* col = V.col;
+    const int lane = threadIdx.x & 31, gl = lane % COL_G, gs = lane - gl;
+    const unsigned gm = ((1u << COL_G) - 1u) << gs;
+    if (phase == CP_INIT) {
+        int m = INT_MAX, tri = 0;
+        for (int i = t; i < n; i += T) {
+            int d = 0;
+            for (int p = ptr[i]; p < ptr[i + 1]; ++p) d += col[p] != i;
+            V.deg[i] = d;
+            V.dec[i] = 0;
+            V.rnd[i] = -1;
+            V.colour[i] = -1;
+            V.blk[i] = -1;
+            V.w[i] = (unsigned)i << 1;
             m = imin(m, d);
+            if (!tri) tri = tri_probe(i, ptr, col);
         }
         m = block_reduce(m, imin, INT_MAX);
-        if (threadIdx.x == 0 && m != INT_MAX) atomicMin(&scal[(r + 1) & 1], m);
-        if (!grid_bar(bar, epoch, err)) return;
-    }
-    volatile int* vc = colour;
-    int64_t coloured = 0;
-    for (int t = 0;; ++t) {
-        if (t > n + 32) {
-            if (tid == 0) atomicCAS(err, 0, 3);
-            return;
+        tri = block_reduce(tri, iadd, 0);
+        if (threadIdx.x == 0) {
+            if (m != INT_MAX) atomicMin(&V.scal[CS_DMIN], m);
+            if (tri) atomicOr(&V.scal[CS_TRI], 1);
         }
-        if (tid == 0) scal[2 + (t + 1) % 3] = 0;
-        int cnt = 0;
-        for (int base = w0; base < n; base += wstride) {       // warp-uniform trip count
-            const int i = base + lane;
-            bool ready = false;
-            int start = 0;
-            if (i < n && vc[i] < 0) {
-                const int b = blk[i];
-                if (b < 0) {
-                    ready = true;                               // first scan of the row
-                    start = ptr[i];
-                } else if (vc[col[b]] >= 0) {
-                    ready = true;                               // its blocker has been coloured
-                    start = b + 1;
+    } else if (phase == CP_UNION) {
+        int fail = 0;
+        for (int i = t; i < n; i += T)
+            for (int p = ptr[i]; p < ptr[i + 1]; ++p)
+                if (col[p] > i && !uf_join(V.w, i, col[p])) fail = 1;
+        fail = block_reduce(fail, iadd, 0);
+        if (threadIdx.x == 0 && fail) atomicOr(&V.scal[CS_BAD], 2);
+    } else if (phase == CP_FIND) {
+        for (int i = t; i < n; i += T) {
+            int par;
+            uf_find(V.w, i, par);
+            V.colour[i] = par;
+        }
+    } else if (phase == CP_CHECK) {
+        int bad = 0;
+        for (int i = t; i < n && !bad; i += T) {
+            const int ci = __ldcg(&V.colour[i]);
+            for (int p = ptr[i]; p < ptr[i + 1]; ++p)
+                if (col[p] != i && __ldcg(&V.colour[col[p]]) == ci) { bad = 1; break; }
+        }
+        bad = block_reduce(bad, iadd, 0);
+        if (threadIdx.x == 0 && bad) atomicOr(&V.scal[CS_BAD], 1);
+    } else if (phase == CP_RESET) {
+        for (int i = t; i < n; i += T) V.colour[i] = -1;
+    } else if (phase == CP_MARK) {
+        for (int b0 = t - lane; b0 < n; b0 += COL_K * T) {     // warp-uniform trip count
+            bool take[COL_K];
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) {                   // loads of COL_K points in flight
+                const int i = b0 + k * T + lane;
+                take[k] = i < n && __ldcg(&V.rnd[i]) < 0 && __ldcg(&V.deg[i]) <= 2 * dm;
+            }
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) {
+                const int base = b0 + k * T;
+                if (take[k]) V.rnd[base + lane] = rnd_no;
+                unsigned bits = __ballot_sync(0xffffffffu, take[k]);
+                while (bits) {                                  // two taken points at a time
+                    const int p0 = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int p1 = bits ? __ffs(bits) - 1 : -1;
+                    if (bits) bits &= bits - 1;
+                    const int mine = gs == 0 ? p0 : p1;
+                    if (mine >= 0) {
+                        const int ip = base + mine;
+                        for (int p = ptr[ip] + gl; p < ptr[ip + 1]; p += COL_G)
+                            if (col[p] != ip) atomicSub(&V.dec[col[p]], 1);
+                    }
                 }
             }
-            unsigned bits = __ballot_sync(0xffffffffu, ready);
-            while (bits) {                                      // two ready points at a time
-                const int b0 = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int b1 = bits ? __ffs(bits) - 1 : -1;
-                if (bits) bits &= bits - 1;
-                const int s0 = __shfl_sync(0xffffffffu, start, b0);
-                const int s1 = __shfl_sync(0xffffffffu, start, b1 < 0 ? 0 : b1);
-                const int mine = gs == 0 ? b0 : b1;
-                if (mine >= 0 && jp_scan_group(base + mine, gs == 0 ? s0 : s1, ptr, col, rnd, vc, blk, gl, gm, gs) &&
-                    gl == 0)
-                    ++cnt;
+        }
+    } else if (phase == CP_MIN) {
+        int m = INT_MAX;
+        for (int i0 = t; i0 < n; i0 += COL_K * T) {
+            int rv[COL_K], dv[COL_K], ev[COL_K];
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) {                   // loads of COL_K points in flight
+                const int i = i0 + k * T;
+                rv[k] = i < n ? __ldcg(&V.rnd[i]) : 0;
+                dv[k] = i < n ? __ldcg(&V.deg[i]) : 0;
+                ev[k] = i < n ? __ldcg(&V.dec[i]) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) {
+                const int i = i0 + k * T;
+                if (i >= n || rv[k] >= 0) continue;
+                const int d = dv[k] + ev[k];
+                V.deg[i] = d;
+                V.dec[i] = 0;
+                m = imin(m, d);
+            }
+        }
+        m = block_reduce(m, imin, INT_MAX);
+        if (threadIdx.x == 0 && m != INT_MAX) atomicMin(&V.scal[CS_DMIN + ((rnd_no + 1) & 1)], m);
+    } else if (phase == CP_JP) {
+        volatile int* vc = V.colour;
+        int cnt = 0;
+        for (int b0 = t - lane; b0 < n; b0 += COL_K * T) {     // warp-uniform trip count
+            int cv[COL_K], bv[COL_K], cb[COL_K], vb[COL_K];
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) {                   // loads of COL_K points in flight
+                const int i = b0 + k * T + lane;
+                cv[k] = i < n ? vc[i] : 0;
+                bv[k] = i < n ? V.blk[i] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) cb[k] = cv[k] < 0 && bv[k] >= 0 ? col[bv[k]] : -1;
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) vb[k] = cb[k] >= 0 ? vc[cb[k]] : -1;
+#pragma unroll
+            for (int k = 0; k < COL_K; ++k) {
+                const int base = b0 + k * T;
+                // uncoloured, and either never examined or its blocker has been coloured since
+                const bool ready = cv[k] < 0 && (bv[k] < 0 || vb[k] >= 0);
+                unsigned bits = __ballot_sync(0xffffffffu, ready);
+                while (bits) {                                  // two ready points at a time
+                    const int p0 = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int p1 = bits ? __ffs(bits) - 1 : -1;
+                    if (bits) bits &= bits - 1;
+                    const int mine = gs == 0 ? p0 : p1;
+                    if (mine >= 0 && jp_group(base + mine, ptr, col, V.rnd, vc, V.blk, gl, gm, gs) && gl == 0) ++cnt;
+                }
             }
         }
         cnt = block_reduce(cnt, iadd, 0);
-        if (threadIdx.x == 0 && cnt) atomicAdd(&scal[2 + t % 3], cnt);
-        if (!grid_bar(bar, epoch, err)) return;
-        coloured += __ldcg(&scal[2 + t % 3]);
-        if (coloured >= n) {
-            if (tid == 0) {
-                scal[5] = r;
-                scal[6] = t + 1;
+        if (threadIdx.x == 0 && cnt) atomicAdd(&V.scal[CS_JP + rnd_no % 3], cnt);
+    }
+}
+
+// *err: 1 a barrier gave up, 2 peel rounds or 3 colour rounds beyond their bound, 4 a union-find
+// join kept losing its race.
+// Each CTA keeps the level descriptors and the levels' phases in shared memory; at each step its
+// threads load every level's counters at once (they change only before a barrier), thread 0 takes
+// the phase decisions (the same in every CTA) and picks the CTA's level, and the CTA works on it.
+__global__ void __launch_bounds__(COL_TPB) k_colour(const ColLev* levs, int nlev, unsigned long long* bar, int* err) {
+    __shared__ ColLev lv[COL_MAXL];
+    __shared__ int sc[COL_MAXL * COL_NS];
+    __shared__ int ph[COL_MAXL], rr[COL_MAXL], work[COL_MAXL], dmv[COL_MAXL];
+    __shared__ long long done[COL_MAXL];
+    __shared__ int mine, c0s, cns, quit;
+    unsigned long long epoch = 0;
+    const bool lead = threadIdx.x == 0, first = lead && blockIdx.x == 0;
+    for (int l = threadIdx.x; l < nlev; l += blockDim.x) {
+        lv[l] = levs[l];
+        ph[l] = CP_INIT;
+        rr[l] = 0;
+        done[l] = 0;
+    }
+    __syncthreads();
+    for (int step = 0;; ++step) {
+        for (int q = threadIdx.x; q < nlev * COL_NS; q += blockDim.x) sc[q] = __ldcg(&lv[q / COL_NS].scal[q % COL_NS]);
+        __syncthreads();
+        if (lead) {
+            // transitions: every CTA reads the same counters and takes the same decisions
+            int active = 0;
+            long long wsum = 0;
+            quit = 0;
+            for (int l = 0; l < nlev && !quit; ++l) {
+                const int* c = sc + l * COL_NS;
+                int* g = lv[l].scal;
+                const int n = lv[l].n;
+                work[l] = -1;
+                for (;;) {                                      // a phase change may act at once
+                    const int p = ph[l];
+                    if (p == CP_INIT) {
+                        if (step == 0) { work[l] = CP_INIT; break; }
+                        ph[l] = c[CS_TRI] ? CP_MARK : CP_UNION;
+                        rr[l] = 0;
+                        if (ph[l] == CP_UNION) { work[l] = CP_UNION; break; }
+                    } else if (p == CP_UNION) {
+                        if (c[CS_BAD] & 2) { if (first) atomicCAS(err, 0, 4); quit = 1; break; }
+                        ph[l] = CP_FIND;
+                        work[l] = CP_FIND;
+                        break;
+                    } else if (p == CP_FIND) {
+                        ph[l] = CP_CHECK;
+                        work[l] = CP_CHECK;
+                        break;
+                    } else if (p == CP_CHECK) {
+                        if (c[CS_BAD]) {
+                            ph[l] = CP_RESET;
+                            work[l] = CP_RESET;
+                        } else {
+                            ph[l] = CP_DONE;
+                        }
+                        break;
+                    } else if (p == CP_RESET) {
+                        ph[l] = CP_MARK;
+                        rr[l] = 0;
+                    } else if (p == CP_MARK) {
+                        dmv[l] = c[CS_DMIN + (rr[l] & 1)];
+                        if (dmv[l] == INT_MAX) {
+                            if (first) g[CS_PEEL_ROUNDS] = rr[l];
+                            ph[l] = CP_JP;
+                            rr[l] = 0;
+                            continue;
+                        }
+                        if (rr[l] > n + 16) { if (first) atomicCAS(err, 0, 2); quit = 1; break; }
+                        if (first) g[CS_DMIN + ((rr[l] + 1) & 1)] = INT_MAX;
+                        work[l] = CP_MARK;
+                        break;
+                    } else if (p == CP_MIN) {
+                        work[l] = CP_MIN;
+                        break;
+                    } else if (p == CP_JP) {
+                        if (rr[l] > 0) {
+                            done[l] += c[CS_JP + (rr[l] - 1) % 3];
+                            if (done[l] >= n) {
+                                if (first) g[CS_JP_ROUNDS] = rr[l];
+                                ph[l] = CP_DONE;
+                                break;
+                            }
+                        }
+                        if (rr[l] > n + 32) { if (first) atomicCAS(err, 0, 3); quit = 1; break; }
+                        if (first) g[CS_JP + (rr[l] + 1) % 3] = 0;
+                        work[l] = CP_JP;
+                        break;
+                    } else {
+                        break;                                  // done
+                    }
+                }
+                if (work[l] >= 0) {
+                    ++active;
+                    wsum += n;
+                }
             }
-            return;
+            mine = -1;
+            if (!quit && active == 0) {
+                bool all = true;
+                for (int l = 0; l < nlev; ++l) all = all && ph[l] == CP_DONE;
+                quit = all ? 2 : 3;                             // 3: transitions only, no work, no barrier
+            }
+            if (!quit) {
+                // one CTA per level with work, the others in proportion to points
+                const int G = gridDim.x, spare = G - active;
+                int c0 = 0, cs = 0;
+                long long wacc = 0;
+                for (int l = 0; l < nlev && mine < 0; ++l) {
+                    if (work[l] < 0) continue;
+                    wacc += lv[l].n;
+                    const int c1 = (int)(((long long)spare * wacc) / wsum) + (++cs);
+                    if ((int)blockIdx.x >= c0 && (int)blockIdx.x < c1) {
+                        mine = l;
+                        c0s = c0;
+                        cns = c1 - c0;
+                    } else {
+                        c0 = c1;
+                    }
+                }
+            }
         }
+        __syncthreads();
+        if (quit == 1 || quit == 2) return;
+        if (quit == 3) continue;
+        if (mine >= 0) {
+            const int l = mine;
+            col_step(lv[l], work[l], rr[l], work[l] == CP_MARK ? dmv[l] : 0, ((int)blockIdx.x - c0s) * COL_TPB + threadIdx.x,
+                     cns * COL_TPB);
+        }
+        __syncthreads();
+        if (lead) {                                             // advance the phases worked in this step
+            for (int l = 0; l < nlev; ++l) {
+                if (work[l] == CP_JP) ++rr[l];
+                else if (work[l] == CP_MARK) ph[l] = CP_MIN;
+                else if (work[l] == CP_MIN) {
+                    ph[l] = CP_MARK;
+                    ++rr[l];
+                }
+            }
+        }
+        if (!grid_bar(bar, epoch, err)) return;
     }
-}
-
-// Breadth-first parity 2-colouring, propagated: every vertex adopts the smallest (root, parity^1)
-// offered by a neighbour; at the fixed point root = smallest index of the component and, for a
-// bipartite graph, parity = distance parity from it (the only 2-colouring with the root at 0).
-// (root, parity) is one word, 2 root + parity, updated in place: roots only decrease and each
-// point writes only its own word, so a round may use values written in the same round (fewer
-// rounds) and still reaches that fixed point.
-__global__ void k_bip_init(int n, unsigned* w) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) w[i] = (unsigned)i << 1;
-}
-
-__global__ void k_bip_round(int n, const int* ptr, const int* col, unsigned* w, int* changed) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    volatile unsigned* vw = w;
-    const unsigned v = vw[i];
-    unsigned best = v;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
-        const int j = col[p];
-        if (j == i) continue;
-        const unsigned vj = vw[j];
-        if ((vj >> 1) < (best >> 1)) best = vj ^ 1u;
-    }
-    if ((best >> 1) != (v >> 1)) {
-        vw[i] = best;
-        atomicAdd(changed, 1);
-    }
-}
-
-__global__ void k_bip_unpack(int n, const unsigned* w, int* colour) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) colour[i] = (int)(w[i] & 1u);
-}
-
-__global__ void k_bip_check(int n, const int* ptr, const int* col, const unsigned* w, int* bad) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p)
-        if (col[p] != i && ((w[col[p]] ^ w[i]) & 1u) == 0u) { atomicOr(bad, 1); return; }
 }
 
 // ============================================================================================
@@ -1497,29 +1740,6 @@ void setup_level_sells(Level& L, cudaStream_t s, bool last, bool tune) {
     }
 }
 
-// Triangle probe: point i with adjacent neighbours j, k (among its first 8 entries) proves the
-// graph is not bipartite.  Finding none proves nothing; the parity propagation then decides.
-__global__ void k_tri_probe(int n, const int* ptr, const int* col, int* found) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int p0 = ptr[i], p1 = min(ptr[i + 1], ptr[i] + 8);
-    for (int a = p0; a < p1; ++a) {
-        const int j = col[a];
-        if (j == i) continue;
-        for (int b = a + 1; b < p1; ++b) {
-            const int k = col[b];
-            if (k == i) continue;
-            int lo = ptr[j], hi = ptr[j + 1] - 1;        // columns ascending: binary search for k
-            while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
-                const int c = col[mid];
-                if (c == k) { atomicOr(found, 1); return; }
-                if (c < k) lo = mid + 1; else hi = mid - 1;
-            }
-        }
-    }
-}
-
 // Natural-order Gauss-Seidel ("standard GS", Section 3.3): the group of row i is its wavefront in the
 // lower-triangular dependency graph of A_l, w(i) = 1 + max w(j) over j < i with a_ij != 0 (0 when
 // there is none).  Rows of one wavefront are not coupled, and the pattern is symmetric, so every
@@ -1535,27 +1755,41 @@ void wavefront_levels(Handle& h, cudaStream_t s) {
 }
 
 // Smoothing colours of levels [0, nl - 1): the breadth-first parity 2-colouring if the pattern
-// graph is bipartite, else Jones-Plassmann with peel-round priority.  The bipartite probe and the
-// parity propagation run as small state machines of round loops, one stream per level, all levels
-// advancing one batch of launches at a time (16 rounds: rounds after the fixed point change
-// nothing) before they read their counters.  The levels that are not bipartite are then coloured
-// one after another, each by one cooperative launch of k_colour that runs all its rounds.
-struct ColourJob {
-    enum Phase { TRI, BIP, BIP_CHECK, MAX, JP, DONE };
-    int l = 0, n = 0, phase = TRI, rounds = 0;
-    cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    int* pin = nullptr;                                         // pinned counter read back per batch
-    std::unique_ptr<Tmp<int>> a0, cnt;                          // phase buffers
-};
-
-// Peel and Jones-Plassmann rounds of level L in one cooperative launch (k_colour).
-void colour_jp(Level& L, cudaStream_t s) {
-    const int n = L.n;
-    Tmp<int> deg(n, s), dec(n, s), rnd(n, s), blk(n, s), scal(8, s), err(1, s);
+// graph is bipartite, else Jones-Plassmann with peel-round priority; all levels in one cooperative
+// launch of k_colour.
+void colour_levels(Handle& h, cudaStream_t s) {
+    const int nl = (int)h.lev.size();
+    if (nl < 2) return;
+    const int nj = nl - 1;
+    if (nj > COL_MAXL) fail(CPC_ESETUP, "too many levels to colour");
+    int64_t tot = 0;
+    for (int l = 0; l < nj; ++l) tot += h.lev[l].n;
+    Tmp<int> work((size_t)5 * tot, s), scal((size_t)COL_NS * nj, s), err(1, s);
     Tmp<unsigned long long> bar(1, s);
-    k_fill_int<<<1, 32, 0, s>>>(scal.get(), 2, INT_MAX);
-    CPC_CK(cudaMemsetAsync(scal.get() + 2, 0, sizeof(int) * 6, s));
+    Tmp<ColLev> dlev(nj, s);
+    std::vector<ColLev> hl(nj);
+    std::vector<int> hs((size_t)COL_NS * nj, 0);
+    int64_t off = 0;
+    for (int l = 0; l < nj; ++l) {
+        Level& L = h.lev[l];
+        L.colour.alloc(L.n);
+        ColLev& V = hl[l];
+        V.n = L.n;
+        V.ptr = L.A.ptr.p;
+        V.col = L.A.col.p;
+        V.colour = L.colour.p;
+        V.deg = work.get() + off;
+        V.dec = V.deg + L.n;
+        V.rnd = V.dec + L.n;
+        V.blk = V.rnd + L.n;
+        V.w = (unsigned*)(V.blk + L.n);
+        V.scal = scal.get() + (size_t)COL_NS * l;
+        off += (int64_t)5 * L.n;
+        hs[(size_t)COL_NS * l + CS_DMIN] = INT_MAX;
+        hs[(size_t)COL_NS * l + CS_DMIN + 1] = INT_MAX;
+    }
+    CPC_CK(cudaMemcpyAsync(dlev.get(), hl.data(), sizeof(ColLev) * nj, cudaMemcpyHostToDevice, s));
+    CPC_CK(cudaMemcpyAsync(scal.get(), hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, s));
     CPC_CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
     CPC_CK(cudaMemsetAsync(bar.get(), 0, sizeof(unsigned long long), s));
     int dev = 0, sms = 0, per_sm = 0;
@@ -1563,148 +1797,28 @@ void colour_jp(Level& L, cudaStream_t s) {
     CPC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CPC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour, COL_TPB, 0));
     if (per_sm < 1) fail(CPC_ESETUP, "colouring kernel does not fit on an SM");
-    // up to four CTAs per SM, one thread per point at most
-    const int grid = std::max(1, std::min(std::min(per_sm, 4) * sms, nblk(n, COL_TPB)));
-    int* pdeg = deg.get();
-    int* pdec = dec.get();
-    int* prnd = rnd.get();
-    int* pblk = blk.get();
-    int* pscal = scal.get();
-    int* perr = err.get();
+    // every CTA the GPU holds at once, one thread per point at most, at least one CTA per level
+    const int grid = (int)std::max<int64_t>(nj, std::min<int64_t>((int64_t)per_sm * sms, nblk(tot, COL_TPB)));
+    const ColLev* pl = dlev.get();
+    int nn = nj;
     unsigned long long* pbar = bar.get();
-    const int* ptr = L.A.ptr.p;
-    const int* col = L.A.col.p;
-    int* colour = L.colour.p;
-    int nn = n;
-    void* args[] = {&nn, (void*)&ptr, (void*)&col, &pdeg, &pdec, &prnd, &colour, &pblk, &pscal, &pbar, &perr};
+    int* perr = err.get();
+    void* args[] = {(void*)&pl, &nn, &pbar, &perr};
     CPC_CK(cudaLaunchCooperativeKernel((void*)k_colour, grid, COL_TPB, args, 0, s));
+    CPC_LAUNCH_CK();
     const int e = d2h(err.get(), s);
     if (e == 1) fail(CPC_ESETUP, "colouring: a grid barrier gave up");
     if (e == 2) fail(CPC_ESETUP, "peel rounds did not terminate");
     if (e == 3) fail(CPC_ESETUP, "colouring did not terminate");
-    Tmp<int> mx(1, s);
-    CPC_CK(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
-    k_max_int<<<nblk(n), TPB, 0, s>>>(colour, n, mx.get());
+    if (e == 4) fail(CPC_ESETUP, "colouring: a union-find join did not complete");
+    Tmp<int> mx(nj, s);
+    CPC_CK(cudaMemsetAsync(mx.get(), 0, sizeof(int) * nj, s));
+    for (int l = 0; l < nj; ++l) k_max_int<<<nblk(h.lev[l].n), TPB, 0, s>>>(h.lev[l].colour.p, h.lev[l].n, mx.get() + l);
     CPC_LAUNCH_CK();
-    L.ncolours = d2h(mx.get(), s) + 1;
-}
-
-void colour_levels(Handle& h, cudaStream_t s) {
-    const int nl = (int)h.lev.size();
-    if (nl < 2) return;
+    std::vector<int> hm(nj);
+    CPC_CK(cudaMemcpyAsync(hm.data(), mx.get(), sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
     CPC_CK(cudaStreamSynchronize(s));
-    const int nj = nl - 1;
-    struct Res {
-        std::vector<cudaStream_t> st;
-        std::vector<cudaEvent_t> ev;
-        int* pin = nullptr;
-        ~Res() {
-            for (auto e : ev) cudaEventDestroy(e);
-            for (auto q : st) { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
-            if (pin) cudaFreeHost(pin);
-        }
-    } res;                                                      // outlives the jobs' buffers
-    CPC_CK(cudaMallocHost(&res.pin, sizeof(int) * nj));
-    std::vector<ColourJob> jobs(nj);
-    for (int l = 0; l < nj; ++l) {
-        cudaStream_t q;
-        cudaEvent_t e;
-        CPC_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
-        res.st.push_back(q);
-        CPC_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        res.ev.push_back(e);
-        ColourJob& J = jobs[l];
-        J.l = l;
-        J.n = h.lev[l].n;
-        J.st = q;
-        J.ev = e;
-        J.pin = res.pin + l;
-        h.lev[l].colour.alloc(J.n);
-    }
-    auto mk = [](int count, cudaStream_t q) { return std::make_unique<Tmp<int>>((size_t)count, q); };
-    auto readback = [](ColourJob& J) {
-        CPC_CK(cudaMemcpyAsync(J.pin, J.cnt->get(), sizeof(int), cudaMemcpyDeviceToHost, J.st));
-        CPC_CK(cudaEventRecord(J.ev, J.st));
-    };
-    auto enter = [&](ColourJob& J, int phase) {                 // allocate and initialise a phase
-        J.phase = phase;
-        J.rounds = 0;
-        if (phase == ColourJob::BIP) {
-            J.a0 = mk(J.n, J.st);                                // (root, parity) words
-            k_bip_init<<<nblk(J.n), TPB, 0, J.st>>>(J.n, (unsigned*)J.a0->get());
-        }
-    };
-    for (auto& J : jobs) J.cnt = mk(1, J.st);
-    for (int active = nj; active > 0;) {
-        for (auto& J : jobs) {                                  // one batch per unfinished level
-            if (J.phase == ColourJob::DONE || J.phase == ColourJob::JP) continue;
-            const Level& L = h.lev[J.l];
-            const int n = J.n;
-            cudaStream_t q = J.st;
-            switch (J.phase) {
-                case ColourJob::TRI:
-                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
-                    k_tri_probe<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, J.cnt->get());
-                    break;
-                case ColourJob::BIP:
-                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
-                    for (int k = 0; k < 16; ++k)
-                        k_bip_round<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, (unsigned*)J.a0->get(),
-                                                            J.cnt->get());
-                    J.rounds += 16;
-                    break;
-                case ColourJob::BIP_CHECK:
-                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
-                    k_bip_check<<<nblk(n), TPB, 0, q>>>(n, L.A.ptr.p, L.A.col.p, (const unsigned*)J.a0->get(),
-                                                        J.cnt->get());
-                    break;
-                case ColourJob::MAX:
-                    CPC_CK(cudaMemsetAsync(J.cnt->get(), 0, sizeof(int), q));
-                    k_max_int<<<nblk(n), TPB, 0, q>>>(L.colour.p, n, J.cnt->get());
-                    break;
-            }
-            CPC_LAUNCH_CK();
-            readback(J);
-        }
-        for (auto& J : jobs) {                                  // read the counters, advance phases
-            if (J.phase == ColourJob::DONE || J.phase == ColourJob::JP) continue;
-            CPC_CK(cudaEventSynchronize(J.ev));
-            const int v = *J.pin;
-            Level& L = h.lev[J.l];
-            switch (J.phase) {
-                case ColourJob::TRI:
-                    if (v) {
-                        J.phase = ColourJob::JP;                 // has a triangle: not bipartite
-                        --active;
-                    } else {
-                        enter(J, ColourJob::BIP);
-                    }
-                    break;
-                case ColourJob::BIP:
-                    if (v == 0) enter(J, ColourJob::BIP_CHECK);
-                    else if (J.rounds > J.n + 16) fail(CPC_ESETUP, "parity propagation did not converge");
-                    break;
-                case ColourJob::BIP_CHECK:
-                    if (v == 0) {
-                        k_bip_unpack<<<nblk(J.n), TPB, 0, J.st>>>(J.n, (const unsigned*)J.a0->get(), L.colour.p);
-                        enter(J, ColourJob::MAX);
-                    } else {
-                        J.phase = ColourJob::JP;
-                        --active;
-                    }
-                    break;
-                case ColourJob::MAX:
-                    L.ncolours = v + 1;
-                    J.phase = ColourJob::DONE;
-                    --active;
-                    break;
-            }
-        }
-    }
-    for (auto& J : jobs) CPC_CK(cudaStreamSynchronize(J.st));
-    // a cooperative grid takes the whole GPU: levels one after another, on the setup stream
-    for (auto& J : jobs)
-        if (J.phase == ColourJob::JP) colour_jp(h.lev[J.l], s);
+    for (int l = 0; l < nj; ++l) h.lev[l].ncolours = hm[l] + 1;
 }
 
 // One coarsening step on level l; returns false when l becomes the coarsest level.
