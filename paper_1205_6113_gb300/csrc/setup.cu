@@ -461,22 +461,33 @@ __device__ int block_reduce(int v, Op op, int identity) {
     return v;                                                   // valid in thread 0
 }
 
-// blk[i]: the position in row i of the uncoloured neighbour of higher priority that stopped point
-// i last time (-1: none yet).  While that neighbour stays uncoloured the point is skipped.  Once it
+// blk[i]: the uncoloured neighbour of higher priority that stopped point i last time (-1: none
+// yet).  While that neighbour stays uncoloured the point is skipped.  Once it
 // is coloured, the point's row is examined again by a group of COL_G lanes (gl = lane in the
 // group, gm = the group's lane mask, gs = its first lane in the warp), COL_U entries per lane per
 // pass, with all loads of a pass in flight together: the first uncoloured neighbour of higher
 // priority in row order is recorded and false returned; if there is none, the point takes the
 // smallest colour left free by its neighbours of higher priority (from the colours just loaded
 // when the row fits one pass) and true is returned (group-uniform).  Entries before the old
-// blocking entry are examined again although they cannot block (lower priority, or coloured for
+// blocking one are examined again although they cannot block (lower priority, or coloured for
 // good): with the loads in flight together that costs nothing, and their colours are needed.
 constexpr int COL_U = 4;
 
-__device__ bool jp_group(int i, const int* ptr, const int* col, const int* rnd, volatile int* vc, int* blk, int gl,
-                         unsigned gm, int gs) {
-    const int p0 = ptr[i], p1 = ptr[i + 1];
-    const int ri = rnd[i];
+// The lowest 32 / COL_G set bits of a warp-uniform mask go to the groups of the warp, one each in
+// order: returns group g's bit (-1: none left for it) and clears them all.
+__device__ __forceinline__ int take_group_bit(unsigned& bits, int g) {
+    int mine = -1;
+#pragma unroll
+    for (int q = 0; q < 32 / COL_G; ++q) {
+        const int b = bits ? __ffs(bits) - 1 : -1;
+        if (q == g) mine = b;
+        if (bits) bits &= bits - 1;
+    }
+    return mine;
+}
+
+__device__ bool jp_group(int i, int p0, int p1, int ri, const int* col, const int* rnd, volatile int* vc, int* blk,
+                         int gl, unsigned gm, int gs) {
     const uint32_t hi = fmix32((uint32_t)i ^ COLOUR_SEED);
     constexpr int W = COL_U * COL_G;                             // entries per pass
     int cj[COL_U];
@@ -499,7 +510,9 @@ __device__ bool jp_group(int i, const int* ptr, const int* col, const int* rnd, 
         for (int u = 0; u < COL_U; ++u) {
             const unsigned bits = (__ballot_sync(gm, up[u] && cj[u] < 0) >> gs) & ((1u << COL_G) - 1u);
             if (bits) {
-                if (gl == 0) blk[i] = base + u * COL_G + __ffs(bits) - 1;
+                const int q = __ffs(bits) - 1;                  // first blocking entry of this batch
+                const int jq = __shfl_sync(gm, j[u], gs + q);
+                if (gl == 0) blk[i] = jq;
                 return false;
             }
         }
@@ -696,12 +709,8 @@ __device__ void col_step(const ColLev& V, int phase, int rnd_no, int dm, int t, 
                 const int base = b0 + k * T;
                 if (take[k]) V.rnd[base + lane] = rnd_no;
                 unsigned bits = __ballot_sync(0xffffffffu, take[k]);
-                while (bits) {                                  // two taken points at a time
-                    const int p0 = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int p1 = bits ? __ffs(bits) - 1 : -1;
-                    if (bits) bits &= bits - 1;
-                    const int mine = gs == 0 ? p0 : p1;
+                while (bits) {                                  // a taken point per group at a time
+                    const int mine = take_group_bit(bits, gs / COL_G);
                     if (mine >= 0) {
                         const int ip = base + mine;
                         for (int p = ptr[ip] + gl; p < ptr[ip + 1]; p += COL_G)
@@ -737,7 +746,7 @@ __device__ void col_step(const ColLev& V, int phase, int rnd_no, int dm, int t, 
         volatile int* vc = V.colour;
         int cnt = 0;
         for (int b0 = t - lane; b0 < n; b0 += COL_K * T) {     // warp-uniform trip count
-            int cv[COL_K], bv[COL_K], cb[COL_K], vb[COL_K];
+            int cv[COL_K], bv[COL_K], vb[COL_K];
 #pragma unroll
             for (int k = 0; k < COL_K; ++k) {                   // loads of COL_K points in flight
                 const int i = b0 + k * T + lane;
@@ -745,22 +754,25 @@ __device__ void col_step(const ColLev& V, int phase, int rnd_no, int dm, int t, 
                 bv[k] = i < n ? V.blk[i] : -1;
             }
 #pragma unroll
-            for (int k = 0; k < COL_K; ++k) cb[k] = cv[k] < 0 && bv[k] >= 0 ? col[bv[k]] : -1;
-#pragma unroll
-            for (int k = 0; k < COL_K; ++k) vb[k] = cb[k] >= 0 ? vc[cb[k]] : -1;
+            for (int k = 0; k < COL_K; ++k) vb[k] = cv[k] < 0 && bv[k] >= 0 ? vc[bv[k]] : -1;
 #pragma unroll
             for (int k = 0; k < COL_K; ++k) {
                 const int base = b0 + k * T;
                 // uncoloured, and either never examined or its blocker has been coloured since
                 const bool ready = cv[k] < 0 && (bv[k] < 0 || vb[k] >= 0);
+                int q0 = 0, q1 = 0, qr = 0;                     // row bounds and round of a ready point
+                if (ready) {
+                    q0 = ptr[base + lane];
+                    q1 = ptr[base + lane + 1];
+                    qr = V.rnd[base + lane];
+                }
                 unsigned bits = __ballot_sync(0xffffffffu, ready);
-                while (bits) {                                  // two ready points at a time
-                    const int p0 = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int p1 = bits ? __ffs(bits) - 1 : -1;
-                    if (bits) bits &= bits - 1;
-                    const int mine = gs == 0 ? p0 : p1;
-                    if (mine >= 0 && jp_group(base + mine, ptr, col, V.rnd, vc, V.blk, gl, gm, gs) && gl == 0) ++cnt;
+                while (bits) {                                  // a ready point per group at a time
+                    const int mine = take_group_bit(bits, gs / COL_G);
+                    const int src = mine < 0 ? 0 : mine;
+                    const int m0 = __shfl_sync(0xffffffffu, q0, src), m1 = __shfl_sync(0xffffffffu, q1, src);
+                    const int mr = __shfl_sync(0xffffffffu, qr, src);
+                    if (mine >= 0 && jp_group(base + mine, m0, m1, mr, col, V.rnd, vc, V.blk, gl, gm, gs) && gl == 0) ++cnt;
                 }
             }
         }
