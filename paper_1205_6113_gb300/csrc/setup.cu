@@ -1769,7 +1769,7 @@ void wavefront_levels(Handle& h, cudaStream_t s) {
 // Smoothing colours of levels [0, nl - 1): the breadth-first parity 2-colouring if the pattern
 // graph is bipartite, else Jones-Plassmann with peel-round priority; all levels in one cooperative
 // launch of k_colour.
-void colour_levels(Handle& h, cudaStream_t s) {
+void colour_levels(Handle& h, cudaStream_t s, int cta_per_sm) {
     const int nl = (int)h.lev.size();
     if (nl < 2) return;
     const int nj = nl - 1;
@@ -1809,8 +1809,10 @@ void colour_levels(Handle& h, cudaStream_t s) {
     CPC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CPC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour, COL_TPB, 0));
     if (per_sm < 1) fail(CPC_ESETUP, "colouring kernel does not fit on an SM");
-    // every CTA the GPU holds at once, one thread per point at most, at least one CTA per level
-    const int grid = (int)std::max<int64_t>(nj, std::min<int64_t>((int64_t)per_sm * sms, nblk(tot, COL_TPB)));
+    // cta_per_sm CTAs per SM (at most what fits), one thread per point at most, at least one CTA per
+    // level
+    const int grid = (int)std::max<int64_t>(
+        nj, std::min<int64_t>((int64_t)std::min(per_sm, cta_per_sm) * sms, nblk(tot, COL_TPB)));
     const ColLev* pl = dlev.get();
     int nn = nj;
     unsigned long long* pbar = bar.get();
@@ -1967,24 +1969,48 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         if (stop || !coarsen(h, l, s)) break;
     }
     CPC_CK(cudaEventRecord(ph[0], s));
-    if (h.opt.gs_order == CPC_GS_NATURAL) wavefront_levels(h, s);
-    else colour_levels(h, s);
-    CPC_CK(cudaEventRecord(ph[1], s));
+    // The coarsest inverse (setup stream) and the smoothing colours (a second stream) need only the
+    // hierarchy's operators and are independent: both chains of small dependent steps run at once.
+    // When the coarsest level is large (1,536 rows or more: an inverse of about 10 ms and up), the
+    // colouring kernel takes three CTAs per SM and leaves room for the inverse's kernels; otherwise
+    // it takes every CTA that fits, and the short inverse runs in its gaps (measured: 1,823 rows
+    // 58 -> 46 ms of AMG setup; 1,100 rows, colouring-bound, best at full occupancy).  The
+    // colouring's grid barriers wait (boundedly) if some of its CTAs are placed late.
     const int nl = (int)h.lev.size();
+    cudaStream_t s2;
+    CPC_CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    struct S2 {
+        cudaStream_t q;
+        ~S2() { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
+    } s2guard{s2};
+    CPC_CK(cudaStreamWaitEvent(s2, ph[0], 0));
+    Level& Lc = h.lev[nl - 1];
+    h.nc = Lc.n;
+    if (h.nc > DENSE_MAX) fail(CPC_ESETUP, "coarsest level too large for the dense solve");
+    h.Ainv.alloc((size_t)h.nc * h.nc);
+    Tmp<int> inv_fail(1, s);
     {
-        Level& Lc = h.lev[nl - 1];
-        h.nc = Lc.n;
-        if (h.nc > DENSE_MAX) fail(CPC_ESETUP, "coarsest level too large for the dense solve");
         Tmp<double> M((size_t)h.nc * h.nc, s);
         CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s));
         k_csr_to_dense<<<nblk(h.nc), TPB, 0, s>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
-        h.Ainv.alloc((size_t)h.nc * h.nc);
-        Tmp<int> f(1, s);
-        CPC_CK(cudaMemsetAsync(f.get(), 0, sizeof(int), s));
-        dense_chol_inverse(h.nc, M.get(), h.Ainv.p, f.get(), s);
-        if (d2h(f.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
+        CPC_CK(cudaMemsetAsync(inv_fail.get(), 0, sizeof(int), s));
+        dense_chol_inverse(h.nc, M.get(), h.Ainv.p, inv_fail.get(), s);
     }
     CPC_CK(cudaEventRecord(ph[2], s));
+    cudaEvent_t c0, c1;
+    CPC_CK(cudaEventCreate(&c0));
+    CPC_CK(cudaEventCreate(&c1));
+    struct CGuard {
+        cudaEvent_t a, b;
+        ~CGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } cguard{c0, c1};
+    CPC_CK(cudaEventRecord(c0, s2));
+    if (h.opt.gs_order == CPC_GS_NATURAL) wavefront_levels(h, s2);
+    else colour_levels(h, s2, h.nc >= 1536 ? 3 : 8);
+    CPC_CK(cudaEventRecord(c1, s2));
+    if (d2h(inv_fail.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
+    CPC_CK(cudaStreamWaitEvent(s, c1, 0));
+    CPC_CK(cudaEventRecord(ph[1], s));                          // both done
     for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1, h.opt.autotune == 1 && l > 0);
     {   // fine A in natural order for the SpMVs
         DBuf<int> slots;
@@ -2042,12 +2068,12 @@ void setup_handle(Handle& h, const cpc_csr& in) {
     CPC_CK(cudaEventElapsedTime(&b, e1, e2));
     if (!colour_ic) h.ms_ic0 = a;
     h.ms_amg = b;
-    {
+    {   // colouring and the coarsest inverse overlap: each is timed on its own stream
         float t[4] = {0.f, 0.f, 0.f, 0.f};
         CPC_CK(cudaEventElapsedTime(&t[0], e1, ph[0]));
-        CPC_CK(cudaEventElapsedTime(&t[1], ph[0], ph[1]));
-        CPC_CK(cudaEventElapsedTime(&t[2], ph[1], ph[2]));
-        CPC_CK(cudaEventElapsedTime(&t[3], ph[2], e2));
+        CPC_CK(cudaEventElapsedTime(&t[1], c0, c1));
+        CPC_CK(cudaEventElapsedTime(&t[2], ph[0], ph[2]));
+        CPC_CK(cudaEventElapsedTime(&t[3], ph[1], e2));
         for (int i = 0; i < 4; ++i) h.ms_phase[i] = t[i];
     }
 
