@@ -243,8 +243,427 @@ __global__ void k_seg_sum(int nseg, int64_t N, const int64_t* start, const uint6
     atomicAdd(&rowcnt[(int)(kk / (uint64_t)m)], 1);
 }
 
+__global__ void k_max_int(const int* a, int n, int* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, a[i]);
+}
+
+__global__ void k_max_i64(const int64_t* a, int n, int64_t* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax((unsigned long long*)out, (unsigned long long)a[i]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Hash sparse product C = A B, one warp per row i of C.  The row's entries live in a hash table in
+// shared memory (open addressing, linear probing).  Row i of A is taken in order of its entries
+// (ascending k); for each k the products a_ik b_kj of row k of B enter the table together, one per
+// lane: the j of one row of B are distinct, so no two lanes touch one entry in the same step, and
+// entry (i, j) receives its products in ascending k, each product rounded and then added: the
+// sums of the sort-based product below, bit for bit.  Before the steps, the products of the rows
+// of B for up to HS_STAGE of them are formed and staged in shared memory, all loads in flight.  A symbolic pass
+// counts each row's entries; the numeric pass compacts the table, sorts it by column (bitonic, in
+// registers) and writes the row.  A row with more than half a table of entries, or a row of B
+// longer than the stage, is not taken: the caller falls back to the sort-based product.
+// ---------------------------------------------------------------------------------------------
+constexpr int HS_WARPS = 4;                 // warps per CTA
+constexpr int HS_STAGE = 512;               // staged products per warp
+constexpr int HS_SYM = 1024;                // table slots per warp in the symbolic pass
+constexpr int HS_SORT = 128;                // most entries of a row sorted in registers
+constexpr unsigned FULLW = 0xffffffffu;
+
+__device__ __forceinline__ int hs_slot(int j, int lg) { return (int)(((uint32_t)j * 0x9E3779B1u) >> (32 - lg)); }
+
+// Per-warp shared memory: staged columns / values, the table, the group's entries of A.
+struct HsEntry {
+    int k, b0, len, off;
+    double a;
+};
+
+// Row i: the steps k of row i of A in order; insert(j, prod) is called by the lanes of a step.
+// Returns false (warp-uniform) if a row of B is longer than the stage.
+template <bool NUMERIC, class Ins>
+__device__ bool hs_row(int i, const int* aptr, const int* acol, const double* aval, const int* bptr, const int* bcol,
+                       const double* bval, int* sc, double* sv, HsEntry* ent, int lane, Ins&& insert) {
+    const int p0 = aptr[i], p1 = aptr[i + 1];
+    for (int c0 = p0; c0 < p1; c0 += 32) {
+        const int cn = min(32, p1 - c0);
+        int k = -1, b0 = 0, len = 0;
+        double a = 0.0;
+        if (lane < cn) {
+            k = acol[c0 + lane];
+            if (NUMERIC) a = aval[c0 + lane];
+        }
+        if (lane < cn) {
+            b0 = bptr[k];
+            len = bptr[k + 1] - b0;
+        }
+        if (__any_sync(FULLW, len > HS_STAGE)) return false;
+        for (int e0 = 0; e0 < cn;) {
+            // entries [e0, e1) whose products fit the stage
+            const int my = lane >= e0 && lane < cn ? len : 0;
+            int inc = my;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULLW, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const unsigned fm = __ballot_sync(FULLW, lane >= e0 && lane < cn && inc <= HS_STAGE);
+            const int e1 = 32 - __clz(fm);                      // one past the last entry that fits
+            const int tot = __shfl_sync(FULLW, inc, e1 - 1);
+            __syncwarp();
+            if (lane >= e0 && lane < e1) ent[lane] = HsEntry{k, b0, len, inc - my, a};
+            __syncwarp();
+            // stage: flattened product f of the group -> its entry by binary search on the offsets
+            for (int f0 = 0; f0 < tot; f0 += 8 * 32) {
+                int cj[8];
+                double cv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int f = f0 + u * 32 + lane;
+                    cj[u] = -1;
+                    cv[u] = 0.0;
+                    if (f < tot) {
+                        int lo = e0, hi = e1 - 1;                   // last entry with off <= f
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (ent[mid].off <= f) lo = mid; else hi = mid - 1;
+                        }
+                        const int q = ent[lo].b0 + (f - ent[lo].off);
+                        cj[u] = bcol[q];
+                        if (NUMERIC) cv[u] = __dmul_rn(ent[lo].a, bval[q]);      // the product, rounded
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int f = f0 + u * 32 + lane;
+                    if (f < tot) {
+                        sc[f] = cj[u];
+                        if (NUMERIC) sv[f] = cv[u];
+                    }
+                }
+            }
+            __syncwarp();
+            for (int e = e0; e < e1; ++e) {                     // steps in ascending k
+                const HsEntry en = ent[e];
+                for (int q = lane; q < en.len; q += 32) insert(sc[en.off + q], NUMERIC ? sv[en.off + q] : 0.0);
+                __syncwarp();
+            }
+            e0 = e1;
+        }
+    }
+    return true;
+}
+
+// Claims or finds j's slot; returns the slot, or -1 if the table is full.  *fresh: claimed now.
+__device__ __forceinline__ int hs_find(int* key, int lg, int j, bool* fresh) {
+    const int ts = 1 << lg;
+    int sl = hs_slot(j, lg);
+    for (int t = 0; t < ts; ++t) {
+        const int cur = key[sl];
+        if (cur == j) { *fresh = false; return sl; }
+        if (cur == -1) {
+            const int prev = atomicCAS(&key[sl], -1, j);
+            if (prev == -1) { *fresh = true; return sl; }
+            if (prev == j) { *fresh = false; return sl; }
+        }
+        sl = (sl + 1) & (ts - 1);
+    }
+    return -1;
+}
+
+// Sorts the cnt (<= 32 E) entries sk[], svv[] of a row by column, bitonic over 32 E elements held
+// E per lane (element g = e * 32 + lane), and writes them to col[], val[].
+template <int E>
+__device__ void hs_sort_write(const int* sk, const double* svv, int cnt, int lane, int* col, double* val) {
+    constexpr int M = 32 * E;
+    int kr[E];
+    double vr[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = e * 32 + lane;
+        kr[e] = g < cnt ? sk[g] : INT_MAX;
+        vr[e] = g < cnt ? svv[g] : 0.0;
+    }
+#pragma unroll
+    for (int kk = 2; kk <= M; kk <<= 1) {
+#pragma unroll
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            if (jj >= 32) {
+                const int de = jj >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int e2 = e ^ de;
+                    if (e2 > e) {
+                        const bool asc = ((e * 32 + lane) & kk) == 0;
+                        if ((kr[e] > kr[e2]) == asc) {
+                            const int tk = kr[e]; kr[e] = kr[e2]; kr[e2] = tk;
+                            const double tv = vr[e]; vr[e] = vr[e2]; vr[e2] = tv;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int g = e * 32 + lane;
+                    const int ok2 = __shfl_xor_sync(FULLW, kr[e], jj);
+                    const double ov = __shfl_xor_sync(FULLW, vr[e], jj);
+                    const bool asc = (g & kk) == 0;
+                    const bool lower = (g & jj) == 0;               // g < partner
+                    if (lower == asc ? ok2 < kr[e] : ok2 > kr[e]) {
+                        kr[e] = ok2;
+                        vr[e] = ov;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int g = e * 32 + lane;
+        if (g < cnt) {
+            col[g] = kr[e];
+            val[g] = vr[e];
+        }
+    }
+}
+
+// Symbolic pass: cnt[i] = entries of row i of C; *over = 1 if a row cannot be taken.
+__global__ void __launch_bounds__(HS_WARPS * 32) k_hs_count(int n, const int* aptr, const int* acol, const int* bptr,
+                                                             const int* bcol, int* cnt, int* over) {
+    __shared__ int s_key[HS_WARPS][HS_SYM];
+    __shared__ int s_col[HS_WARPS][HS_STAGE];
+    __shared__ HsEntry s_ent[HS_WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* key = s_key[w];
+    constexpr int LG = 10;
+    static_assert((1 << LG) == HS_SYM, "table size");
+    for (int t = lane; t < HS_SYM; t += 32) key[t] = -1;
+    __syncwarp();
+    for (int i = blockIdx.x * HS_WARPS + w; i < n; i += gridDim.x * HS_WARPS) {
+        int claimed = 0;
+        bool full = false;
+        const bool ok = hs_row<false>(i, aptr, acol, nullptr, bptr, bcol, nullptr, s_col[w], nullptr, s_ent[w], lane,
+                                      [&](int j, double) {
+                                          bool fresh;
+                                          if (hs_find(key, LG, j, &fresh) < 0) full = true;
+                                          else if (fresh) ++claimed;
+                                      });
+        for (int o = 16; o > 0; o >>= 1) claimed += __shfl_xor_sync(FULLW, claimed, o);
+        const bool bad = !ok || __any_sync(FULLW, full) || claimed > HS_SYM / 2;
+        if (lane == 0) {
+            cnt[i] = claimed;
+            if (bad) atomicOr(over, 1);
+        }
+        __syncwarp();
+        for (int t = lane; t < HS_SYM; t += 32) key[t] = -1;
+        __syncwarp();
+    }
+}
+
+// Numeric pass: row i of C into col[cptr[i] ..], val[..], sorted by column.  LG: log2 table slots.
+template <int LG, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_hs_fill(int n, const int* aptr, const int* acol, const double* aval,
+                                                         const int* bptr, const int* bcol, const double* bval,
+                                                         const int* cptr, int* ccol, double* cval, int* over) {
+    constexpr int TS = 1 << LG;
+    __shared__ int s_key[WARPS][TS];
+    __shared__ double s_val[WARPS][TS];
+    __shared__ int s_col[WARPS][HS_STAGE];
+    __shared__ double s_sv[WARPS][HS_STAGE];
+    __shared__ HsEntry s_ent[WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* key = s_key[w];
+    double* val = s_val[w];
+    for (int t = lane; t < TS; t += 32) key[t] = -1;
+    __syncwarp();
+    for (int i = blockIdx.x * WARPS + w; i < n; i += gridDim.x * WARPS) {
+        bool full = false;
+        const bool ok = hs_row<true>(i, aptr, acol, aval, bptr, bcol, bval, s_col[w], s_sv[w], s_ent[w], lane,
+                                     [&](int j, double prod) {
+                                         bool fresh;
+                                         const int sl = hs_find(key, LG, j, &fresh);
+                                         if (sl < 0) full = true;
+                                         else val[sl] = fresh ? prod : __dadd_rn(val[sl], prod);
+                                     });
+        const int c0 = cptr[i], cnt = cptr[i + 1] - c0;
+        if (!ok || __any_sync(FULLW, full) || cnt > HS_STAGE) {
+            if (lane == 0) atomicOr(over, 1);
+        } else {
+            // compact the table into the stage (cnt entries), then sort by column
+            int* sk = s_col[w];
+            double* svv = s_sv[w];
+            int base = 0;
+            for (int t0 = 0; t0 < TS; t0 += 32) {
+                const int kk = key[t0 + lane];
+                const unsigned um = __ballot_sync(FULLW, kk != -1);
+                if (kk != -1) {
+                    const int r = base + __popc(um & ((1u << lane) - 1u));
+                    if (r < HS_STAGE) {
+                        sk[r] = kk;
+                        svv[r] = val[t0 + lane];
+                    }
+                }
+                base += __popc(um);
+            }
+            __syncwarp();
+            if (base != cnt) {
+                if (lane == 0) atomicOr(over, 1);
+            } else if (cnt <= 32) {
+                hs_sort_write<1>(sk, svv, cnt, lane, ccol + c0, cval + c0);
+            } else if (cnt <= 64) {
+                hs_sort_write<2>(sk, svv, cnt, lane, ccol + c0, cval + c0);
+            } else if (cnt <= HS_SORT) {
+                hs_sort_write<4>(sk, svv, cnt, lane, ccol + c0, cval + c0);
+            } else {
+                // long row: rank of each entry among the row's columns (distinct)
+                for (int g = lane; g < cnt; g += 32) {
+                    const int kg = sk[g];
+                    int r = 0;
+                    for (int h = 0; h < cnt; ++h) r += sk[h] < kg;
+                    ccol[c0 + r] = kg;
+                    cval[c0 + r] = svv[g];
+                }
+            }
+        }
+        __syncwarp();
+        for (int t = lane; t < TS; t += 32) key[t] = -1;
+        __syncwarp();
+    }
+}
+
+// Short rows: one thread per row of C, the row's entries kept sorted by column in the thread's
+// slice of shared memory (entry e of thread t at [e][t]: no bank conflicts), at most RP_CAP of
+// them.  Products are taken in ascending k and each is rounded, then added to its entry (or starts
+// it): the same sums as the other products.  The row goes to tmp at off[i] (its product count is a
+// bound on its entries); cnt[i] = its entries; *over = 1 if a row has more than RP_CAP.
+constexpr int RP_TPB = 64;
+constexpr int RP_CAP = 64;
+
+__global__ void __launch_bounds__(RP_TPB) k_rowprod(int n, const int* aptr, const int* acol, const double* aval,
+                                                     const int* bptr, const int* bcol, const double* bval,
+                                                     const int64_t* off, int* tcol, double* tval, int* cnt, int* over) {
+    __shared__ int sc[RP_CAP][RP_TPB];
+    __shared__ double sv[RP_CAP][RP_TPB];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * RP_TPB + t;
+    if (i >= n) return;
+    int m = 0;
+    bool full = false;
+    for (int p = aptr[i]; p < aptr[i + 1] && !full; ++p) {
+        const int k = acol[p];
+        const double a = aval[p];
+        for (int q = bptr[k]; q < bptr[k + 1]; ++q) {
+            const int j = bcol[q];
+            const double prod = __dmul_rn(a, bval[q]);
+            int lo = 0, hi = m;                                 // first entry with column >= j
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sc[mid][t] < j) lo = mid + 1; else hi = mid;
+            }
+            if (lo < m && sc[lo][t] == j) {
+                sv[lo][t] = __dadd_rn(sv[lo][t], prod);
+            } else {
+                if (m == RP_CAP) { full = true; break; }
+                for (int e = m; e > lo; --e) {
+                    sc[e][t] = sc[e - 1][t];
+                    sv[e][t] = sv[e - 1][t];
+                }
+                sc[lo][t] = j;
+                sv[lo][t] = prod;
+                ++m;
+            }
+        }
+    }
+    if (full) {
+        atomicOr(over, 1);
+        return;
+    }
+    const int64_t o = off[i];
+    for (int e = 0; e < m; ++e) {
+        tcol[o + e] = sc[e][t];
+        tval[o + e] = sv[e][t];
+    }
+    cnt[i] = m;
+}
+
+__global__ void k_rowprod_compact(int n, const int64_t* off, const int* tcol, const double* tval, const int* cptr,
+                                  int* ccol, double* cval) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = off[i];
+    const int c0 = cptr[i], m = cptr[i + 1] - c0;
+    for (int e = 0; e < m; ++e) {
+        ccol[c0 + e] = tcol[o + e];
+        cval[c0 + e] = tval[o + e];
+    }
+}
+
+// Product of short rows (thread per row); false (C untouched) if a row has more than RP_CAP entries.
+bool spgemm_rows(const Csr& A, const Csr& B, Csr& C, const int64_t* off, int64_t N, cudaStream_t s) {
+    const int n = A.n;
+    Tmp<int> tcol(std::max<int64_t>(1, N), s), cnt(n + 1, s), over(1, s);
+    Tmp<double> tval(std::max<int64_t>(1, N), s);
+    CPC_CK(cudaMemsetAsync(over.get(), 0, sizeof(int), s));
+    CPC_CK(cudaMemsetAsync(cnt.get() + n, 0, sizeof(int), s));
+    k_rowprod<<<nblk(n, RP_TPB), RP_TPB, 0, s>>>(n, A.ptr.p, A.col.p, A.val.p, B.ptr.p, B.col.p, B.val.p, off,
+                                                 tcol.get(), tval.get(), cnt.get(), over.get());
+    CPC_LAUNCH_CK();
+    if (d2h(over.get(), s)) return false;
+    C.n = n;
+    C.m = B.m;
+    C.ptr.alloc(n + 1);
+    exclusive_scan(cnt.get(), C.ptr.p, n + 1, s);
+    C.nnz = d2h(C.ptr.p + n, s);
+    C.col.alloc(std::max<int64_t>(1, C.nnz));
+    C.val.alloc(std::max<int64_t>(1, C.nnz));
+    k_rowprod_compact<<<nblk(n), TPB, 0, s>>>(n, off, tcol.get(), tval.get(), C.ptr.p, C.col.p, C.val.p);
+    CPC_LAUNCH_CK();
+    return true;
+}
+
+// Hash product; false (C untouched) if a row cannot be taken.
+bool spgemm_hash(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+    const int n = A.n;
+    Tmp<int> cnt(n + 1, s), over(1, s), mx(1, s);
+    CPC_CK(cudaMemsetAsync(over.get(), 0, sizeof(int), s));
+    CPC_CK(cudaMemsetAsync(cnt.get() + n, 0, sizeof(int), s));
+    int dev = 0, sms = 0;
+    CPC_CK(cudaGetDevice(&dev));
+    CPC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int g = std::max(1, std::min(nblk(n, HS_WARPS), sms * 16));
+    k_hs_count<<<g, HS_WARPS * 32, 0, s>>>(n, A.ptr.p, A.col.p, B.ptr.p, B.col.p, cnt.get(), over.get());
+    CPC_CK(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+    k_max_int<<<nblk(n), TPB, 0, s>>>(cnt.get(), n, mx.get());
+    CPC_LAUNCH_CK();
+    if (d2h(over.get(), s)) return false;
+    const int most = d2h(mx.get(), s);
+    C.n = n;
+    C.m = B.m;
+    C.ptr.alloc(n + 1);
+    exclusive_scan(cnt.get(), C.ptr.p, n + 1, s);
+    const int64_t nnz = d2h(C.ptr.p + n, s);
+    C.nnz = nnz;
+    C.col.alloc(std::max<int64_t>(1, nnz));
+    C.val.alloc(std::max<int64_t>(1, nnz));
+    int lg = 6;
+    while ((1 << lg) < 2 * most) ++lg;
+    auto run = [&](auto lgc) {                                 // two warps per CTA for the larger tables
+        constexpr int L = decltype(lgc)::value;
+        constexpr int W = L <= 8 ? HS_WARPS : 2;
+        const int gf = std::max(1, std::min(nblk(n, W), sms * 32));
+        k_hs_fill<L, W><<<gf, W * 32, 0, s>>>(n, A.ptr.p, A.col.p, A.val.p, B.ptr.p, B.col.p, B.val.p, C.ptr.p,
+                                              C.col.p, C.val.p, over.get());
+    };
+    if (lg <= 6) run(std::integral_constant<int, 6>{});
+    else if (lg == 7) run(std::integral_constant<int, 7>{});
+    else if (lg == 8) run(std::integral_constant<int, 8>{});
+    else if (lg == 9) run(std::integral_constant<int, 9>{});
+    else run(std::integral_constant<int, 10>{});
+    CPC_LAUNCH_CK();
+    return d2h(over.get(), s) == 0;
+}
+
 // C = A * B; every entry sums its products in generation order (row of A ascending, then row of B).
-void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+void spgemm_sort(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
     const int n = A.n;
     C.n = n; C.m = B.m;
     Tmp<int64_t> cnt(n + 1, s), off(n + 1, s);
@@ -280,6 +699,26 @@ void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
                                          C.col.p, C.val.p, rowcnt.get());
     exclusive_scan(rowcnt.get(), C.ptr.p, n + 1, s);
     CPC_LAUNCH_CK();
+}
+
+// C = A * B: the hash product, or the sort-based one for rows the hash product cannot take (same
+// sums, bit for bit).
+void spgemm(const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+    // products per row: short rows (at most twice RP_CAP products) a thread each, else a warp each
+    const int n = A.n;
+    Tmp<int64_t> cnt(n + 1, s), off(n + 1, s), mx(1, s);
+    k_prod_count<<<nblk(n + 1), TPB, 0, s>>>(n, A.ptr.p, A.col.p, B.ptr.p, cnt.get());
+    CPC_CK(cudaMemsetAsync(mx.get(), 0, sizeof(int64_t), s));
+    k_max_i64<<<nblk(n), TPB, 0, s>>>(cnt.get(), n, mx.get());
+    exclusive_scan(cnt.get(), off.get(), n + 1, s);
+    CPC_LAUNCH_CK();
+    const int64_t most = d2h(mx.get(), s);
+    const int64_t N = d2h(off.get() + n, s);
+    if (most <= 2 * RP_CAP && spgemm_rows(A, B, C, off.get(), N, s)) return;
+    C = Csr{};
+    if (spgemm_hash(A, B, C, s)) return;
+    C = Csr{};
+    spgemm_sort(A, B, C, s);
 }
 
 // ============================================================================================
@@ -1038,10 +1477,6 @@ __global__ void k_slot_to_nat(int nslots, const int* perm, const T* v, T* out) {
     if (s < nslots && perm[s] >= 0) out[perm[s]] = v[s];
 }
 
-__global__ void k_max_int(const int* a, int n, int* out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicMax(out, a[i]);
-}
 
 // Slots refer to rows of the CSR; imap (optional) renames rows and columns on output
 // (IC factor stored in its own ordering but applied to naturally ordered vectors).
@@ -1972,9 +2407,9 @@ void setup_handle(Handle& h, const cpc_csr& in) {
     // The coarsest inverse (setup stream) and the smoothing colours (a second stream) need only the
     // hierarchy's operators and are independent: both chains of small dependent steps run at once.
     // When the coarsest level is large (1,536 rows or more: an inverse of about 10 ms and up), the
-    // colouring kernel takes three CTAs per SM and leaves room for the inverse's kernels; otherwise
+    // colouring kernel takes two CTAs per SM and leaves room for the inverse's kernels; otherwise
     // it takes every CTA that fits, and the short inverse runs in its gaps (measured: 1,823 rows
-    // 58 -> 46 ms of AMG setup; 1,100 rows, colouring-bound, best at full occupancy).  The
+    // 58 -> 45 ms of AMG setup; 1,100 rows, colouring-bound, best at full occupancy).  The
     // colouring's grid barriers wait (boundedly) if some of its CTAs are placed late.
     const int nl = (int)h.lev.size();
     cudaStream_t s2;
@@ -2006,7 +2441,7 @@ void setup_handle(Handle& h, const cpc_csr& in) {
     } cguard{c0, c1};
     CPC_CK(cudaEventRecord(c0, s2));
     if (h.opt.gs_order == CPC_GS_NATURAL) wavefront_levels(h, s2);
-    else colour_levels(h, s2, h.nc >= 1536 ? 3 : 8);
+    else colour_levels(h, s2, h.nc >= 1536 ? 2 : 8);
     CPC_CK(cudaEventRecord(c1, s2));
     if (d2h(inv_fail.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
     CPC_CK(cudaStreamWaitEvent(s, c1, 0));
