@@ -44,7 +44,7 @@ TRAFFIC_K_GS_FINE = 48238848
 # The same for one forward sweep of every coarse level (the k_gs launches of the sweep, summed,
 # cold cache; profiles/dram_bco_fp64_correlated3d_128x128x64.md); None until a capture of the
 # current hierarchy exists.
-TRAFFIC_COARSE_SWEEP = 225700000
+TRAFFIC_COARSE_SWEEP = 230672896
 
 
 def peaks():
