@@ -1388,10 +1388,11 @@ __global__ void k_dag_round(int n, const int* ptr, const int* col, int* lvl, int
 // then a_ij -= l_im u_mj for j > m in both rows.  Products and differences are rounded
 // separately (no fused multiply-add), in the same order as the plain sequential algorithm.
 __global__ void k_ic0_level(const int* rows, int cnt, const int* ptr, const int* col, const int* diag,
-                            double* lu, int* fail) {
+                            double* lu, int* fail, int min_len) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     const int i = rows[t];
+    if (ptr[i + 1] - ptr[i] < min_len) return;               // a warp of k_ic0_level_warp has it
     const int di = diag[i];
     const int end_i = ptr[i + 1];
     for (int p = ptr[i]; p < di; ++p) {
@@ -1408,6 +1409,64 @@ __global__ void k_ic0_level(const int* rows, int cnt, const int* ptr, const int*
     }
     const double u = lu[di];
     if (!(u > 0.0) || !isfinite(u)) atomicMin(fail, i);
+}
+
+__global__ void k_max_rowlen(int n, const int* ptr, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, ptr[i + 1] - ptr[i]);
+}
+
+// The same elimination with a warp per row, for long rows: row i (columns and values) is staged in
+// shared memory; for each m (ascending) one lane forms l_im, then the lanes take the entries j > m
+// of row m, find j in row i by binary search and apply a_ij -= l_im u_mj, each product and
+// difference rounded separately.  Every entry of row i receives its updates in ascending m, as in
+// k_ic0_level, so the factor is the same to the bit.  Rows longer than IC_WROW are left to
+// k_ic0_level (min_len = IC_WROW + 1 there: each kernel takes its own rows).
+constexpr int IC_WROW = 2048;
+constexpr int IC_WARPS = 2;
+
+__global__ void __launch_bounds__(IC_WARPS * 32) k_ic0_level_warp(const int* rows, int cnt, const int* ptr,
+                                                                   const int* col, const int* diag, double* lu,
+                                                                   int* fail) {
+    __shared__ int s_col[IC_WARPS][IC_WROW];
+    __shared__ double s_val[IC_WARPS][IC_WROW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * IC_WARPS + w;
+    if (t >= cnt) return;
+    const int i = rows[t];
+    const int p0 = ptr[i], len = ptr[i + 1] - p0;
+    if (len > IC_WROW) return;
+    int* sc = s_col[w];
+    double* sv = s_val[w];
+    for (int e = lane; e < len; e += 32) {
+        sc[e] = col[p0 + e];
+        sv[e] = lu[p0 + e];
+    }
+    __syncwarp();
+    const int dl = diag[i] - p0;                              // the diagonal's position in row i
+    for (int e = 0; e < dl; ++e) {                            // m = col of entry e, ascending
+        const int m = sc[e];
+        const int dm = diag[m];
+        const double l = sv[e] / lu[dm];                      // every lane forms the same quotient
+        __syncwarp();
+        if (lane == 0) sv[e] = l;
+        const int q1 = ptr[m + 1];
+        for (int q = dm + 1 + lane; q < q1; q += 32) {
+            const int j = col[q];
+            int lo = e + 1, hi = len - 1;                     // j > m: after entry e
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sc[mid] < j) lo = mid + 1; else hi = mid;
+            }
+            if (lo < len && sc[lo] == j) sv[lo] = __dsub_rn(sv[lo], __dmul_rn(l, lu[q]));
+        }
+        __syncwarp();
+    }
+    for (int e = lane; e < len; e += 32) lu[p0 + e] = sv[e];
+    if (lane == 0) {
+        const double u = sv[dl];
+        if (!(u > 0.0) || !isfinite(u)) atomicMin(fail, i);
+    }
 }
 
 // Symmetric permutation B = Q^T A Q: new row q is old row order[q], columns renumbered by inv.
@@ -2073,10 +2132,28 @@ void setup_ic0(Handle& h, cudaStream_t s) {
     h.ic_rows_L1 = h.ic_levels_L > 1 ? hc[1] : 0;
     Tmp<int> failrow(1, s);
     k_fill_int<<<1, 1, 0, s>>>(failrow.get(), 1, INT_MAX);
+    // rows of more than 64 entries are eliminated by a warp each
+    int most = 0;
+    {
+        Tmp<int> mx(1, s);
+        CPC_CK(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+        k_max_rowlen<<<nblk(n), TPB, 0, s>>>(n, A.ptr.p, mx.get());
+        CPC_LAUNCH_CK();
+        most = d2h(mx.get(), s);
+    }
+    const bool long_rows = most > 64;
     int off = 0;
     for (int g = 0; g < h.ic_levels_L; ++g) {
-        k_ic0_level<<<nblk(hc[g], 128), 128, 0, s>>>(rowsL.p + off, hc[g], A.ptr.p, A.col.p, h.lu_diag.p, h.lu.p,
-                                                      failrow.get());
+        if (long_rows) {
+            k_ic0_level_warp<<<nblk(hc[g], IC_WARPS), IC_WARPS * 32, 0, s>>>(rowsL.p + off, hc[g], A.ptr.p, A.col.p,
+                                                                             h.lu_diag.p, h.lu.p, failrow.get());
+            if (most > IC_WROW)
+                k_ic0_level<<<nblk(hc[g], 128), 128, 0, s>>>(rowsL.p + off, hc[g], A.ptr.p, A.col.p, h.lu_diag.p,
+                                                              h.lu.p, failrow.get(), IC_WROW + 1);
+        } else {
+            k_ic0_level<<<nblk(hc[g], 128), 128, 0, s>>>(rowsL.p + off, hc[g], A.ptr.p, A.col.p, h.lu_diag.p, h.lu.p,
+                                                          failrow.get(), 0);
+        }
         off += hc[g];
     }
     CPC_LAUNCH_CK();

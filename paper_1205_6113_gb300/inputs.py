@@ -176,6 +176,45 @@ def small_3d(nx, ny, nz, seed=7, sigma=1.5, corr_len=3.0, kz_ratio=0.1, dirichle
     return p
 
 
+def long_range_2d(nx=64, ny=64, radius=14.0, seed=60):
+    """CSR (rowptr, col, val) of an SPD M-matrix on an nx x ny grid: strong couplings to the four
+    grid neighbours (weights 0.5..1.5) and weak ones (weights 0.5e-3..1.5e-3) to every other point
+    within Euclidean distance ``radius``; diagonal = the sum of the row's couplings + 1e-2.  The
+    strong part keeps many coarse points, the weak part makes the Galerkin rows long."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny
+    r = int(np.floor(radius))
+    rows, cols, vals = [], [], []
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    ii, jj = ii.ravel(), jj.ravel()
+    for dy in range(0, r + 1):
+        for dx in range(-r, r + 1):
+            if dy == 0 and dx <= 0:
+                continue                               # each unordered pair once
+            if dx * dx + dy * dy > radius * radius:
+                continue
+            ok = (ii + dx >= 0) & (ii + dx < nx) & (jj + dy < ny)
+            a = (ii + nx * jj)[ok]
+            b = a + dx + nx * dy
+            strong = (dx, dy) in ((1, 0), (0, 1))
+            w = (0.5 + rng.random(a.size)) * (1.0 if strong else 1e-3)
+            rows += [a, b]
+            cols += [b, a]
+            vals += [-w, -w]
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    diag = np.zeros(n)
+    np.add.at(diag, rows, -vals)
+    rows = np.concatenate([rows, np.arange(n)])
+    cols = np.concatenate([cols, np.arange(n)])
+    vals = np.concatenate([vals, diag + 1e-2])
+    order = np.lexsort((cols, rows))
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    return rowptr, cols[order].astype(np.int32), vals[order].astype(np.float64)
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal(n)

@@ -353,3 +353,33 @@ def test_host_buffers_solve(case):
     ref = orc.pcg(b, op=O.BCO, tol=1e-10, maxit=3000)
     assert status == 0 and abs(iters - ref["iters"]) <= 2
     assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+
+
+@pytest.mark.parametrize("radius,longest", [(14.0, 256), (20.0, 512)])
+def test_galerkin_products_on_long_rows(radius, longest):
+    """Strong 5-point couplings keep many coarse points while weak couplings out to `radius` make
+    the Galerkin rows long: with radius 14 the rows of A P and R (A P) reach about 300 entries (the
+    hash product's largest tables), with radius 20 more than 512 (the sort-based fallback).  The
+    hierarchy must still equal the oracle's to the bit, and a B_co application to 1e-11.  IC(0) is
+    taken in the colour order (its rows of several hundred entries go to the warp-per-row
+    elimination), which keeps the dependent chain of the factorisation short."""
+    ptr, col, val = inputs.long_range_2d(radius=radius)
+    A = O.Csr(len(ptr) - 1, ptr, col, val)
+    orc = O.Oracle(A, coarse_max=256, ic_colour_order=True)
+    s = cpc.Solver(ptr, col, val, coarse_max=256, ic_order="colour")
+    assert rel(s.ic0_values(), orc.ic0_values()) < 1e-13
+    assert s.nlevels == orc.nlevels >= 3
+    assert np.diff(orc.level_A(1).rowptr).max() > longest
+    for l in range(orc.nlevels):
+        lp, lc, lv = s.level_matrix(l)
+        Ao = orc.level_A(l)
+        assert np.array_equal(lp, Ao.rowptr) and np.array_equal(lc, Ao.col), l
+        assert np.array_equal(lv, Ao.val), l
+        if l + 1 < orc.nlevels:
+            cf, colour = s.level_splitting(l)
+            cfo, colo = orc.level_cf_colour(l)
+            assert np.array_equal(cf, cfo) and np.array_equal(colour, colo), l
+    r = inputs.random_vector(A.n, seed=61)
+    z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    s.close()
+    assert rel(z, orc.apply(O.BCO, r)) < 1e-11
