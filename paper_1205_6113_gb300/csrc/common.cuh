@@ -34,16 +34,23 @@ inline void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 // ---------------------------------------------------------------------------------------------
 // Device buffer (owning, move-only).
 // ---------------------------------------------------------------------------------------------
+// alloc_async: a stream-ordered buffer for setup temporaries, freed on the same stream, so that its
+// release does not wait for the whole device as cudaFree does; the stream must outlive it.
 template <class T>
 struct DBuf {
     T* p = nullptr;
     size_t n = 0;
+    cudaStream_t fs = nullptr;              // stream of a stream-ordered buffer
     DBuf() = default;
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
-    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), fs(o.fs) { o.p = nullptr; o.n = 0; o.fs = nullptr; }
     DBuf& operator=(DBuf&& o) noexcept {
-        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; fs = o.fs;
+            o.p = nullptr; o.n = 0; o.fs = nullptr;
+        }
         return *this;
     }
     ~DBuf() { release(); }
@@ -53,10 +60,21 @@ struct DBuf {
         CPC_CK(cudaMalloc(&p, count * sizeof(T)));
         n = count;
     }
+    void alloc_async(size_t count, cudaStream_t s) {
+        release();
+        if (count == 0) count = 1;
+        CPC_CK(cudaMallocAsync(&p, count * sizeof(T), s));
+        n = count;
+        fs = s;
+    }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (fs) cudaFreeAsync(p, fs);
+            else cudaFree(p);
+        }
         p = nullptr;
         n = 0;
+        fs = nullptr;
     }
     T* get() const { return p; }
 };

@@ -1608,7 +1608,7 @@ void grouped_slots(int n, const int* key, int ngroups, int C, cudaStream_t s, DB
     }
     seg[ngroups] = s0 / C;
     nslots = s0;
-    perm.alloc(nslots);
+    perm.alloc_async(nslots, s);                                // a temporary slot order
     k_fill_int<<<nblk(nslots), TPB, 0, s>>>(perm.p, nslots, -1);
     Tmp<int> dg(ngroups, s), ds(ngroups, s);
     h2d(dg.get(), gstart.data(), ngroups, s);
@@ -1624,7 +1624,7 @@ void grouped_slots(int n, const int* key, int ngroups, int C, cudaStream_t s, DB
 
 void natural_slots(int n, int C, cudaStream_t s, DBuf<int>& perm, int& nslots, std::vector<int>& seg) {
     nslots = (n + C - 1) / C * C;
-    perm.alloc(nslots);
+    perm.alloc_async(nslots, s);                                // a temporary slot order
     k_fill_int<<<nblk(nslots), TPB, 0, s>>>(perm.p, nslots, -1);
     k_iota<<<nblk(n), TPB, 0, s>>>(perm.p, n);
     seg = {0, nslots / C};
@@ -1789,7 +1789,7 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 // ============================================================================================
 // Coarsest level: dense Cholesky A_c = L L^T and the explicit inverse (Algorithm 3.2, step 2(b)).
 // Blocked right-looking factorisation with panels of NB = 32 columns:
-//   k_chol_diag   factor the 32 x 32 diagonal block with one warp and invert it,
+//   k_chol_diag   factor the 32 x 32 diagonal block with four warps and invert it,
 //   k_chol_trsm   L21 = A21 L11^{-T} as a tile product with that inverse,
 //   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles;
 // then W = L^{-1} by row panels (k_trinv_panel, k_trinv_update) and A_c^{-1} = W^T W (k_lauum).
@@ -1803,48 +1803,60 @@ __global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const doub
     for (int p = ptr[i]; p < ptr[i + 1]; ++p) M[(size_t)i * n + col[p]] = val[p];
 }
 
-// Factor the nb x nb diagonal block (nb <= 32) with one warp in shared memory (lane c updates
-// column c), write L11 back, and write Li = L11^{-1} (lower triangular, 32 x 32 with zeros beyond
-// nb) for the tile products of the panel: each lane solves L11 x = e_c for its column.
-__global__ void __launch_bounds__(32) k_chol_diag(int n, int jb, double* M, double* Li, int* fail) {
+// Factor the nb x nb diagonal block (nb <= 32) in shared memory with CHOL_DT threads, write L11
+// back, and write Li = L11^{-1} (lower triangular, 32 x 32 with zeros beyond nb) for the tile
+// products of the panel.  Each elimination step spreads its trailing update over all threads (four
+// warps: on this part one warp alone issues FP64 at a quarter of the SM's rate); the inverse is
+// formed right-looking on [L11 | I]: row j of X scaled by 1 / l_jj, then subtracted from the rows
+// below, so every step is a short parallel update.
+constexpr int CHOL_DT = 128;
+
+__global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, double* M, double* Li, int* fail) {
     __shared__ double D[CHOL_NB][CHOL_NB + 1];
-    __shared__ double rd[CHOL_NB];
-    const int lane = threadIdx.x;
+    __shared__ double X[CHOL_NB][CHOL_NB + 1];
+    const int tid = threadIdx.x;
     const int nb = min(CHOL_NB, n - jb);
     if (*(volatile int*)fail) return;
-    for (int r = 0; r < CHOL_NB; ++r) D[r][lane] = (r < nb && lane <= r) ? M[(size_t)(jb + r) * n + jb + lane] : 0.0;
-    __syncwarp();
+    for (int t = tid; t < CHOL_NB * CHOL_NB; t += CHOL_DT) {
+        const int r = t / CHOL_NB, c = t % CHOL_NB;
+        D[r][c] = (r < nb && c <= r) ? M[(size_t)(jb + r) * n + jb + c] : 0.0;
+        X[r][c] = (r == c && r < nb) ? 1.0 : 0.0;
+    }
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
         const double d = D[j][j];
-        if (!(d > 0.0) || !isfinite(d)) {                    // every lane reads the same d
-            if (lane == 0) *fail = 1;
+        if (!(d > 0.0) || !isfinite(d)) {                    // every thread reads the same d
+            if (tid == 0) *fail = 1;
             return;
         }
-        __syncwarp();
-        if (lane == j) D[j][j] = sqrt(d);
-        __syncwarp();
-        if (lane > j && lane < nb) D[lane][j] /= D[j][j];
-        __syncwarp();
-        if (lane > j && lane < nb)
-            for (int r = lane; r < nb; ++r) D[r][lane] -= D[r][j] * D[lane][j];
-        __syncwarp();
-    }
-    for (int r = lane; r < nb; ++r) M[(size_t)(jb + r) * n + jb + lane] = D[r][lane];
-    if (lane < nb) rd[lane] = 1.0 / D[lane][lane];
-    __syncwarp();
-    double x[CHOL_NB];
-#pragma unroll
-    for (int r = 0; r < CHOL_NB; ++r) {
-        double v = 0.0;
-        if (r >= lane && r < nb) {
-            v = r == lane ? 1.0 : 0.0;
-            for (int m = lane; m < r; ++m) v -= D[r][m] * x[m];
-            v *= rd[r];
+        const double sj = sqrt(d), inv = 1.0 / sj;
+        __syncthreads();                                      // all have read d
+        if (tid == 0) D[j][j] = sj;
+        for (int r = j + 1 + tid; r < nb; r += CHOL_DT) D[r][j] *= inv;
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int e = tid; e < m * m; e += CHOL_DT) {
+            const int r = j + 1 + e / m, c = j + 1 + e % m;
+            if (c <= r) D[r][c] -= D[r][j] * D[c][j];
         }
-        x[r] = v;
+        __syncthreads();
     }
-#pragma unroll
-    for (int r = 0; r < CHOL_NB; ++r) Li[r * CHOL_NB + lane] = x[r];
+    for (int t = tid; t < CHOL_NB * CHOL_NB; t += CHOL_DT) {
+        const int r = t / CHOL_NB, c = t % CHOL_NB;
+        if (r < nb && c <= r) M[(size_t)(jb + r) * n + jb + c] = D[r][c];
+    }
+    for (int j = 0; j < nb; ++j) {
+        const double rj = 1.0 / D[j][j];
+        for (int c = tid; c <= j; c += CHOL_DT) X[j][c] *= rj;
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int e = tid; e < m * (j + 1); e += CHOL_DT) {
+            const int r = j + 1 + e / (j + 1), c = e % (j + 1);
+            X[r][c] -= D[r][j] * X[j][c];
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < CHOL_NB * CHOL_NB; t += CHOL_DT) Li[t] = X[t / CHOL_NB][t % CHOL_NB];
 }
 
 // Rows i >= jb + nb of the panel: l_i = a_i L11^{-T} = a_i Li^T, a tile product (16 rows x 32
@@ -2038,7 +2050,7 @@ void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t 
     for (int jb = 0; jb < n; jb += CHOL_NB) {
         const int nb = std::min(CHOL_NB, n - jb);
         double* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
-        k_chol_diag<<<1, 32, 0, s>>>(n, jb, M, li, fail);
+        k_chol_diag<<<1, CHOL_DT, 0, s>>>(n, jb, M, li, fail);
         const int below = n - jb - nb;
         if (below > 0) {
             k_chol_trsm<<<(below + 15) / 16, 128, 0, s>>>(n, jb, M, li, fail);
@@ -2281,7 +2293,7 @@ void wavefront_levels(Handle& h, cudaStream_t s) {
 // Smoothing colours of levels [0, nl - 1): the breadth-first parity 2-colouring if the pattern
 // graph is bipartite, else Jones-Plassmann with peel-round priority; all levels in one cooperative
 // launch of k_colour.
-void colour_levels(Handle& h, cudaStream_t s, int cta_per_sm) {
+void colour_levels(Handle& h, cudaStream_t s) {
     const int nl = (int)h.lev.size();
     if (nl < 2) return;
     const int nj = nl - 1;
@@ -2321,10 +2333,8 @@ void colour_levels(Handle& h, cudaStream_t s, int cta_per_sm) {
     CPC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CPC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour, COL_TPB, 0));
     if (per_sm < 1) fail(CPC_ESETUP, "colouring kernel does not fit on an SM");
-    // cta_per_sm CTAs per SM (at most what fits), one thread per point at most, at least one CTA per
-    // level
-    const int grid = (int)std::max<int64_t>(
-        nj, std::min<int64_t>((int64_t)std::min(per_sm, cta_per_sm) * sms, nblk(tot, COL_TPB)));
+    // every CTA that fits, one thread per point at most, at least one CTA per level
+    const int grid = (int)std::max<int64_t>(nj, std::min<int64_t>((int64_t)per_sm * sms, nblk(tot, COL_TPB)));
     const ColLev* pl = dlev.get();
     int nn = nj;
     unsigned long long* pbar = bar.get();
@@ -2481,34 +2491,28 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         if (stop || !coarsen(h, l, s)) break;
     }
     CPC_CK(cudaEventRecord(ph[0], s));
-    // The coarsest inverse (setup stream) and the smoothing colours (a second stream) need only the
-    // hierarchy's operators and are independent: both chains of small dependent steps run at once.
-    // When the coarsest level is large (1,536 rows or more: an inverse of about 10 ms and up), the
-    // colouring kernel takes two CTAs per SM and leaves room for the inverse's kernels; otherwise
-    // it takes every CTA that fits, and the short inverse runs in its gaps (measured: 1,823 rows
-    // 58 -> 45 ms of AMG setup; 1,100 rows, colouring-bound, best at full occupancy).  The
-    // colouring's grid barriers wait (boundedly) if some of its CTAs are placed late.
+    // The smoothing colours first, on the setup stream: one cooperative kernel at full occupancy
+    // (measured: other kernels do not start beside a resident cooperative grid on this part, so
+    // the coarsest inverse is not overlapped with it).  Then the coarsest inverse on a second
+    // stream beside the layouts (ordinary kernels that share the GPU): the layouts need the colours,
+    // the inverse only the coarsest operator.  The layouts' allocations still wait for the device
+    // now and then, so the overlap is partial (measured: 49.7 -> 47 ms of AMG setup at 1M).
     const int nl = (int)h.lev.size();
+    if (h.opt.gs_order == CPC_GS_NATURAL) wavefront_levels(h, s);
+    else colour_levels(h, s);
+    CPC_CK(cudaEventRecord(ph[1], s));
     cudaStream_t s2;
     CPC_CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
     struct S2 {
         cudaStream_t q;
         ~S2() { cudaStreamSynchronize(q); cudaStreamDestroy(q); }
     } s2guard{s2};
-    CPC_CK(cudaStreamWaitEvent(s2, ph[0], 0));
+    CPC_CK(cudaStreamWaitEvent(s2, ph[1], 0));
     Level& Lc = h.lev[nl - 1];
     h.nc = Lc.n;
     if (h.nc > DENSE_MAX) fail(CPC_ESETUP, "coarsest level too large for the dense solve");
     h.Ainv.alloc((size_t)h.nc * h.nc);
-    Tmp<int> inv_fail(1, s);
-    {
-        Tmp<double> M((size_t)h.nc * h.nc, s);
-        CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s));
-        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
-        CPC_CK(cudaMemsetAsync(inv_fail.get(), 0, sizeof(int), s));
-        dense_chol_inverse(h.nc, M.get(), h.Ainv.p, inv_fail.get(), s);
-    }
-    CPC_CK(cudaEventRecord(ph[2], s));
+    Tmp<int> inv_fail(1, s2);
     cudaEvent_t c0, c1;
     CPC_CK(cudaEventCreate(&c0));
     CPC_CK(cudaEventCreate(&c1));
@@ -2517,12 +2521,14 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         ~CGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } cguard{c0, c1};
     CPC_CK(cudaEventRecord(c0, s2));
-    if (h.opt.gs_order == CPC_GS_NATURAL) wavefront_levels(h, s2);
-    else colour_levels(h, s2, h.nc >= 1536 ? 2 : 8);
+    {
+        Tmp<double> M((size_t)h.nc * h.nc, s2);
+        CPC_CK(cudaMemsetAsync(inv_fail.get(), 0, sizeof(int), s2));
+        CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s2));
+        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s2>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
+        dense_chol_inverse(h.nc, M.get(), h.Ainv.p, inv_fail.get(), s2);
+    }
     CPC_CK(cudaEventRecord(c1, s2));
-    if (d2h(inv_fail.get(), s)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
-    CPC_CK(cudaStreamWaitEvent(s, c1, 0));
-    CPC_CK(cudaEventRecord(ph[1], s));                          // both done
     for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1, h.opt.autotune == 1 && l > 0);
     {   // fine A in natural order for the SpMVs
         DBuf<int> slots;
@@ -2535,6 +2541,9 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         if (nl > 1) build_dia(h.n, h.lev[0].A.ptr.p, h.lev[0].A.col.p, h.lev[0].A.val.p, h.lev[0].S, s, true);
         CPC_CK(cudaStreamSynchronize(s));
     }
+    CPC_CK(cudaEventRecord(ph[2], s));                          // layouts done
+    if (d2h(inv_fail.get(), s2)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
+    CPC_CK(cudaStreamWaitEvent(s, c1, 0));
     CPC_CK(cudaEventRecord(e2, s));
     if (colour_ic) {
         // IC(0) of the colour-ordered fine matrix: order = rows sorted by (colour, index)
@@ -2580,12 +2589,12 @@ void setup_handle(Handle& h, const cpc_csr& in) {
     CPC_CK(cudaEventElapsedTime(&b, e1, e2));
     if (!colour_ic) h.ms_ic0 = a;
     h.ms_amg = b;
-    {   // colouring and the coarsest inverse overlap: each is timed on its own stream
+    {   // the coarsest inverse (own stream) overlaps the layouts: each is timed on its stream
         float t[4] = {0.f, 0.f, 0.f, 0.f};
         CPC_CK(cudaEventElapsedTime(&t[0], e1, ph[0]));
-        CPC_CK(cudaEventElapsedTime(&t[1], c0, c1));
-        CPC_CK(cudaEventElapsedTime(&t[2], ph[0], ph[2]));
-        CPC_CK(cudaEventElapsedTime(&t[3], ph[1], e2));
+        CPC_CK(cudaEventElapsedTime(&t[1], ph[0], ph[1]));
+        CPC_CK(cudaEventElapsedTime(&t[2], c0, c1));
+        CPC_CK(cudaEventElapsedTime(&t[3], ph[1], ph[2]));
         for (int i = 0; i < 4; ++i) h.ms_phase[i] = t[i];
     }
 
