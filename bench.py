@@ -659,7 +659,9 @@ def profile_mode(name):
     (for `ncu --profile-from-start off`), after two untimed warm-up applications.  With
     name = "blockcg_fp32": one block PCG solve of the 64 right-hand sides of the batched workload
     (FP32 preconditioner) after one untimed warm-up solve.  With name = "sweeps_fp64": one
-    forward Gauss-Seidel sweep of every coarse level, after two untimed ones."""
+    forward Gauss-Seidel sweep of every coarse level, after two untimed ones.  With name =
+    "setup_fp64": one setup of the benchmark's solver (the kernels of the AMG setup; the process
+    does nothing else on the GPU besides the matrix assembly)."""
     import torch
     from paper_1205_6113_gb300 import cpc
     pre, prec = name.split("_")
@@ -667,6 +669,11 @@ def profile_mode(name):
     p = inputs.workload(WORKLOAD)
     logk = torch.tensor(p.logk, device=dev)
     rowptr, col, val = cpc.tpfa_assemble(p.nx, p.ny, p.nz, logk, p.kz_ratio, p.dirichlet)
+    if pre == "setup":
+        s = cpc.Solver(rowptr, col, val, precond="bco", precision=prec, ic_order="colour")
+        torch.cuda.synchronize()
+        print(json.dumps({"profiled": name, "setup_phases_ms": {k: round(v, 2) for k, v in s.setup_phases_ms().items()}}))
+        return
     if pre == "blockcg":
         s = cpc.Solver(rowptr, col, val, precond="bco", precision=prec, ic_order="colour")
         B = torch.tensor(np.ascontiguousarray(inputs.batch_rhs(p.n, 64, seed=5).T), device=dev)
