@@ -1792,7 +1792,8 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 //   k_chol_diag   factor the 32 x 32 diagonal block with four warps and invert it,
 //   k_chol_trsm   L21 = A21 L11^{-T} as a tile product with that inverse,
 //   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles;
-// then W = L^{-1} by row panels (k_trinv_panel, k_trinv_update) and A_c^{-1} = W^T W (k_lauum).
+// then W = L^{-1} by row panels (k_trinv_panel, k_trinv_update) and A_c^{-1} = W^T W (k_lauum_part,
+// k_lauum_sum).
 // L is left in the lower triangle of M.
 // ============================================================================================
 constexpr int CHOL_NB = 32;
@@ -1823,15 +1824,24 @@ __global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, double* M,
         X[r][c] = (r == c && r < nb) ? 1.0 : 0.0;
     }
     __syncthreads();
+    __shared__ double piv_inv;
+    __shared__ int piv_bad;
     for (int j = 0; j < nb; ++j) {
-        const double d = D[j][j];
-        if (!(d > 0.0) || !isfinite(d)) {                    // every thread reads the same d
+        if (tid == 0) {                                       // one thread takes the pivot's root
+            const double d = D[j][j];
+            piv_bad = !(d > 0.0) || !isfinite(d);
+            if (!piv_bad) {
+                const double sj = sqrt(d);
+                D[j][j] = sj;
+                piv_inv = 1.0 / sj;
+            }
+        }
+        __syncthreads();
+        if (piv_bad) {                                        // the same for every thread
             if (tid == 0) *fail = 1;
             return;
         }
-        const double sj = sqrt(d), inv = 1.0 / sj;
-        __syncthreads();                                      // all have read d
-        if (tid == 0) D[j][j] = sj;
+        const double inv = piv_inv;
         for (int r = j + 1 + tid; r < nb; r += CHOL_DT) D[r][j] *= inv;
         __syncthreads();
         const int m = nb - j - 1;
@@ -1845,8 +1855,11 @@ __global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, double* M,
         const int r = t / CHOL_NB, c = t % CHOL_NB;
         if (r < nb && c <= r) M[(size_t)(jb + r) * n + jb + c] = D[r][c];
     }
+    __shared__ double rdiag[CHOL_NB];
+    if (tid < nb) rdiag[tid] = 1.0 / D[tid][tid];
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        const double rj = 1.0 / D[j][j];
+        const double rj = rdiag[j];
         for (int c = tid; c <= j; c += CHOL_DT) X[j][c] *= rj;
         __syncthreads();
         const int m = nb - j - 1;
@@ -2007,34 +2020,51 @@ __global__ void __launch_bounds__(256) k_trinv_update(int n, int jb, const doubl
         }
 }
 
-// A^{-1} = W^T W: block (bi, bj) with bj <= bi computes the 64 x 64 tile
-// x_ij = sum_k w_ki w_kj over k >= max(i0, j0) = i0 (W is lower triangular) and writes it at
-// (i, j) and (j, i).
-__global__ void __launch_bounds__(256) k_lauum(int n, const double* W, double* X, const int* fail) {
+// A^{-1} = W^T W, tile (bi, bj) with bj <= bi: x_ij = sum_k w_ki w_kj over k >= i0 (W is lower
+// triangular), written at (i, j) and (j, i).  The k range of a tile is cut into pieces of LA_KS:
+// one CTA per piece writes its partial tile to part[item], and k_lauum_sum adds a tile's pieces in
+// order (deterministic).  Without the cut, the first row of tiles carried the whole k range on one
+// SM.
+constexpr int LA_KS = 256;
+
+__global__ void __launch_bounds__(256) k_lauum_part(int n, const double* W, const int4* items, double* part,
+                                                     const int* fail) {
     __shared__ double Wi[DT_T][DT_K + 1], Wj[DT_T][DT_K + 1];
     if (*(volatile int*)fail) return;
-    const int bi = blockIdx.y, bj = blockIdx.x;
-    if (bj > bi) return;
-    const int i0 = bi * DT_T, j0 = bj * DT_T;
+    const int4 it = items[blockIdx.x];                        // bi, bj, k0, k1
+    const int i0 = it.x * DT_T, j0 = it.y * DT_T;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     double acc[4][4] = {};
-    for (int k0 = i0; k0 < n; k0 += DT_K) {
-        dt_load_cols(Wi, W, n, k0, i0, n, n);
-        dt_load_cols(Wj, W, n, k0, j0, n, n);
+    for (int k0 = it.z; k0 < it.w; k0 += DT_K) {
+        dt_load_cols(Wi, W, n, k0, i0, it.w, n);
+        dt_load_cols(Wj, W, n, k0, j0, it.w, n);
         __syncthreads();
         dt_mac(Wi, Wj, acc, tx, ty);
         __syncthreads();
     }
+    double* o = part + (size_t)blockIdx.x * DT_T * DT_T;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
-            if (i < n && j < n) {
-                X[(size_t)i * n + j] = acc[a][b];
-                X[(size_t)j * n + i] = acc[a][b];
-            }
+        for (int b = 0; b < 4; ++b) o[(ty * 4 + a) * DT_T + tx * 4 + b] = acc[a][b];
+}
+
+// Tile t: sum its pieces first[t] .. first[t] + cnt[t] - 1 in order.
+__global__ void __launch_bounds__(256) k_lauum_sum(int n, const int4* items, const int* first, const int* cnt,
+                                                    const double* part, double* X, const int* fail) {
+    if (*(volatile int*)fail) return;
+    const int f = first[blockIdx.x], c = cnt[blockIdx.x];
+    const int4 it = items[f];
+    const int i0 = it.x * DT_T, j0 = it.y * DT_T;
+    for (int e = threadIdx.x; e < DT_T * DT_T; e += 256) {
+        double v = part[(size_t)f * DT_T * DT_T + e];
+        for (int q = 1; q < c; ++q) v += part[(size_t)(f + q) * DT_T * DT_T + e];
+        const int i = i0 + e / DT_T, j = j0 + e % DT_T;
+        if (i < n && j < n) {
+            X[(size_t)i * n + j] = v;
+            X[(size_t)j * n + i] = v;
         }
+    }
 }
 
 __global__ void k_identity(int n, double* W) {
@@ -2045,6 +2075,22 @@ __global__ void k_identity(int n, double* W) {
 }
 
 void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t s) {
+    // the pieces of W^T W (host tables copied first: pageable copies return once staged)
+    const int tiles_all = (n + DT_T - 1) / DT_T;
+    std::vector<int4> items;
+    std::vector<int> first, cnt;
+    for (int bi = 0; bi < tiles_all; ++bi)
+        for (int bj = 0; bj <= bi; ++bj) {
+            first.push_back((int)items.size());
+            for (int k0 = bi * DT_T; k0 < n; k0 += LA_KS) items.push_back(make_int4(bi, bj, k0, std::min(n, k0 + LA_KS)));
+            cnt.push_back((int)items.size() - first.back());
+        }
+    Tmp<int4> ditems(items.size(), s);
+    Tmp<int> dfirst(first.size(), s), dcnt(cnt.size(), s);
+    Tmp<double> part(items.size() * DT_T * DT_T, s);
+    h2d(ditems.get(), items.data(), items.size(), s);
+    h2d(dfirst.get(), first.data(), first.size(), s);
+    h2d(dcnt.get(), cnt.data(), cnt.size(), s);
     const int np = (n + CHOL_NB - 1) / CHOL_NB;
     Tmp<double> Li((size_t)np * CHOL_NB * CHOL_NB, s);         // L_pp^{-1} of every panel
     for (int jb = 0; jb < n; jb += CHOL_NB) {
@@ -2069,8 +2115,8 @@ void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t 
             k_trinv_update<<<dim3((e + DT_T - 1) / DT_T, (n - e + DT_T - 1) / DT_T), 256, 0, s>>>(n, jb, M, W.get(),
                                                                                                  fail);
     }
-    const int tiles_all = (n + DT_T - 1) / DT_T;
-    k_lauum<<<dim3(tiles_all, tiles_all), 256, 0, s>>>(n, W.get(), Ainv, fail);
+    k_lauum_part<<<(int)items.size(), 256, 0, s>>>(n, W.get(), ditems.get(), part.get(), fail);
+    k_lauum_sum<<<(int)first.size(), 256, 0, s>>>(n, ditems.get(), dfirst.get(), dcnt.get(), part.get(), Ainv, fail);
     CPC_LAUNCH_CK();
 }
 
