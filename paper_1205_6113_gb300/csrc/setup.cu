@@ -2418,12 +2418,16 @@ bool coarsen(Handle& h, int l, cudaStream_t s) {
     k_st_count<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, tpos.get(), strong.get(), cnt.get());
     k_pmis_init<<<nblk(n), TPB, 0, s>>>(n, cnt.get(), st.get());
     Tmp<int> undec(1, s);
-    for (int round = 0;; ++round) {
-        k_pmis_select<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, tpos.get(), strong.get(), cnt.get(),
-                                              st.get(), sel.get());
-        k_pmis_setc<<<nblk(n), TPB, 0, s>>>(n, sel.get(), st.get());
-        CPC_CK(cudaMemsetAsync(undec.get(), 0, sizeof(int), s));
-        k_pmis_setf<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, strong.get(), st.get(), undec.get());
+    // rounds in batches of 4 per read-back of the undecided count (the last round's): rounds after
+    // every point is decided change nothing
+    for (int round = 0;; round += 4) {
+        for (int k = 0; k < 4; ++k) {
+            k_pmis_select<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, tpos.get(), strong.get(), cnt.get(),
+                                                  st.get(), sel.get());
+            k_pmis_setc<<<nblk(n), TPB, 0, s>>>(n, sel.get(), st.get());
+            CPC_CK(cudaMemsetAsync(undec.get(), 0, sizeof(int), s));
+            k_pmis_setf<<<nblk(n), TPB, 0, s>>>(n, L.A.ptr.p, L.A.col.p, strong.get(), st.get(), undec.get());
+        }
         CPC_LAUNCH_CK();
         if (d2h(undec.get(), s) == 0) break;
         if (round > n) fail(CPC_ESETUP, "PMIS did not terminate");
