@@ -383,3 +383,40 @@ def test_galerkin_products_on_long_rows(radius, longest):
     z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
     s.close()
     assert rel(z, orc.apply(O.BCO, r)) < 1e-11
+
+
+def test_disconnected_matrix_hierarchy():
+    """A block-diagonal matrix of three independent grids: every level's graph has several
+    components, and the parity 2-colouring must root each at its own smallest index (the union-find
+    hooks larger roots under smaller ones).  Splitting, colours and Galerkin values equal the
+    oracle's to the bit; one B_co application to 1e-11."""
+    blocks = [O.tpfa_problem(q) for q in (inputs.small_3d(13, 11, 7, seed=71), inputs.small_3d(9, 9, 5, seed=72),
+                                          inputs.lognormal_2d(20, 20, seed=73))]
+    ptrs, cols, vals, off = [np.zeros(1, np.int32)], [], [], 0
+    for B in blocks:
+        ptrs.append(B.rowptr[1:] + ptrs[-1][-1])
+        cols.append(B.col + off)
+        vals.append(B.val)
+        off += B.n
+    ptr = np.concatenate(ptrs).astype(np.int32)
+    col = np.concatenate(cols).astype(np.int32)
+    val = np.concatenate(vals)
+    A = O.Csr(off, ptr, col, val)
+    orc = O.Oracle(A, coarse_max=64)
+    s = cpc.Solver(ptr, col, val, coarse_max=64)
+    assert s.nlevels == orc.nlevels >= 3
+    for l in range(orc.nlevels):
+        lp, lc, lv = s.level_matrix(l)
+        Ao = orc.level_A(l)
+        assert np.array_equal(lp, Ao.rowptr) and np.array_equal(lc, Ao.col) and np.array_equal(lv, Ao.val), l
+        if l + 1 < orc.nlevels:
+            cf, colour = s.level_splitting(l)
+            cfo, colo = orc.level_cf_colour(l)
+            assert np.array_equal(cf, cfo) and np.array_equal(colour, colo), l
+    _, colour0 = s.level_splitting(0)
+    starts = np.cumsum([0] + [B.n for B in blocks[:-1]])
+    assert s.level_info(0)["ncolours"] == 2 and all(colour0[i] == 0 for i in starts)
+    r = inputs.random_vector(A.n, seed=74)
+    z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
+    s.close()
+    assert rel(z, orc.apply(O.BCO, r)) < 1e-11
