@@ -67,6 +67,10 @@ enum {
                             /* sequential sweep i = 0..n-1 (and n-1..0 for S_l^T).  Far more steps.   */
 };
 
+/* Largest accepted cpc_options.max_levels: the smoothing colourings of all levels but the
+   coarsest are computed in one launch that holds per-level state for 24 levels. */
+#define CPC_MAX_LEVELS 25
+
 /* CSR matrix, caller-owned; cpc_setup copies what it needs. */
 typedef struct {
     int32_t n;              /* rows = columns                                                    */
@@ -86,7 +90,7 @@ typedef struct {
                                                                                     (default 0)   */
     double theta;           /* strength threshold of the AMG coarsening            (0.12)        */
     int32_t coarse_max;     /* stop coarsening at n_l <= coarse_max                (2048)        */
-    int32_t max_levels;     /* at most this many levels                            (20)          */
+    int32_t max_levels;     /* at most this many levels, 1..CPC_MAX_LEVELS          (20)          */
     int32_t autotune;       /* 1: each coarse level's SELL chunk height C (and so its threads per
                                row, 32 / C) is picked at setup by timing a Gauss-Seidel sweep of
                                the candidates C/2, C, 2C around the row-length rule; 0: the rule

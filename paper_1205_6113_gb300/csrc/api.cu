@@ -119,7 +119,7 @@ int cpc_setup(const cpc_csr* A, const cpc_options* opt, cpc_handle** out) {
     if (opt) o = *opt; else cpc_default_options(&o);
     if (o.precond < 0 || o.precond > CPC_PRECOND_AMG_ILU || o.precision < 0 || o.precision > CPC_PREC_FP32_BF16 ||
         o.ic_order < 0 || o.ic_order > 1 || !(o.theta > 0.0 && o.theta < 1.0) || o.coarse_max < 1 || o.autotune < 0 || o.autotune > 1 ||
-        o.max_levels < 1 || o.gs_order < CPC_GS_MULTICOLOUR || o.gs_order > CPC_GS_NATURAL) {
+        o.max_levels < 1 || o.max_levels > CPC_MAX_LEVELS || o.gs_order < CPC_GS_MULTICOLOUR || o.gs_order > CPC_GS_NATURAL) {
         g_setup_err = "invalid options";
         return CPC_EINVAL;
     }

@@ -1000,7 +1000,7 @@ __device__ bool jp_group(int i, int p0, int p1, int ri, const int* col, const in
 // The CTAs of a step are shared among the levels with work in that step, in proportion to their
 // points (at least one each); a CTA works on one level.
 // ---------------------------------------------------------------------------------------------
-constexpr int COL_MAXL = 24;
+constexpr int COL_MAXL = CPC_MAX_LEVELS - 1;     // every level but the coarsest is coloured
 
 struct ColLev {
     int n;

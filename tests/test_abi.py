@@ -77,7 +77,8 @@ def test_pure_host_entry_points(lib):
     rp, ci, va = (ctypes.c_int32 * 2)(0, 1), (ctypes.c_int32 * 1)(0), (ctypes.c_double * 1)(1.0)
     csr = cpc._Csr(1, 1, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(ci, ctypes.c_void_p),
                    ctypes.cast(va, ctypes.c_void_p), 0)
-    for field, value in [("gs_order", 2), ("gs_order", -1), ("precond", 6), ("autotune", 2)]:
+    for field, value in [("gs_order", 2), ("gs_order", -1), ("precond", 6), ("autotune", 2),
+                         ("max_levels", 0), ("max_levels", 26)]:
         bad = cpc._Options()
         L.cpc_default_options(ctypes.byref(bad))
         setattr(bad, field, value)
