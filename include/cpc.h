@@ -255,6 +255,15 @@ int cpc_setup_time_ms(const cpc_handle* h, double* ms_ic0, double* ms_amg);
  * kernels' layouts.  At most cap (<= 4) values are written.  Host memory. */
 int cpc_setup_phases_ms(const cpc_handle* h, double* ms, int32_t cap);
 
+/* How the coarsest level's explicit inverse X = A_c^{-1} (Algorithm 3.2, step 2(b)) was formed:
+ * *method = 1 for the FP32 Cholesky inverse refined by three Newton-Schulz steps
+ * X <- X + X (I - A_c X), the residual I - A_c X in FP64 and the product X (I - A_c X) in FP32;
+ * *method = 0 for the FP64 Cholesky inverse, taken when the FP32 factorisation meets a
+ * non-positive pivot or the refined max |I - A_c X| stays above 1e-12.  *residual = the final
+ * max_ij |(I - A_c X)_ij|, computed on the device in FP64.  Either pointer may be NULL.  Host
+ * memory.  Returns CPC_OK, or CPC_EINVAL if h is NULL. */
+int cpc_coarse_inverse_info(const cpc_handle* h, int32_t* method, double* residual);
+
 /* ---- inspection (tests and diagnostics; all synchronous, outputs in HOST memory) ---------- */
 
 /* Kernel launches of one cpc_solve with the handle's preconditioner: *per_iteration nodes in the

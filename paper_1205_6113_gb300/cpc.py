@@ -69,6 +69,7 @@ SIGNATURES = [
     ("cpc_solve_launches", _I32, [_P, _P, _P]),
     ("cpc_sweep_time_us", _I32, [_P, _I32, _I32, _P]),
     ("cpc_setup_phases_ms", _I32, [_P, _P, _I32]),
+    ("cpc_coarse_inverse_info", _I32, [_P, _P, _P]),
     ("cpc_num_levels", _I32, [_P]),
     ("cpc_level_info", _I32, [_P, _I32, _P]),
     ("cpc_level_layout", _I32, [_P, _I32, _P]),
@@ -348,6 +349,13 @@ class Solver:
         ms = np.zeros(4)
         _check(load().cpc_setup_phases_ms(self._h, ctypes.c_void_p(ms.ctypes.data), 4), self._h)
         return dict(zip(("coarsening", "colouring", "coarsest_inverse", "layouts"), [float(v) for v in ms]))
+
+    def coarse_inverse_info(self):
+        """(method, residual) of the coarsest level's inverse: method 1 = FP32 Cholesky inverse with
+        Newton-Schulz refinement, 0 = FP64 Cholesky inverse; residual = max |I - A_c X|."""
+        m, r = ctypes.c_int32(), ctypes.c_double()
+        _check(load().cpc_coarse_inverse_info(self._h, ctypes.byref(m), ctypes.byref(r)), self._h)
+        return m.value, r.value
 
     def sweep_time_us(self, l, reps=20):
         """Microseconds per forward Gauss-Seidel sweep of level l, replayed from a CUDA graph."""

@@ -246,6 +246,13 @@ int cpc_setup_phases_ms(const cpc_handle* h, double* ms, int32_t cap) {
     return CPC_OK;
 }
 
+int cpc_coarse_inverse_info(const cpc_handle* h, int32_t* method, double* residual) {
+    if (!h) return CPC_EINVAL;
+    if (method) *method = h->h.inv_method;
+    if (residual) *residual = h->h.inv_resid;
+    return CPC_OK;
+}
+
 int cpc_sweep_time_us(cpc_handle* h, int32_t level, int32_t reps, double* us) {
     if (!h || !us) return CPC_EINVAL;
     return guarded(h, [&] { *us = cpc::sweep_time_us(h->h, level, reps); });

@@ -77,6 +77,8 @@ struct Handle {
     int nc = 0;
     DBuf<double> Ainv;
     DBuf<float> Ainv32;
+    int inv_method = 0;     // 1: FP32 Cholesky inverse + Newton-Schulz steps; 0: FP64 Cholesky inverse
+    double inv_resid = 0;   // max |I - A_c Ainv| measured after setup
     // fine-level vectors
     DBuf<double> b, x, r, z, p, q, t, y;
     DBuf<float> z32, t32, y32;

@@ -16,8 +16,10 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <memory>
 
 #include "handle.cuh"
@@ -1787,21 +1789,24 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 }
 
 // ============================================================================================
-// Coarsest level: dense Cholesky A_c = L L^T and the explicit inverse (Algorithm 3.2, step 2(b)).
-// Blocked right-looking factorisation with panels of NB = 32 columns:
+// Coarsest level: the explicit inverse X = A_c^{-1} (Algorithm 3.2, step 2(b)).
+// Dense Cholesky A_c = L L^T, blocked right-looking with panels of NB = 32 columns:
 //   k_chol_diag   factor the 32 x 32 diagonal block with four warps and invert it,
 //   k_chol_trsm   L21 = A21 L11^{-T} as a tile product with that inverse,
 //   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles;
 // then W = L^{-1} by row panels (k_trinv_panel, k_trinv_update) and A_c^{-1} = W^T W (k_lauum_part,
-// k_lauum_sum).
-// L is left in the lower triangle of M.
+// k_lauum_sum).  L is left in the lower triangle of M.  The kernels are templated on the element
+// type: the inverse is first formed in FP32 (FP64 issue is scarce on this part) and then refined
+// to FP64 accuracy by Newton-Schulz steps (refined_inverse); the FP64 instantiation is the
+// fallback when that does not converge.
 // ============================================================================================
 constexpr int CHOL_NB = 32;
 
-__global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const double* val, double* M) {
+template <class T>
+__global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const double* val, T* M) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int p = ptr[i]; p < ptr[i + 1]; ++p) M[(size_t)i * n + col[p]] = val[p];
+    for (int p = ptr[i]; p < ptr[i + 1]; ++p) M[(size_t)i * n + col[p]] = T(val[p]);
 }
 
 // Factor the nb x nb diagonal block (nb <= 32) in shared memory with CHOL_DT threads, write L11
@@ -1812,28 +1817,29 @@ __global__ void k_csr_to_dense(int n, const int* ptr, const int* col, const doub
 // below, so every step is a short parallel update.
 constexpr int CHOL_DT = 128;
 
-__global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, double* M, double* Li, int* fail) {
-    __shared__ double D[CHOL_NB][CHOL_NB + 1];
-    __shared__ double X[CHOL_NB][CHOL_NB + 1];
+template <class T>
+__global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, T* M, T* Li, int* fail) {
+    __shared__ T D[CHOL_NB][CHOL_NB + 1];
+    __shared__ T X[CHOL_NB][CHOL_NB + 1];
     const int tid = threadIdx.x;
     const int nb = min(CHOL_NB, n - jb);
     if (*(volatile int*)fail) return;
     for (int t = tid; t < CHOL_NB * CHOL_NB; t += CHOL_DT) {
         const int r = t / CHOL_NB, c = t % CHOL_NB;
-        D[r][c] = (r < nb && c <= r) ? M[(size_t)(jb + r) * n + jb + c] : 0.0;
-        X[r][c] = (r == c && r < nb) ? 1.0 : 0.0;
+        D[r][c] = (r < nb && c <= r) ? M[(size_t)(jb + r) * n + jb + c] : T(0);
+        X[r][c] = (r == c && r < nb) ? T(1) : T(0);
     }
     __syncthreads();
-    __shared__ double piv_inv;
+    __shared__ T piv_inv;
     __shared__ int piv_bad;
     for (int j = 0; j < nb; ++j) {
         if (tid == 0) {                                       // one thread takes the pivot's root
-            const double d = D[j][j];
-            piv_bad = !(d > 0.0) || !isfinite(d);
+            const T d = D[j][j];
+            piv_bad = !(d > T(0)) || !isfinite(d);
             if (!piv_bad) {
-                const double sj = sqrt(d);
+                const T sj = sqrt(d);
                 D[j][j] = sj;
-                piv_inv = 1.0 / sj;
+                piv_inv = T(1) / sj;
             }
         }
         __syncthreads();
@@ -1841,7 +1847,7 @@ __global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, double* M,
             if (tid == 0) *fail = 1;
             return;
         }
-        const double inv = piv_inv;
+        const T inv = piv_inv;
         for (int r = j + 1 + tid; r < nb; r += CHOL_DT) D[r][j] *= inv;
         __syncthreads();
         const int m = nb - j - 1;
@@ -1855,11 +1861,11 @@ __global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, double* M,
         const int r = t / CHOL_NB, c = t % CHOL_NB;
         if (r < nb && c <= r) M[(size_t)(jb + r) * n + jb + c] = D[r][c];
     }
-    __shared__ double rdiag[CHOL_NB];
-    if (tid < nb) rdiag[tid] = 1.0 / D[tid][tid];
+    __shared__ T rdiag[CHOL_NB];
+    if (tid < nb) rdiag[tid] = T(1) / D[tid][tid];
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        const double rj = rdiag[j];
+        const T rj = rdiag[j];
         for (int c = tid; c <= j; c += CHOL_DT) X[j][c] *= rj;
         __syncthreads();
         const int m = nb - j - 1;
@@ -1874,21 +1880,22 @@ __global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, double* M,
 
 // Rows i >= jb + nb of the panel: l_i = a_i L11^{-T} = a_i Li^T, a tile product (16 rows x 32
 // columns per block of 128 threads; each thread 4 columns of one row).
-__global__ void __launch_bounds__(128) k_chol_trsm(int n, int jb, double* M, const double* Li, const int* fail) {
-    __shared__ double As[16][CHOL_NB + 1], Ls[CHOL_NB][CHOL_NB + 1];
+template <class T>
+__global__ void __launch_bounds__(128) k_chol_trsm(int n, int jb, T* M, const T* Li, const int* fail) {
+    __shared__ T As[16][CHOL_NB + 1], Ls[CHOL_NB][CHOL_NB + 1];
     if (*(volatile int*)fail) return;
     const int nb = min(CHOL_NB, n - jb);
     const int i0 = jb + nb + blockIdx.x * 16;
     for (int t = threadIdx.x; t < 16 * CHOL_NB; t += 128) {
         const int r = t / CHOL_NB, c = t % CHOL_NB;
-        As[r][c] = (i0 + r < n && c < nb) ? M[(size_t)(i0 + r) * n + jb + c] : 0.0;
+        As[r][c] = (i0 + r < n && c < nb) ? M[(size_t)(i0 + r) * n + jb + c] : T(0);
     }
     for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += 128) Ls[t / CHOL_NB][t % CHOL_NB] = Li[t];
     __syncthreads();
     const int row = threadIdx.x / 8, c0 = (threadIdx.x % 8) * 4;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int m = 0; m < CHOL_NB; ++m) {
-        const double a = As[row][m];
+        const T a = As[row][m];
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += a * Ls[c0 + q][m];
     }
@@ -1899,38 +1906,38 @@ __global__ void __launch_bounds__(128) k_chol_trsm(int n, int jb, double* M, con
             if (c0 + q < nb) M[(size_t)i * n + jb + c0 + q] = acc[q];
 }
 
-// FP64 tile products for the dense factorisation and inverse: one 256-thread block computes a
-// 64 x 64 tile, each thread a 4 x 4 block of it, from 32-wide slices of the operands staged in
-// shared memory.  FP64 issue bounds these kernels on this part, so every FMA reads its operands
-// from registers loaded once per slice.
+// Tile products for the dense factorisation, the inverse and its refinement: one 256-thread block
+// computes a 64 x 64 tile, each thread a 4 x 4 block of it, from 32-wide slices of the operands
+// staged in shared memory.  FP64 issue bounds the FP64 instantiations on this part, so every FMA
+// reads its operands from registers loaded once per slice.
 constexpr int DT_T = 64;           // tile edge
 constexpr int DT_K = 32;           // slice depth
 
 // Loads rows [r0, r0 + 64) x columns [c0, c0 + 32) of a row-major matrix with leading dimension ld
 // (zero outside rows < nr, columns < nc) into S[64][33] (row r, column c at S[r][c]).
-__device__ __forceinline__ void dt_load_rows(double (*S)[DT_K + 1], const double* M, int ld, int r0, int c0, int nr,
-                                             int nc) {
+template <class T>
+__device__ __forceinline__ void dt_load_rows(T (*S)[DT_K + 1], const T* M, int ld, int r0, int c0, int nr, int nc) {
     for (int t = threadIdx.x; t < DT_T * DT_K; t += 256) {
         const int r = t / DT_K, c = t % DT_K;
-        S[r][c] = (r0 + r < nr && c0 + c < nc) ? M[(size_t)(r0 + r) * ld + c0 + c] : 0.0;
+        S[r][c] = (r0 + r < nr && c0 + c < nc) ? M[(size_t)(r0 + r) * ld + c0 + c] : T(0);
     }
 }
 
 // Loads rows [k0, k0 + 32) x columns [c0, c0 + 64) into S[64][33] transposed (S[c][k]).
-__device__ __forceinline__ void dt_load_cols(double (*S)[DT_K + 1], const double* M, int ld, int k0, int c0, int nk,
-                                             int nc) {
+template <class T>
+__device__ __forceinline__ void dt_load_cols(T (*S)[DT_K + 1], const T* M, int ld, int k0, int c0, int nk, int nc) {
     for (int t = threadIdx.x; t < DT_T * DT_K; t += 256) {
         const int k = t / DT_T, c = t % DT_T;
-        S[c][k] = (k0 + k < nk && c0 + c < nc) ? M[(size_t)(k0 + k) * ld + c0 + c] : 0.0;
+        S[c][k] = (k0 + k < nk && c0 + c < nc) ? M[(size_t)(k0 + k) * ld + c0 + c] : T(0);
     }
 }
 
 // acc[a][b] += sum_k X[ty * 4 + a][k] * Y[tx * 4 + b][k] over one slice.
-__device__ __forceinline__ void dt_mac(const double (*X)[DT_K + 1], const double (*Y)[DT_K + 1], double (&acc)[4][4],
-                                       int tx, int ty) {
+template <class T>
+__device__ __forceinline__ void dt_mac(const T (*X)[DT_K + 1], const T (*Y)[DT_K + 1], T (&acc)[4][4], int tx, int ty) {
 #pragma unroll 4
     for (int k = 0; k < DT_K; ++k) {
-        double xa[4], yb[4];
+        T xa[4], yb[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) xa[a] = X[ty * 4 + a][k];
 #pragma unroll
@@ -1944,20 +1951,21 @@ __device__ __forceinline__ void dt_mac(const double (*X)[DT_K + 1], const double
 
 // Trailing update of the lower triangle: a_ik -= sum_m l_im l_km over the panel columns
 // [jb, jb + nb), for jb + nb <= k <= i; block (bi, bk) with bk <= bi covers a 64 x 64 tile.
-__global__ void __launch_bounds__(256) k_chol_syrk(int n, int jb, double* M, const int* fail) {
-    __shared__ double Li[DT_T][DT_K + 1], Lk[DT_T][DT_K + 1];
+template <class T>
+__global__ void __launch_bounds__(256) k_chol_syrk(int n, int jb, T* M, const int* fail) {
+    __shared__ T Li[DT_T][DT_K + 1], Lk[DT_T][DT_K + 1];
     if (*(volatile int*)fail) return;
     const int bi = blockIdx.y, bk = blockIdx.x;
     if (bk > bi) return;
     const int nb = min(CHOL_NB, n - jb);
     const int t0 = jb + nb;
     const int i0 = t0 + bi * DT_T, k0 = t0 + bk * DT_T;
-    dt_load_rows(Li, M, n, i0, jb, n, jb + nb);
-    dt_load_rows(Lk, M, n, k0, jb, n, jb + nb);
+    dt_load_rows<T>(Li, M, n, i0, jb, n, jb + nb);
+    dt_load_rows<T>(Lk, M, n, k0, jb, n, jb + nb);
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4] = {};
-    dt_mac(Li, Lk, acc, tx, ty);
+    T acc[4][4] = {};
+    dt_mac<T>(Li, Lk, acc, tx, ty);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1972,22 +1980,23 @@ __global__ void __launch_bounds__(256) k_chol_syrk(int n, int jb, double* M, con
 // start, held in W), for columns j < e = the panel's end; W is lower triangular, so columns from e
 // on stay zero.  A tile product: 32 rows x 16 columns per block of 128 threads, each thread 4 rows
 // of one column.
-__global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const double* Li, double* W, const int* fail) {
-    __shared__ double Rs[CHOL_NB][17], Ls[CHOL_NB][CHOL_NB + 1];
+template <class T>
+__global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const T* Li, T* W, const int* fail) {
+    __shared__ T Rs[CHOL_NB][17], Ls[CHOL_NB][CHOL_NB + 1];
     if (*(volatile int*)fail) return;
     const int nb = min(CHOL_NB, n - jb);
     const int e = jb + nb;
     const int j0 = blockIdx.x * 16;
     for (int t = threadIdx.x; t < CHOL_NB * 16; t += 128) {
         const int r = t / 16, c = t % 16;
-        Rs[r][c] = (r < nb && j0 + c < e) ? W[(size_t)(jb + r) * n + j0 + c] : 0.0;
+        Rs[r][c] = (r < nb && j0 + c < e) ? W[(size_t)(jb + r) * n + j0 + c] : T(0);
     }
     for (int t = threadIdx.x; t < CHOL_NB * CHOL_NB; t += 128) Ls[t / CHOL_NB][t % CHOL_NB] = Li[t];
     __syncthreads();
     const int col = threadIdx.x % 16, r0 = (threadIdx.x / 16) * 4;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int m = 0; m < CHOL_NB; ++m) {
-        const double v = Rs[m][col];
+        const T v = Rs[m][col];
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += Ls[r0 + q][m] * v;
     }
@@ -1999,18 +2008,19 @@ __global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const double
 }
 
 // Rows below panel p: R_ij -= sum_m l_i,jb+m w_jb+m,j for i >= e, j < e (e = the panel's end).
-__global__ void __launch_bounds__(256) k_trinv_update(int n, int jb, const double* L, double* W, const int* fail) {
-    __shared__ double Ls[DT_T][DT_K + 1], Ws[DT_T][DT_K + 1];
+template <class T>
+__global__ void __launch_bounds__(256) k_trinv_update(int n, int jb, const T* L, T* W, const int* fail) {
+    __shared__ T Ls[DT_T][DT_K + 1], Ws[DT_T][DT_K + 1];
     if (*(volatile int*)fail) return;
     const int nb = min(CHOL_NB, n - jb);
     const int e = jb + nb;
     const int i0 = e + blockIdx.y * DT_T, j0 = blockIdx.x * DT_T;
-    dt_load_rows(Ls, L, n, i0, jb, n, e);           // rows i, panel columns
-    dt_load_cols(Ws, W, n, jb, j0, e, e);           // panel rows of W, columns j < e (transposed)
+    dt_load_rows<T>(Ls, L, n, i0, jb, n, e);        // rows i, panel columns
+    dt_load_cols<T>(Ws, W, n, jb, j0, e, e);        // panel rows of W, columns j < e (transposed)
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4] = {};
-    dt_mac(Ls, Ws, acc, tx, ty);
+    T acc[4][4] = {};
+    dt_mac<T>(Ls, Ws, acc, tx, ty);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -2027,22 +2037,22 @@ __global__ void __launch_bounds__(256) k_trinv_update(int n, int jb, const doubl
 // SM.
 constexpr int LA_KS = 256;
 
-__global__ void __launch_bounds__(256) k_lauum_part(int n, const double* W, const int4* items, double* part,
-                                                     const int* fail) {
-    __shared__ double Wi[DT_T][DT_K + 1], Wj[DT_T][DT_K + 1];
+template <class T>
+__global__ void __launch_bounds__(256) k_lauum_part(int n, const T* W, const int4* items, T* part, const int* fail) {
+    __shared__ T Wi[DT_T][DT_K + 1], Wj[DT_T][DT_K + 1];
     if (*(volatile int*)fail) return;
     const int4 it = items[blockIdx.x];                        // bi, bj, k0, k1
     const int i0 = it.x * DT_T, j0 = it.y * DT_T;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4] = {};
+    T acc[4][4] = {};
     for (int k0 = it.z; k0 < it.w; k0 += DT_K) {
-        dt_load_cols(Wi, W, n, k0, i0, it.w, n);
-        dt_load_cols(Wj, W, n, k0, j0, it.w, n);
+        dt_load_cols<T>(Wi, W, n, k0, i0, it.w, n);
+        dt_load_cols<T>(Wj, W, n, k0, j0, it.w, n);
         __syncthreads();
-        dt_mac(Wi, Wj, acc, tx, ty);
+        dt_mac<T>(Wi, Wj, acc, tx, ty);
         __syncthreads();
     }
-    double* o = part + (size_t)blockIdx.x * DT_T * DT_T;
+    T* o = part + (size_t)blockIdx.x * DT_T * DT_T;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -2050,14 +2060,15 @@ __global__ void __launch_bounds__(256) k_lauum_part(int n, const double* W, cons
 }
 
 // Tile t: sum its pieces first[t] .. first[t] + cnt[t] - 1 in order.
+template <class T>
 __global__ void __launch_bounds__(256) k_lauum_sum(int n, const int4* items, const int* first, const int* cnt,
-                                                    const double* part, double* X, const int* fail) {
+                                                    const T* part, T* X, const int* fail) {
     if (*(volatile int*)fail) return;
     const int f = first[blockIdx.x], c = cnt[blockIdx.x];
     const int4 it = items[f];
     const int i0 = it.x * DT_T, j0 = it.y * DT_T;
     for (int e = threadIdx.x; e < DT_T * DT_T; e += 256) {
-        double v = part[(size_t)f * DT_T * DT_T + e];
+        T v = part[(size_t)f * DT_T * DT_T + e];
         for (int q = 1; q < c; ++q) v += part[(size_t)(f + q) * DT_T * DT_T + e];
         const int i = i0 + e / DT_T, j = j0 + e % DT_T;
         if (i < n && j < n) {
@@ -2067,14 +2078,18 @@ __global__ void __launch_bounds__(256) k_lauum_sum(int n, const int4* items, con
     }
 }
 
-__global__ void k_identity(int n, double* W) {
+template <class T>
+__global__ void k_identity(int n, T* W) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * n) return;
     const int i = (int)(t / n), j = (int)(t % n);
-    W[t] = i == j ? 1.0 : 0.0;
+    W[t] = i == j ? T(1) : T(0);
 }
 
-void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t s) {
+// Dense Cholesky inverse of the n x n SPD matrix in M (lower triangle read, L left there) into
+// Ainv (full, symmetric).  *fail = 1 on a non-positive or non-finite pivot.
+template <class T>
+void dense_chol_inverse(int n, T* M, T* Ainv, int* fail, cudaStream_t s) {
     // the pieces of W^T W (host tables copied first: pageable copies return once staged)
     const int tiles_all = (n + DT_T - 1) / DT_T;
     std::vector<int4> items;
@@ -2087,36 +2102,135 @@ void dense_chol_inverse(int n, double* M, double* Ainv, int* fail, cudaStream_t 
         }
     Tmp<int4> ditems(items.size(), s);
     Tmp<int> dfirst(first.size(), s), dcnt(cnt.size(), s);
-    Tmp<double> part(items.size() * DT_T * DT_T, s);
+    Tmp<T> part(items.size() * DT_T * DT_T, s);
     h2d(ditems.get(), items.data(), items.size(), s);
     h2d(dfirst.get(), first.data(), first.size(), s);
     h2d(dcnt.get(), cnt.data(), cnt.size(), s);
     const int np = (n + CHOL_NB - 1) / CHOL_NB;
-    Tmp<double> Li((size_t)np * CHOL_NB * CHOL_NB, s);         // L_pp^{-1} of every panel
+    Tmp<T> Li((size_t)np * CHOL_NB * CHOL_NB, s);               // L_pp^{-1} of every panel
     for (int jb = 0; jb < n; jb += CHOL_NB) {
         const int nb = std::min(CHOL_NB, n - jb);
-        double* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
-        k_chol_diag<<<1, CHOL_DT, 0, s>>>(n, jb, M, li, fail);
+        T* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
+        k_chol_diag<T><<<1, CHOL_DT, 0, s>>>(n, jb, M, li, fail);
         const int below = n - jb - nb;
         if (below > 0) {
-            k_chol_trsm<<<(below + 15) / 16, 128, 0, s>>>(n, jb, M, li, fail);
+            k_chol_trsm<T><<<(below + 15) / 16, 128, 0, s>>>(n, jb, M, li, fail);
             const int tiles = (below + DT_T - 1) / DT_T;
-            k_chol_syrk<<<dim3(tiles, tiles), 256, 0, s>>>(n, jb, M, fail);
+            k_chol_syrk<T><<<dim3(tiles, tiles), 256, 0, s>>>(n, jb, M, fail);
         }
     }
     // W = L^{-1} in a scratch of its own, then A^{-1} = W^T W
-    Tmp<double> W((size_t)n * n, s);
-    k_identity<<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, W.get());
+    Tmp<T> W((size_t)n * n, s);
+    k_identity<T><<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, W.get());
     for (int jb = 0; jb < n; jb += CHOL_NB) {
         const int e = std::min(jb + CHOL_NB, n);
-        const double* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
-        k_trinv_panel<<<(e + 15) / 16, 128, 0, s>>>(n, jb, li, W.get(), fail);
+        const T* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
+        k_trinv_panel<T><<<(e + 15) / 16, 128, 0, s>>>(n, jb, li, W.get(), fail);
         if (e < n)
-            k_trinv_update<<<dim3((e + DT_T - 1) / DT_T, (n - e + DT_T - 1) / DT_T), 256, 0, s>>>(n, jb, M, W.get(),
-                                                                                                 fail);
+            k_trinv_update<T><<<dim3((e + DT_T - 1) / DT_T, (n - e + DT_T - 1) / DT_T), 256, 0, s>>>(n, jb, M, W.get(),
+                                                                                                    fail);
     }
-    k_lauum_part<<<(int)items.size(), 256, 0, s>>>(n, W.get(), ditems.get(), part.get(), fail);
-    k_lauum_sum<<<(int)first.size(), 256, 0, s>>>(n, ditems.get(), dfirst.get(), dcnt.get(), part.get(), Ainv, fail);
+    k_lauum_part<T><<<(int)items.size(), 256, 0, s>>>(n, W.get(), ditems.get(), part.get(), fail);
+    k_lauum_sum<T><<<(int)first.size(), 256, 0, s>>>(n, ditems.get(), dfirst.get(), dcnt.get(), part.get(), Ainv, fail);
+    CPC_LAUNCH_CK();
+}
+
+// --------------------------------------------------------------------------------------------
+// Refinement of an approximate inverse by Newton-Schulz steps (Schulz's iteration for the
+// inverse): X <- X (2I - A_c X) = X + X E with E = I - A_c X, so E_new = E^2 in exact arithmetic.
+// E is formed in FP64 from the sparse A_c and the FP64 X; the correction X E needs only the
+// relative accuracy of E's size, so it is a tile product in FP32 (X and E rounded), added to X in
+// FP64.  From the FP32 Cholesky inverse (max |E| about 1e-5 at kappa 6e5) two steps reach the FP64
+// rounding level; INV_STEPS = 3, then the final max |E| decides (INV_TOL) whether X is kept.
+// --------------------------------------------------------------------------------------------
+constexpr int INV_STEPS = 3;
+constexpr double INV_TOL = 1e-12;
+
+template <class A, class B>
+__global__ void k_convert(int64_t count, const A* x, B* y, const int* fail) {
+    if (*(volatile int*)fail) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) y[t] = B(x[t]);
+}
+
+// E = I - A_c X, row i = blockIdx.y, columns over the threads; E (if not null) is stored rounded
+// to FP32.  The largest |E_ij| goes to *emax as the bits of a non-negative double (which order as
+// unsigned integers); a NaN or an infinity counts as infinity.
+__global__ void __launch_bounds__(256) k_inv_resid(int n, const int* ptr, const int* col, const double* val,
+                                                   const double* X, float* E, unsigned long long* emax,
+                                                   const int* fail) {
+    __shared__ double wmax[8];
+    if (*(volatile int*)fail) return;
+    const int i = blockIdx.y, j = blockIdx.x * 256 + threadIdx.x;
+    double m = 0.0;
+    if (j < n) {
+        double e = i == j ? 1.0 : 0.0;
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) e -= val[p] * X[(size_t)col[p] * n + j];
+        if (E) E[(size_t)i * n + j] = (float)e;
+        m = fabs(e);
+        if (!(m <= DBL_MAX)) m = INFINITY;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmax(m, wmax[w]);
+        atomicMax(emax, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// X += Xf E as FP32 tiles (Xf = X rounded to FP32), with the sum in FP64; Xn receives the new X
+// rounded to FP32 for the next step (a buffer of its own: other blocks still read Xf).
+__global__ void __launch_bounds__(256) k_inv_correct(int n, const float* Xf, const float* E, double* X, float* Xn,
+                                                     const int* fail) {
+    __shared__ float Xs[DT_T][DT_K + 1], Es[DT_T][DT_K + 1];
+    if (*(volatile int*)fail) return;
+    const int i0 = blockIdx.y * DT_T, j0 = blockIdx.x * DT_T;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < n; k0 += DT_K) {
+        dt_load_rows<float>(Xs, Xf, n, i0, k0, n, n);          // rows i, columns k
+        dt_load_cols<float>(Es, E, n, k0, j0, n, n);           // rows k, columns j (transposed)
+        __syncthreads();
+        dt_mac<float>(Xs, Es, acc, tx, ty);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+            if (i < n && j < n) {
+                const double v = X[(size_t)i * n + j] + (double)acc[a][b];
+                X[(size_t)i * n + j] = v;
+                Xn[(size_t)i * n + j] = (float)v;
+            }
+        }
+}
+
+// X = A_c^{-1} from the FP32 Cholesky inverse and INV_STEPS Newton-Schulz steps.  *fail32 = 1 if
+// the FP32 factorisation broke down (the later kernels then do nothing); emax[k] = max |E| before
+// step k, emax[INV_STEPS] after the last step (all zero-initialised by the caller).
+void refined_inverse(const Csr& Ac, double* X, int* fail32, unsigned long long* emax, cudaStream_t s) {
+    const int n = Ac.n;
+    const size_t nn = (size_t)n * n;
+    Tmp<float> Xa(nn, s), Xb(nn, s), E(nn, s);
+    {
+        Tmp<float> M(nn, s);
+        CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(float) * nn, s));
+        k_csr_to_dense<float><<<nblk(n), TPB, 0, s>>>(n, Ac.ptr.p, Ac.col.p, Ac.val.p, M.get());
+        dense_chol_inverse<float>(n, M.get(), Xa.get(), fail32, s);
+    }
+    k_convert<float, double><<<(int)((nn + TPB - 1) / TPB), TPB, 0, s>>>((int64_t)nn, Xa.get(), X, fail32);
+    float* xf = Xa.get();
+    float* xn = Xb.get();
+    const dim3 rgrid((n + 255) / 256, n), tgrid((n + DT_T - 1) / DT_T, (n + DT_T - 1) / DT_T);
+    for (int k = 0; k < INV_STEPS; ++k) {
+        k_inv_resid<<<rgrid, 256, 0, s>>>(n, Ac.ptr.p, Ac.col.p, Ac.val.p, X, E.get(), emax + k, fail32);
+        k_inv_correct<<<tgrid, 256, 0, s>>>(n, xf, E.get(), X, xn, fail32);
+        std::swap(xf, xn);
+    }
+    k_inv_resid<<<rgrid, 256, 0, s>>>(n, Ac.ptr.p, Ac.col.p, Ac.val.p, X, nullptr, emax + INV_STEPS, fail32);
     CPC_LAUNCH_CK();
 }
 
@@ -2562,7 +2676,9 @@ void setup_handle(Handle& h, const cpc_csr& in) {
     h.nc = Lc.n;
     if (h.nc > DENSE_MAX) fail(CPC_ESETUP, "coarsest level too large for the dense solve");
     h.Ainv.alloc((size_t)h.nc * h.nc);
-    Tmp<int> inv_fail(1, s2);
+    // flags[0]: FP64 factorisation failure, flags[1]: FP32 factorisation failure
+    Tmp<int> inv_fail(2, s2);
+    Tmp<unsigned long long> emax(INV_STEPS + 2, s2);
     cudaEvent_t c0, c1;
     CPC_CK(cudaEventCreate(&c0));
     CPC_CK(cudaEventCreate(&c1));
@@ -2571,13 +2687,9 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         ~CGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } cguard{c0, c1};
     CPC_CK(cudaEventRecord(c0, s2));
-    {
-        Tmp<double> M((size_t)h.nc * h.nc, s2);
-        CPC_CK(cudaMemsetAsync(inv_fail.get(), 0, sizeof(int), s2));
-        CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s2));
-        k_csr_to_dense<<<nblk(h.nc), TPB, 0, s2>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
-        dense_chol_inverse(h.nc, M.get(), h.Ainv.p, inv_fail.get(), s2);
-    }
+    CPC_CK(cudaMemsetAsync(inv_fail.get(), 0, 2 * sizeof(int), s2));
+    CPC_CK(cudaMemsetAsync(emax.get(), 0, (INV_STEPS + 2) * sizeof(unsigned long long), s2));
+    refined_inverse(Lc.A, h.Ainv.p, inv_fail.get() + 1, emax.get(), s2);
     CPC_CK(cudaEventRecord(c1, s2));
     for (int l = 0; l < nl; ++l) setup_level_sells(h.lev[l], s, l == nl - 1, h.opt.autotune == 1 && l > 0);
     {   // fine A in natural order for the SpMVs
@@ -2592,6 +2704,30 @@ void setup_handle(Handle& h, const cpc_csr& in) {
         CPC_CK(cudaStreamSynchronize(s));
     }
     CPC_CK(cudaEventRecord(ph[2], s));                          // layouts done
+    {   // keep the refined inverse if its residual reached INV_TOL, else the FP64 Cholesky inverse
+        const int f32 = d2h(inv_fail.get() + 1, s2);
+        const unsigned long long eb = d2h(emax.get() + INV_STEPS, s2);
+        double e;
+        std::memcpy(&e, &eb, sizeof e);
+        h.inv_method = 1;
+        h.inv_resid = f32 ? INFINITY : e;
+        if (f32 || !(e <= INV_TOL)) {
+            h.inv_method = 0;
+            {
+                Tmp<double> M((size_t)h.nc * h.nc, s2);
+                CPC_CK(cudaMemsetAsync(M.get(), 0, sizeof(double) * h.nc * h.nc, s2));
+                k_csr_to_dense<double><<<nblk(h.nc), TPB, 0, s2>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
+                dense_chol_inverse<double>(h.nc, M.get(), h.Ainv.p, inv_fail.get(), s2);
+            }
+            k_inv_resid<<<dim3((h.nc + 255) / 256, h.nc), 256, 0, s2>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p,
+                                                                         h.Ainv.p, nullptr, emax.get() + INV_STEPS + 1,
+                                                                         inv_fail.get());
+            CPC_LAUNCH_CK();
+            CPC_CK(cudaEventRecord(c1, s2));
+            const unsigned long long eb64 = d2h(emax.get() + INV_STEPS + 1, s2);
+            std::memcpy(&h.inv_resid, &eb64, sizeof(double));
+        }
+    }
     if (d2h(inv_fail.get(), s2)) fail(CPC_ESETUP, "coarsest operator is not positive definite");
     CPC_CK(cudaStreamWaitEvent(s, c1, 0));
     CPC_CK(cudaEventRecord(e2, s));

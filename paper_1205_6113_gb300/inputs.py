@@ -176,11 +176,12 @@ def small_3d(nx, ny, nz, seed=7, sigma=1.5, corr_len=3.0, kz_ratio=0.1, dirichle
     return p
 
 
-def long_range_2d(nx=64, ny=64, radius=14.0, seed=60):
+def long_range_2d(nx=64, ny=64, radius=14.0, seed=60, shift=1e-2):
     """CSR (rowptr, col, val) of an SPD M-matrix on an nx x ny grid: strong couplings to the four
     grid neighbours (weights 0.5..1.5) and weak ones (weights 0.5e-3..1.5e-3) to every other point
-    within Euclidean distance ``radius``; diagonal = the sum of the row's couplings + 1e-2.  The
-    strong part keeps many coarse points, the weak part makes the Galerkin rows long."""
+    within Euclidean distance ``radius``; diagonal = the sum of the row's couplings + ``shift``.  The
+    strong part keeps many coarse points, the weak part makes the Galerkin rows long; a tiny shift
+    makes the matrix nearly singular (smallest eigenvalue about ``shift``, the constant vector)."""
     rng = np.random.default_rng(seed)
     n = nx * ny
     r = int(np.floor(radius))
@@ -208,7 +209,7 @@ def long_range_2d(nx=64, ny=64, radius=14.0, seed=60):
     np.add.at(diag, rows, -vals)
     rows = np.concatenate([rows, np.arange(n)])
     cols = np.concatenate([cols, np.arange(n)])
-    vals = np.concatenate([vals, diag + 1e-2])
+    vals = np.concatenate([vals, diag + shift])
     order = np.lexsort((cols, rows))
     rowptr = np.zeros(n + 1, dtype=np.int32)
     rowptr[1:] = np.cumsum(np.bincount(rows, minlength=n))

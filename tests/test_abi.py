@@ -61,6 +61,7 @@ def test_pure_host_entry_points(lib):
     h = ctypes.c_void_p()
     assert L.cpc_setup(None, None, ctypes.byref(h)) == 1 and not h.value
     assert L.cpc_solve(None, None, None, 1e-6, 10, None, None, 0) == 1
+    assert L.cpc_coarse_inverse_info(None, None, None) == 1
     L.cpc_destroy(None)
     # mixed-hybrid sizes are host arithmetic: they must match the oracle's assembled system
     import oracle as O

@@ -2,9 +2,9 @@
 two-point-flux matrix (1,048,576 unknowns), B_co with the red-black IC(0) ordering and the
 multicolour Gauss-Seidel V-cycle, exactly the handle that bench.py times.
 
-At this size the hierarchy has six levels with 12 to 21 colours on the coarse levels, so the
-wide-batch colour-step kernels, the one-pass black-row B_co step (2) and the blocked Cholesky of
-the 489-row coarsest level all run.  The oracle (single-threaded FP64) needs a few seconds for its
+At this size the hierarchy has five levels with 12 to 24 colours on the coarse levels, so the
+wide-batch colour-step kernels, the one-pass black-row B_co step (2) and the refined inverse of
+the 1,823-row coarsest level (FP32 blocked Cholesky, then Newton-Schulz steps) all run.  The oracle (single-threaded FP64) needs a few seconds for its
 setup and about half a second per preconditioner application here.
 
 Gates: structure identical (splitting, colouring, level patterns), level values to 1e-12,
@@ -69,6 +69,14 @@ def test_full_size_hierarchy_matches_oracle(full):
             assert np.array_equal(colour, colo), l
     assert s.level_info(0)["ncolours"] == 2
     assert max(s.level_info(l)["ncolours"] for l in range(1, s.nlevels - 1)) >= 12
+    # the coarsest inverse: FP32 Cholesky refined to FP64 accuracy, and its solve equals the
+    # oracle's dense Cholesky solve
+    method, res = s.coarse_inverse_info()
+    assert method == 1 and res <= 1e-12
+    last = orc.nlevels - 1
+    x = inputs.random_vector(orc.level_sizes(last)["n"], seed=70)
+    y = s.level_apply(last, 3, torch.tensor(x, device=DEV)).cpu().numpy()
+    assert rel(y, orc.level_apply(last, 3, x)) < 1e-11
 
 
 def test_full_size_bco_application_matches_oracle(full):

@@ -156,7 +156,33 @@ def test_blocked_cholesky_on_a_large_coarsest_level():
     r = inputs.random_vector(A.n, seed=53)
     z = s.apply(torch.tensor(r, device=DEV), which="bco").cpu().numpy()
     assert rel(z, orc.apply(O.BCO, r)) < 1e-11
+    # the FP32 Cholesky inverse refined by Newton-Schulz steps reached FP64 accuracy and was kept
+    method, res = s.coarse_inverse_info()
+    assert method == 1 and res <= 1e-12
     s.close()
+
+
+def test_coarse_inverse_falls_back_to_fp64_cholesky():
+    """A nearly singular M-matrix (diagonal excess 1e-9 over the row sums, so the smallest
+    eigenvalue is about 1e-9): kappa(A_c) is about 6e9 on its 1,533-row coarsest level, beyond what
+    an FP32 factorisation resolves, so the Newton-Schulz steps from the FP32 inverse do not
+    converge and setup forms the FP64 Cholesky inverse instead.  That coarsest solve must equal the
+    oracle's dense Cholesky solve within kappa * eps, and a well-shifted matrix of the same pattern
+    keeps the refined inverse."""
+    for shift, method_want in [(1e-9, 0), (1e-2, 1)]:
+        ptr, col, val = inputs.long_range_2d(nx=64, ny=64, radius=1.5, seed=61, shift=shift)
+        A = O.Csr(len(ptr) - 1, ptr, col, val)
+        orc = O.Oracle(A)
+        s = cpc.Solver(ptr, col, val)
+        assert s.nlevels == orc.nlevels == 2
+        method, res = s.coarse_inverse_info()
+        assert method == method_want, (shift, method, res)
+        assert res < (1e-7 if method == 0 else 1e-12)
+        nc = s.level_info(1)["n"]
+        x = inputs.random_vector(nc, seed=62)
+        y = s.level_apply(1, 3, torch.tensor(x, device=DEV)).cpu().numpy()
+        assert rel(y, orc.level_apply(1, 3, x)) < (1e-6 if method == 0 else 1e-12)
+        s.close()
 
 
 def test_chained_cycles_read_fresh_data():
