@@ -34,6 +34,24 @@ inline void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 // ---------------------------------------------------------------------------------------------
 // Device buffer (owning, move-only).
 // ---------------------------------------------------------------------------------------------
+// Stream on which DBuf::alloc takes its memory while an AllocOn scope is open (this thread only).
+// cudaMalloc and cudaFree can wait for the work queued on the whole device, so a setup phase that
+// runs beside another stream's kernels allocates stream-ordered instead, from the device's default
+// pool.  The buffer is owned like any other: released inside the scope with cudaFreeAsync on that
+// stream, after it with cudaFree (which accepts pool memory).  Code that uses a buffer on a stream
+// of its own opens AllocOn(nullptr).
+inline cudaStream_t& alloc_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
+struct AllocOn {
+    cudaStream_t prev;
+    explicit AllocOn(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+    ~AllocOn() { alloc_stream() = prev; }
+    AllocOn(const AllocOn&) = delete;
+    AllocOn& operator=(const AllocOn&) = delete;
+};
+
 // alloc_async: a stream-ordered buffer for setup temporaries, freed on the same stream, so that its
 // release does not wait for the whole device as cudaFree does; the stream must outlive it.
 template <class T>
@@ -41,15 +59,18 @@ struct DBuf {
     T* p = nullptr;
     size_t n = 0;
     cudaStream_t fs = nullptr;              // stream of a stream-ordered buffer
+    bool pooled = false;                    // taken from the pool inside an AllocOn scope
     DBuf() = default;
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
-    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), fs(o.fs) { o.p = nullptr; o.n = 0; o.fs = nullptr; }
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), fs(o.fs), pooled(o.pooled) {
+        o.p = nullptr; o.n = 0; o.fs = nullptr; o.pooled = false;
+    }
     DBuf& operator=(DBuf&& o) noexcept {
         if (this != &o) {
             release();
-            p = o.p; n = o.n; fs = o.fs;
-            o.p = nullptr; o.n = 0; o.fs = nullptr;
+            p = o.p; n = o.n; fs = o.fs; pooled = o.pooled;
+            o.p = nullptr; o.n = 0; o.fs = nullptr; o.pooled = false;
         }
         return *this;
     }
@@ -57,7 +78,12 @@ struct DBuf {
     void alloc(size_t count) {
         release();
         if (count == 0) count = 1;          // keep a valid pointer for empty arrays
-        CPC_CK(cudaMalloc(&p, count * sizeof(T)));
+        if (cudaStream_t s = alloc_stream()) {
+            CPC_CK(cudaMallocAsync(&p, count * sizeof(T), s));
+            pooled = true;
+        } else {
+            CPC_CK(cudaMalloc(&p, count * sizeof(T)));
+        }
         n = count;
     }
     void alloc_async(size_t count, cudaStream_t s) {
@@ -70,11 +96,13 @@ struct DBuf {
     void release() {
         if (p) {
             if (fs) cudaFreeAsync(p, fs);
+            else if (pooled && alloc_stream()) cudaFreeAsync(p, alloc_stream());
             else cudaFree(p);
         }
         p = nullptr;
         n = 0;
         fs = nullptr;
+        pooled = false;
     }
     T* get() const { return p; }
 };

@@ -1099,6 +1099,7 @@ void spmv_fine(Handle& h, const double* x, double* y, cudaStream_t s) {
 }
 
 float time_gs_sweep(const Sell& S, int n) {
+    AllocOn plain(nullptr);                 // f and x are used on cs, not on a setup stream
     cudaStream_t cs;
     CPC_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     struct SG { cudaStream_t s; ~SG() { cudaStreamSynchronize(s); cudaStreamDestroy(s); } } sg{cs};
