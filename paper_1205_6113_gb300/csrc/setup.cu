@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 
 #include "handle.cuh"
 #include "tpfa_cell.cuh"
@@ -1878,6 +1879,74 @@ __global__ void __launch_bounds__(CHOL_DT) k_chol_diag(int n, int jb, T* M, T* L
     for (int t = tid; t < CHOL_NB * CHOL_NB; t += CHOL_DT) Li[t] = X[t / CHOL_NB][t % CHOL_NB];
 }
 
+// The FP32 diagonal block on one warp, with no block barrier: lane r keeps row r of the block in
+// registers (rows beyond nb are identity rows, which factor trivially).  Column j's pivot a_jj is
+// broadcast from lane j by a shuffle and each later column c receives l_cj from lane c the same
+// way; then Li = L11^{-1} right-looking in the same form (lane r keeps row r of X).  Shared memory
+// only stages the coalesced loads and stores.
+__global__ void __launch_bounds__(32) k_chol_diag_warp(int n, int jb, float* M, float* Li, int* fail) {
+    __shared__ float T[CHOL_NB][CHOL_NB + 1];
+    if (*(volatile int*)fail) return;
+    const unsigned FULL = 0xffffffffu;
+    const int r = threadIdx.x;
+    const int nb = min(CHOL_NB, n - jb);
+    {
+        float v[CHOL_NB];                                       // all 32 loads in flight
+#pragma unroll
+        for (int q = 0; q < CHOL_NB; ++q) v[q] = (q < nb && r <= q) ? M[(size_t)(jb + q) * n + jb + r] : 0.f;
+#pragma unroll
+        for (int q = 0; q < CHOL_NB; ++q) T[q][r] = v[q];       // coalesced: row q, column r
+    }
+    __syncwarp();
+    float a[CHOL_NB];
+#pragma unroll
+    for (int c = 0; c < CHOL_NB; ++c) a[c] = r < nb ? (c <= r ? T[r][c] : 0.f) : (c == r ? 1.f : 0.f);
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < CHOL_NB; ++j) {
+        const float d = __shfl_sync(FULL, a[j], j);            // a_jj, the same in every lane
+        bad = bad || !(d > 0.f) || !isfinite(d);
+        const float ljj = sqrtf(d);
+        if (r == j) a[j] = ljj;
+        if (r > j) a[j] *= 1.f / ljj;                          // l_rj
+#pragma unroll
+        for (int c = j + 1; c < CHOL_NB; ++c) {
+            const float lcj = __shfl_sync(FULL, a[j], c);
+            if (r >= c) a[c] -= a[j] * lcj;
+        }
+    }
+    if (bad) {                                                  // the same in every lane
+        if (r == 0) *fail = 1;
+        return;
+    }
+    float x[CHOL_NB];
+#pragma unroll
+    for (int c = 0; c < CHOL_NB; ++c) x[c] = c == r ? 1.f : 0.f;
+#pragma unroll
+    for (int j = 0; j < CHOL_NB; ++j) {
+        const float rj = 1.f / __shfl_sync(FULL, a[j], j);     // 1 / l_jj
+        if (r == j)
+#pragma unroll
+            for (int c = 0; c <= j; ++c) x[c] *= rj;
+#pragma unroll
+        for (int c = 0; c <= j; ++c) {
+            const float xjc = __shfl_sync(FULL, x[c], j);
+            if (r > j) x[c] -= a[j] * xjc;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < CHOL_NB; ++c) T[r][c] = (r < nb && c <= r) ? a[c] : 0.f;
+    __syncwarp();
+    for (int q = 0; q < nb; ++q)
+        if (r <= q) M[(size_t)(jb + q) * n + jb + r] = T[q][r];
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < CHOL_NB; ++c) T[r][c] = (r < nb && c <= r) ? x[c] : 0.f;
+    __syncwarp();
+    for (int q = 0; q < CHOL_NB; ++q) Li[q * CHOL_NB + r] = T[q][r];
+}
+
 // Rows i >= jb + nb of the panel: l_i = a_i L11^{-T} = a_i Li^T, a tile product (16 rows x 32
 // columns per block of 128 threads; each thread 4 columns of one row).
 template <class T>
@@ -1915,21 +1984,54 @@ constexpr int DT_K = 32;           // slice depth
 
 // Loads rows [r0, r0 + 64) x columns [c0, c0 + 32) of a row-major matrix with leading dimension ld
 // (zero outside rows < nr, columns < nc) into S[64][33] (row r, column c at S[r][c]).
+// (256 threads, 8 elements each: the loads of a thread are all issued before the first store.)
+constexpr int DT_PER = DT_T * DT_K / 256;
+
+template <class T>
+__device__ __forceinline__ void dt_fetch_rows(T (&v)[DT_PER], const T* M, int ld, int r0, int c0, int nr, int nc) {
+#pragma unroll
+    for (int q = 0; q < DT_PER; ++q) {
+        const int t = threadIdx.x + q * 256, r = t / DT_K, c = t % DT_K;
+        v[q] = (r0 + r < nr && c0 + c < nc) ? M[(size_t)(r0 + r) * ld + c0 + c] : T(0);
+    }
+}
+template <class T>
+__device__ __forceinline__ void dt_store_rows(T (*S)[DT_K + 1], const T (&v)[DT_PER]) {
+#pragma unroll
+    for (int q = 0; q < DT_PER; ++q) {
+        const int t = threadIdx.x + q * 256;
+        S[t / DT_K][t % DT_K] = v[q];
+    }
+}
 template <class T>
 __device__ __forceinline__ void dt_load_rows(T (*S)[DT_K + 1], const T* M, int ld, int r0, int c0, int nr, int nc) {
-    for (int t = threadIdx.x; t < DT_T * DT_K; t += 256) {
-        const int r = t / DT_K, c = t % DT_K;
-        S[r][c] = (r0 + r < nr && c0 + c < nc) ? M[(size_t)(r0 + r) * ld + c0 + c] : T(0);
-    }
+    T v[DT_PER];
+    dt_fetch_rows<T>(v, M, ld, r0, c0, nr, nc);
+    dt_store_rows<T>(S, v);
 }
 
 // Loads rows [k0, k0 + 32) x columns [c0, c0 + 64) into S[64][33] transposed (S[c][k]).
 template <class T>
-__device__ __forceinline__ void dt_load_cols(T (*S)[DT_K + 1], const T* M, int ld, int k0, int c0, int nk, int nc) {
-    for (int t = threadIdx.x; t < DT_T * DT_K; t += 256) {
-        const int k = t / DT_T, c = t % DT_T;
-        S[c][k] = (k0 + k < nk && c0 + c < nc) ? M[(size_t)(k0 + k) * ld + c0 + c] : T(0);
+__device__ __forceinline__ void dt_fetch_cols(T (&v)[DT_PER], const T* M, int ld, int k0, int c0, int nk, int nc) {
+#pragma unroll
+    for (int q = 0; q < DT_PER; ++q) {
+        const int t = threadIdx.x + q * 256, k = t / DT_T, c = t % DT_T;
+        v[q] = (k0 + k < nk && c0 + c < nc) ? M[(size_t)(k0 + k) * ld + c0 + c] : T(0);
     }
+}
+template <class T>
+__device__ __forceinline__ void dt_store_cols(T (*S)[DT_K + 1], const T (&v)[DT_PER]) {
+#pragma unroll
+    for (int q = 0; q < DT_PER; ++q) {
+        const int t = threadIdx.x + q * 256;
+        S[t % DT_T][t / DT_T] = v[q];
+    }
+}
+template <class T>
+__device__ __forceinline__ void dt_load_cols(T (*S)[DT_K + 1], const T* M, int ld, int k0, int c0, int nk, int nc) {
+    T v[DT_PER];
+    dt_fetch_cols<T>(v, M, ld, k0, c0, nk, nc);
+    dt_store_cols<T>(S, v);
 }
 
 // acc[a][b] += sum_k X[ty * 4 + a][k] * Y[tx * 4 + b][k] over one slice.
@@ -2111,7 +2213,8 @@ void dense_chol_inverse(int n, T* M, T* Ainv, int* fail, cudaStream_t s) {
     for (int jb = 0; jb < n; jb += CHOL_NB) {
         const int nb = std::min(CHOL_NB, n - jb);
         T* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
-        k_chol_diag<T><<<1, CHOL_DT, 0, s>>>(n, jb, M, li, fail);
+        if constexpr (std::is_same<T, float>::value) k_chol_diag_warp<<<1, 32, 0, s>>>(n, jb, M, li, fail);
+        else k_chol_diag<T><<<1, CHOL_DT, 0, s>>>(n, jb, M, li, fail);
         const int below = n - jb - nb;
         if (below > 0) {
             k_chol_trsm<T><<<(below + 15) / 16, 128, 0, s>>>(n, jb, M, li, fail);
@@ -2141,10 +2244,18 @@ void dense_chol_inverse(int n, T* M, T* Ainv, int* fail, cudaStream_t s) {
 // E is formed in FP64 from the sparse A_c and the FP64 X; the correction X E needs only the
 // relative accuracy of E's size, so it is a tile product in FP32 (X and E rounded), added to X in
 // FP64.  From the FP32 Cholesky inverse (max |E| about 1e-5 at kappa 6e5) two steps reach the FP64
-// rounding level; INV_STEPS = 3, then the final max |E| decides (INV_TOL) whether X is kept.
+// rounding level.  At most INV_STEPS steps; once max |E| <= INV_SKIP (the rounding level) the later
+// kernels return at once, and the last max |E| formed decides (INV_TOL) whether X is kept.
 // --------------------------------------------------------------------------------------------
 constexpr int INV_STEPS = 3;
 constexpr double INV_TOL = 1e-12;
+constexpr double INV_SKIP = 1e-13;
+constexpr int INV_ROWS = 4;             // rows of E per block of k_inv_resid
+
+// max |E| of an earlier step (bits of a non-negative double) at the rounding level: stop refining
+__device__ __forceinline__ bool inv_converged(const unsigned long long* e) {
+    return e && __longlong_as_double((long long)*(volatile unsigned long long*)e) <= INV_SKIP;
+}
 
 template <class A, class B>
 __global__ void k_convert(int64_t count, const A* x, B* y, const int* fail) {
@@ -2153,22 +2264,23 @@ __global__ void k_convert(int64_t count, const A* x, B* y, const int* fail) {
     if (t < count) y[t] = B(x[t]);
 }
 
-// E = I - A_c X, row i = blockIdx.y, columns over the threads; E (if not null) is stored rounded
+// E = I - A_c X, rows [INV_ROWS blockIdx.y, + INV_ROWS), columns over the threads; E (if not null) is stored rounded
 // to FP32.  The largest |E_ij| goes to *emax as the bits of a non-negative double (which order as
-// unsigned integers); a NaN or an infinity counts as infinity.
+// unsigned integers); a NaN or an infinity counts as infinity.  Nothing is done if the previous
+// step's max |E| (prev, may be null) had reached the rounding level.
 __global__ void __launch_bounds__(256) k_inv_resid(int n, const int* ptr, const int* col, const double* val,
                                                    const double* X, float* E, unsigned long long* emax,
-                                                   const int* fail) {
+                                                   const unsigned long long* prev, const int* fail) {
     __shared__ double wmax[8];
-    if (*(volatile int*)fail) return;
-    const int i = blockIdx.y, j = blockIdx.x * 256 + threadIdx.x;
+    if (*(volatile int*)fail || inv_converged(prev)) return;
+    const int j = blockIdx.x * 256 + threadIdx.x;
     double m = 0.0;
-    if (j < n) {
+    for (int i = blockIdx.y * INV_ROWS; i < min(n, (int)(blockIdx.y + 1) * INV_ROWS) && j < n; ++i) {
         double e = i == j ? 1.0 : 0.0;
         for (int p = ptr[i]; p < ptr[i + 1]; ++p) e -= val[p] * X[(size_t)col[p] * n + j];
         if (E) E[(size_t)i * n + j] = (float)e;
-        m = fabs(e);
-        if (!(m <= DBL_MAX)) m = INFINITY;
+        const double a = fabs(e);
+        m = a <= DBL_MAX ? fmax(m, a) : INFINITY;
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
@@ -2180,18 +2292,26 @@ __global__ void __launch_bounds__(256) k_inv_resid(int n, const int* ptr, const 
 }
 
 // X += Xf E as FP32 tiles (Xf = X rounded to FP32), with the sum in FP64; Xn receives the new X
-// rounded to FP32 for the next step (a buffer of its own: other blocks still read Xf).
+// rounded to FP32 for the next step (a buffer of its own: other blocks still read Xf).  Nothing is
+// done if this step's max |E| (emax) is at the rounding level.
 __global__ void __launch_bounds__(256) k_inv_correct(int n, const float* Xf, const float* E, double* X, float* Xn,
-                                                     const int* fail) {
+                                                     const unsigned long long* emax, const int* fail) {
     __shared__ float Xs[DT_T][DT_K + 1], Es[DT_T][DT_K + 1];
-    if (*(volatile int*)fail) return;
+    if (*(volatile int*)fail || inv_converged(emax)) return;
     const int i0 = blockIdx.y * DT_T, j0 = blockIdx.x * DT_T;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float acc[4][4] = {};
+    float xv[DT_PER], ev[DT_PER];                              // the next slice, fetched during the products
+    dt_fetch_rows<float>(xv, Xf, n, i0, 0, n, n);              // rows i, columns k
+    dt_fetch_cols<float>(ev, E, n, 0, j0, n, n);               // rows k, columns j (transposed)
     for (int k0 = 0; k0 < n; k0 += DT_K) {
-        dt_load_rows<float>(Xs, Xf, n, i0, k0, n, n);          // rows i, columns k
-        dt_load_cols<float>(Es, E, n, k0, j0, n, n);           // rows k, columns j (transposed)
+        dt_store_rows<float>(Xs, xv);
+        dt_store_cols<float>(Es, ev);
         __syncthreads();
+        if (k0 + DT_K < n) {
+            dt_fetch_rows<float>(xv, Xf, n, i0, k0 + DT_K, n, n);
+            dt_fetch_cols<float>(ev, E, n, k0 + DT_K, j0, n, n);
+        }
         dt_mac<float>(Xs, Es, acc, tx, ty);
         __syncthreads();
     }
@@ -2208,9 +2328,10 @@ __global__ void __launch_bounds__(256) k_inv_correct(int n, const float* Xf, con
         }
 }
 
-// X = A_c^{-1} from the FP32 Cholesky inverse and INV_STEPS Newton-Schulz steps.  *fail32 = 1 if
-// the FP32 factorisation broke down (the later kernels then do nothing); emax[k] = max |E| before
-// step k, emax[INV_STEPS] after the last step (all zero-initialised by the caller).
+// X = A_c^{-1} from the FP32 Cholesky inverse and up to INV_STEPS Newton-Schulz steps.  *fail32 = 1
+// if the FP32 factorisation broke down (the later kernels then do nothing); emax[k] = max |E| before
+// step k, emax[INV_STEPS] after the last step (all zero-initialised by the caller; entries after
+// the first at the rounding level stay 0).
 void refined_inverse(const Csr& Ac, double* X, int* fail32, unsigned long long* emax, cudaStream_t s) {
     const int n = Ac.n;
     const size_t nn = (size_t)n * n;
@@ -2224,14 +2345,26 @@ void refined_inverse(const Csr& Ac, double* X, int* fail32, unsigned long long* 
     k_convert<float, double><<<(int)((nn + TPB - 1) / TPB), TPB, 0, s>>>((int64_t)nn, Xa.get(), X, fail32);
     float* xf = Xa.get();
     float* xn = Xb.get();
-    const dim3 rgrid((n + 255) / 256, n), tgrid((n + DT_T - 1) / DT_T, (n + DT_T - 1) / DT_T);
+    const dim3 rgrid((n + 255) / 256, (n + INV_ROWS - 1) / INV_ROWS), tgrid((n + DT_T - 1) / DT_T, (n + DT_T - 1) / DT_T);
     for (int k = 0; k < INV_STEPS; ++k) {
-        k_inv_resid<<<rgrid, 256, 0, s>>>(n, Ac.ptr.p, Ac.col.p, Ac.val.p, X, E.get(), emax + k, fail32);
-        k_inv_correct<<<tgrid, 256, 0, s>>>(n, xf, E.get(), X, xn, fail32);
+        k_inv_resid<<<rgrid, 256, 0, s>>>(n, Ac.ptr.p, Ac.col.p, Ac.val.p, X, E.get(), emax + k,
+                                          k ? emax + k - 1 : nullptr, fail32);
+        k_inv_correct<<<tgrid, 256, 0, s>>>(n, xf, E.get(), X, xn, emax + k, fail32);
         std::swap(xf, xn);
     }
-    k_inv_resid<<<rgrid, 256, 0, s>>>(n, Ac.ptr.p, Ac.col.p, Ac.val.p, X, nullptr, emax + INV_STEPS, fail32);
+    k_inv_resid<<<rgrid, 256, 0, s>>>(n, Ac.ptr.p, Ac.col.p, Ac.val.p, X, nullptr, emax + INV_STEPS,
+                                      emax + INV_STEPS - 1, fail32);
     CPC_LAUNCH_CK();
+}
+
+// The residual the refinement ended with: the first max |E| at the rounding level, else the last.
+double refined_residual(const unsigned long long* emax_host) {
+    double e = 0.0;
+    for (int k = 0; k <= INV_STEPS; ++k) {
+        std::memcpy(&e, &emax_host[k], sizeof e);
+        if (e <= INV_SKIP) return e;
+    }
+    return e;
 }
 
 // ============================================================================================
@@ -2720,9 +2853,10 @@ void setup_handle(Handle& h, const cpc_csr& in) {
     CPC_CK(cudaStreamWaitEvent(s, ph[2], 0));
     {   // keep the refined inverse if its residual reached INV_TOL, else the FP64 Cholesky inverse
         const int f32 = d2h(inv_fail.get() + 1, s2);
-        const unsigned long long eb = d2h(emax.get() + INV_STEPS, s2);
-        double e;
-        std::memcpy(&e, &eb, sizeof e);
+        unsigned long long eb[INV_STEPS + 1];
+        CPC_CK(cudaMemcpyAsync(eb, emax.get(), sizeof eb, cudaMemcpyDeviceToHost, s2));
+        CPC_CK(cudaStreamSynchronize(s2));
+        const double e = refined_residual(eb);
         h.inv_method = 1;
         h.inv_resid = f32 ? INFINITY : e;
         if (f32 || !(e <= INV_TOL)) {
@@ -2733,9 +2867,9 @@ void setup_handle(Handle& h, const cpc_csr& in) {
                 k_csr_to_dense<double><<<nblk(h.nc), TPB, 0, s2>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, M.get());
                 dense_chol_inverse<double>(h.nc, M.get(), h.Ainv.p, inv_fail.get(), s2);
             }
-            k_inv_resid<<<dim3((h.nc + 255) / 256, h.nc), 256, 0, s2>>>(h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p,
-                                                                         h.Ainv.p, nullptr, emax.get() + INV_STEPS + 1,
-                                                                         inv_fail.get());
+            k_inv_resid<<<dim3((h.nc + 255) / 256, (h.nc + INV_ROWS - 1) / INV_ROWS), 256, 0, s2>>>(
+                h.nc, Lc.A.ptr.p, Lc.A.col.p, Lc.A.val.p, h.Ainv.p, nullptr, emax.get() + INV_STEPS + 1, nullptr,
+                inv_fail.get());
             CPC_LAUNCH_CK();
             CPC_CK(cudaEventRecord(c1, s2));
             const unsigned long long eb64 = d2h(emax.get() + INV_STEPS + 1, s2);
