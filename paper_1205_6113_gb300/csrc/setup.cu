@@ -1792,11 +1792,11 @@ void sell_lowp(Sell& S, VType vt, cudaStream_t s) {
 // ============================================================================================
 // Coarsest level: the explicit inverse X = A_c^{-1} (Algorithm 3.2, step 2(b)).
 // Dense Cholesky A_c = L L^T, blocked right-looking with panels of NB = 32 columns:
-//   k_chol_diag   factor the 32 x 32 diagonal block with four warps and invert it,
-//   k_chol_trsm   L21 = A21 L11^{-T} as a tile product with that inverse,
-//   k_chol_syrk   A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles;
-// then W = L^{-1} by row panels (k_trinv_panel, k_trinv_update) and A_c^{-1} = W^T W (k_lauum_part,
-// k_lauum_sum).  L is left in the lower triangle of M.  The kernels are templated on the element
+//   k_chol_diag   factor the 32 x 32 diagonal block and invert it (k_chol_diag_warp in FP32),
+//   chol_trsm     L21 = A21 L11^{-T} as a tile product with that inverse,
+//   chol_syrk     A22 -= L21 L21^T on the lower triangle, 64 x 64 tiles;
+// with W = L^{-1} by row panels in the same launches (trinv_panel, trinv_update: k_panel_rows and
+// k_panel_update), then A_c^{-1} = W^T W (k_lauum_part, k_lauum_sum).  L is left in the lower triangle of M.  The kernels are templated on the element
 // type: the inverse is first formed in FP32 (FP64 issue is scarce on this part) and then refined
 // to FP64 accuracy by Newton-Schulz steps (refined_inverse); the FP64 instantiation is the
 // fallback when that does not converge.
@@ -1950,11 +1950,10 @@ __global__ void __launch_bounds__(32) k_chol_diag_warp(int n, int jb, float* M, 
 // Rows i >= jb + nb of the panel: l_i = a_i L11^{-T} = a_i Li^T, a tile product (16 rows x 32
 // columns per block of 128 threads; each thread 4 columns of one row).
 template <class T>
-__global__ void __launch_bounds__(128) k_chol_trsm(int n, int jb, T* M, const T* Li, const int* fail) {
-    __shared__ T As[16][CHOL_NB + 1], Ls[CHOL_NB][CHOL_NB + 1];
-    if (*(volatile int*)fail) return;
+__device__ __forceinline__ void chol_trsm_block(int n, int jb, T* M, const T* Li, int bx, T (*As)[CHOL_NB + 1],
+                                                T (*Ls)[CHOL_NB + 1]) {
     const int nb = min(CHOL_NB, n - jb);
-    const int i0 = jb + nb + blockIdx.x * 16;
+    const int i0 = jb + nb + bx * 16;
     for (int t = threadIdx.x; t < 16 * CHOL_NB; t += 128) {
         const int r = t / CHOL_NB, c = t % CHOL_NB;
         As[r][c] = (i0 + r < n && c < nb) ? M[(size_t)(i0 + r) * n + jb + c] : T(0);
@@ -2054,11 +2053,8 @@ __device__ __forceinline__ void dt_mac(const T (*X)[DT_K + 1], const T (*Y)[DT_K
 // Trailing update of the lower triangle: a_ik -= sum_m l_im l_km over the panel columns
 // [jb, jb + nb), for jb + nb <= k <= i; block (bi, bk) with bk <= bi covers a 64 x 64 tile.
 template <class T>
-__global__ void __launch_bounds__(256) k_chol_syrk(int n, int jb, T* M, const int* fail) {
-    __shared__ T Li[DT_T][DT_K + 1], Lk[DT_T][DT_K + 1];
-    if (*(volatile int*)fail) return;
-    const int bi = blockIdx.y, bk = blockIdx.x;
-    if (bk > bi) return;
+__device__ __forceinline__ void chol_syrk_block(int n, int jb, T* M, int bi, int bk, T (*Li)[DT_K + 1],
+                                                T (*Lk)[DT_K + 1]) {
     const int nb = min(CHOL_NB, n - jb);
     const int t0 = jb + nb;
     const int i0 = t0 + bi * DT_T, k0 = t0 + bk * DT_T;
@@ -2083,12 +2079,11 @@ __global__ void __launch_bounds__(256) k_chol_syrk(int n, int jb, T* M, const in
 // on stay zero.  A tile product: 32 rows x 16 columns per block of 128 threads, each thread 4 rows
 // of one column.
 template <class T>
-__global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const T* Li, T* W, const int* fail) {
-    __shared__ T Rs[CHOL_NB][17], Ls[CHOL_NB][CHOL_NB + 1];
-    if (*(volatile int*)fail) return;
+__device__ __forceinline__ void trinv_panel_block(int n, int jb, const T* Li, T* W, int bx, T (*Rs)[17],
+                                                  T (*Ls)[CHOL_NB + 1]) {
     const int nb = min(CHOL_NB, n - jb);
     const int e = jb + nb;
-    const int j0 = blockIdx.x * 16;
+    const int j0 = bx * 16;
     for (int t = threadIdx.x; t < CHOL_NB * 16; t += 128) {
         const int r = t / 16, c = t % 16;
         Rs[r][c] = (r < nb && j0 + c < e) ? W[(size_t)(jb + r) * n + j0 + c] : T(0);
@@ -2111,12 +2106,11 @@ __global__ void __launch_bounds__(128) k_trinv_panel(int n, int jb, const T* Li,
 
 // Rows below panel p: R_ij -= sum_m l_i,jb+m w_jb+m,j for i >= e, j < e (e = the panel's end).
 template <class T>
-__global__ void __launch_bounds__(256) k_trinv_update(int n, int jb, const T* L, T* W, const int* fail) {
-    __shared__ T Ls[DT_T][DT_K + 1], Ws[DT_T][DT_K + 1];
-    if (*(volatile int*)fail) return;
+__device__ __forceinline__ void trinv_update_block(int n, int jb, const T* L, T* W, int bx, int by,
+                                                   T (*Ls)[DT_K + 1], T (*Ws)[DT_K + 1]) {
     const int nb = min(CHOL_NB, n - jb);
     const int e = jb + nb;
-    const int i0 = e + blockIdx.y * DT_T, j0 = blockIdx.x * DT_T;
+    const int i0 = e + by * DT_T, j0 = bx * DT_T;
     dt_load_rows<T>(Ls, L, n, i0, jb, n, e);        // rows i, panel columns
     dt_load_cols<T>(Ws, W, n, jb, j0, e, e);        // panel rows of W, columns j < e (transposed)
     __syncthreads();
@@ -2130,6 +2124,39 @@ __global__ void __launch_bounds__(256) k_trinv_update(int n, int jb, const T* L,
             const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
             if (i < n && j < e) W[(size_t)i * n + j] -= acc[a][b];
         }
+}
+
+// One launch per panel for its rows of L (blocks [0, nt), chol_trsm_block) and its rows of W (the
+// other blocks, trinv_panel_block): both need only Li and the data before the panel, and they
+// write disjoint arrays, so the factorisation and W = L^{-1} advance in the same chain of launches.
+template <class T>
+__global__ void __launch_bounds__(128) k_panel_rows(int n, int jb, T* M, const T* Li, T* W, int nt, const int* fail) {
+    __shared__ T buf[CHOL_NB * (CHOL_NB + 1)];                  // As[16][33] or Rs[32][17]
+    __shared__ T Ls[CHOL_NB][CHOL_NB + 1];
+    if (*(volatile int*)fail) return;
+    if ((int)blockIdx.x < nt)
+        chol_trsm_block<T>(n, jb, M, Li, blockIdx.x, reinterpret_cast<T(*)[CHOL_NB + 1]>(buf), Ls);
+    else
+        trinv_panel_block<T>(n, jb, Li, W, blockIdx.x - nt, reinterpret_cast<T(*)[17]>(buf), Ls);
+}
+
+// One launch per panel for the trailing update of L's lower triangle (blocks [0, ns): the lower
+// triangle of tiles, row-major) and the update of W's rows below the panel (the other blocks, wx
+// tiles per row of tiles).  The trailing update writes columns from the panel's end on, the W update
+// reads L only in the panel's columns.
+template <class T>
+__global__ void __launch_bounds__(256) k_panel_update(int n, int jb, T* M, T* W, int ns, int wx, const int* fail) {
+    __shared__ T S0[DT_T][DT_K + 1], S1[DT_T][DT_K + 1];
+    if (*(volatile int*)fail) return;
+    const int b = blockIdx.x;
+    if (b < ns) {
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= b) ++bi;
+        chol_syrk_block<T>(n, jb, M, bi, b - bi * (bi + 1) / 2, S0, S1);
+    } else {
+        const int q = b - ns;
+        trinv_update_block<T>(n, jb, M, W, q % wx, q / wx, S0, S1);
+    }
 }
 
 // A^{-1} = W^T W, tile (bi, bj) with bj <= bi: x_ij = sum_k w_ki w_kj over k >= i0 (W is lower
@@ -2210,28 +2237,24 @@ void dense_chol_inverse(int n, T* M, T* Ainv, int* fail, cudaStream_t s) {
     h2d(dcnt.get(), cnt.data(), cnt.size(), s);
     const int np = (n + CHOL_NB - 1) / CHOL_NB;
     Tmp<T> Li((size_t)np * CHOL_NB * CHOL_NB, s);               // L_pp^{-1} of every panel
-    for (int jb = 0; jb < n; jb += CHOL_NB) {
-        const int nb = std::min(CHOL_NB, n - jb);
-        T* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
-        if constexpr (std::is_same<T, float>::value) k_chol_diag_warp<<<1, 32, 0, s>>>(n, jb, M, li, fail);
-        else k_chol_diag<T><<<1, CHOL_DT, 0, s>>>(n, jb, M, li, fail);
-        const int below = n - jb - nb;
-        if (below > 0) {
-            k_chol_trsm<T><<<(below + 15) / 16, 128, 0, s>>>(n, jb, M, li, fail);
-            const int tiles = (below + DT_T - 1) / DT_T;
-            k_chol_syrk<T><<<dim3(tiles, tiles), 256, 0, s>>>(n, jb, M, fail);
-        }
-    }
-    // W = L^{-1} in a scratch of its own, then A^{-1} = W^T W
+    // W = L^{-1} in a scratch of its own, formed panel by panel with the factorisation; then
+    // A^{-1} = W^T W
     Tmp<T> W((size_t)n * n, s);
     k_identity<T><<<(int)(((int64_t)n * n + TPB - 1) / TPB), TPB, 0, s>>>(n, W.get());
     for (int jb = 0; jb < n; jb += CHOL_NB) {
-        const int e = std::min(jb + CHOL_NB, n);
-        const T* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
-        k_trinv_panel<T><<<(e + 15) / 16, 128, 0, s>>>(n, jb, li, W.get(), fail);
-        if (e < n)
-            k_trinv_update<T><<<dim3((e + DT_T - 1) / DT_T, (n - e + DT_T - 1) / DT_T), 256, 0, s>>>(n, jb, M, W.get(),
-                                                                                                    fail);
+        const int nb = std::min(CHOL_NB, n - jb);
+        const int e = jb + nb;
+        T* li = Li.get() + (size_t)(jb / CHOL_NB) * CHOL_NB * CHOL_NB;
+        if constexpr (std::is_same<T, float>::value) k_chol_diag_warp<<<1, 32, 0, s>>>(n, jb, M, li, fail);
+        else k_chol_diag<T><<<1, CHOL_DT, 0, s>>>(n, jb, M, li, fail);
+        const int below = n - e;
+        const int nt = (below + 15) / 16;
+        k_panel_rows<T><<<nt + (e + 15) / 16, 128, 0, s>>>(n, jb, M, li, W.get(), nt, fail);
+        if (below > 0) {
+            const int tiles = (below + DT_T - 1) / DT_T, ns = tiles * (tiles + 1) / 2;
+            const int wx = (e + DT_T - 1) / DT_T;
+            k_panel_update<T><<<ns + wx * tiles, 256, 0, s>>>(n, jb, M, W.get(), ns, wx, fail);
+        }
     }
     k_lauum_part<T><<<(int)items.size(), 256, 0, s>>>(n, W.get(), ditems.get(), part.get(), fail);
     k_lauum_sum<T><<<(int)first.size(), 256, 0, s>>>(n, ditems.get(), dfirst.get(), dcnt.get(), part.get(), Ainv, fail);
