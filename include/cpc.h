@@ -251,8 +251,9 @@ int cpc_setup_time_ms(const cpc_handle* h, double* ms_ic0, double* ms_amg);
 /* The AMG setup of cpc_setup_time_ms split into its phases (GPU events, milliseconds): ms[0]
  * coarsening (strength, C/F splitting, interpolation and the Galerkin products A_l = P_l^T A_{l+1}
  * P_l of Section 3.2, all levels), ms[1] smoothing colours (or natural-order wavefronts) of all
- * levels, ms[2] the coarsest level's dense Cholesky inverse (Algorithm 3.2, step 2(b)), ms[3] the
- * kernels' layouts.  At most cap (<= 4) values are written.  Host memory. */
+ * levels, ms[2] the coarsest level's explicit inverse (Algorithm 3.2, step 2(b); see
+ * cpc_coarse_inverse_info), ms[3] the kernels' layouts (built beside the inverse).  At most cap
+ * (<= 4) values are written.  Host memory. */
 int cpc_setup_phases_ms(const cpc_handle* h, double* ms, int32_t cap);
 
 /* How the coarsest level's explicit inverse X = A_c^{-1} (Algorithm 3.2, step 2(b)) was formed:
