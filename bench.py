@@ -368,7 +368,8 @@ def gpu_arm(args, rank, world):
                     fine_gs=fine, spmv=spmv)
     out.update(dict(p=p, arms=arms, matrices=matrices, clocks=clk, e2e_ms=e2e_ms, true_res=true_res,
                     setups=setups, roofline=roofline, headline_ms=headline_ms, bytes_per_iter=bpi, xs=xs,
-                    nlevels=s_bco.nlevels, levels=[s_bco.level_info(l) for l in range(s_bco.nlevels)]))
+                    nlevels=s_bco.nlevels, levels=[s_bco.level_info(l) for l in range(s_bco.nlevels)],
+                    coarse_inverse=s_bco.coarse_inverse_info()))
     out["solve_gbs"] = bpi * iters[-1] / (headline_ms * 1e-3) / 1e9
     out["launches"] = s_bco.solve_launches()
     return out
@@ -781,7 +782,10 @@ def main():
         "hierarchy": {"n": [int(l["n"]) for l in out["levels"]], "nnz": [int(l["nnz"]) for l in out["levels"]],
                       "colours": [int(l["ncolours"]) for l in out["levels"][:-1]],
                       "operator_complexity": round(sum(l["nnz"] for l in out["levels"]) / out["levels"][0]["nnz"], 3),
-                      "grid_complexity": round(sum(l["n"] for l in out["levels"]) / out["levels"][0]["n"], 3)},
+                      "grid_complexity": round(sum(l["n"] for l in out["levels"]) / out["levels"][0]["n"], 3),
+                      "coarse_inverse": {"method": ("fp32 cholesky + newton-schulz" if out["coarse_inverse"][0] == 1
+                                                    else "fp64 cholesky"),
+                                         "residual": float(out["coarse_inverse"][1])}},
     }
     headline_ms = round(value, 3)
     if arms:
